@@ -1,0 +1,849 @@
+/*
+ * Plain FP64 CPU oracle of the dimensional lattice Boltzmann method of
+ * Martins, Alvarino & Cabezas-Gomez, "Dimensional lattice Boltzmann method for
+ * transport phenomena simulation without conversion to lattice units"
+ * (arXiv:2302.04120).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * definition the CUDA path is checked against.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * Formulation (deliberately different from the GPU kernels):
+ *   - state = PRE-collision distributions f(t), g(t), h(t), z(t);
+ *   - one step = moments -> collision -> PUSH streaming with link-wise
+ *     boundary rules (the GPU pulls);
+ *   - MRT collisions use EXPLICIT 9x9 / 5x5 matrix-vector products with the
+ *     dimensional matrices (the GPU uses unrolled closed forms);
+ *   - everything in SI units, FP64.
+ *
+ * Paper passages followed (section / equation labels of the paper):
+ *   LBE and BGK ............................ Sec. 2.1, Eqs. eq_lattice_boltzmann_geral, _BGK
+ *   equilibrium f_eq ....................... Eq. feq_geral
+ *   D2Q9 set, c_s = c/sqrt3, c = dx/dt ...... Eqs. velocity_D2Q9, weights_D2Q9
+ *   nu = (tau - dt/2) c_s^2 ................ Eq. eq_kinematic_viscosity
+ *   Guo forcing ............................ Eq. forcing_term
+ *   MRT, M, collision with forcing ......... Eqs. M_matrix, colisao_MRT
+ *   macroscopic moments .................... Eqs. zero_moment_f, first_moment_f
+ *   link-wise BB / BB-velocity ............. Eq. BB_vel
+ *   anti-BB pressure outlet ................ Eq. anti_BB_vel (+ velocity extrapolation)
+ *   periodic ............................... Sec. 2.1, last paragraph
+ *   thermal DDF, source, g_eq, T ........... Eqs. eq_lattice_boltzmann_BGK_T, forcing_term_g,
+ *                                            geq_geral, zero_moment_g
+ *   thermal anti-BB, heat-flux BB, outlet .. Eqs. anti_BB_T, BB_T, Sec. 2.2 last paragraph
+ *   Allen-Cahn h LBE ....................... Eqs. eq_lattice_boltzmann_interface,
+ *                                            source_term_interface, heq_liang, zero_moment_h
+ *   pressure-evolution z LBE ............... Eqs. eq_lattice_boltzmann_pressure, zeq_liang,
+ *                                            s_i_Liang, forcing_term_pressure_evolution,
+ *                                            p_Liang, u_Liang
+ *   chemical potential, stencils ........... Eqs. chemical_potential, gradient, laplacian
+ *   dimensional M and rates ................ Sec. 3, Eq. M_matrix_dim, App. A Eq. Minv_matrix_dim
+ *
+ * Readings where the paper is silent, ambiguous or misprinted are listed in the
+ * design notes (R1 ... R26); the ones that change arithmetic are marked "reading"
+ * at the line that applies them.
+ *
+ * Lattice D2Q5 used for g and h (extension of the paper, which prints D2Q9 for
+ * both): c = {0, +x, +y, -x, -y}, w = {1/3, 1/6, 1/6, 1/6, 1/6}, c_s^2 = c^2/3.
+ * Its MRT matrix rows are (1, c_x, c_y, 5|c|^2-4c^2, c_x^2-c_y^2), scaled by c^n.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Public parameter block (mirrored field by field by the ctypes wrapper).    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int nx, ny;
+  int flow;        /* 0: no momentum LBE (velocity prescribed), 9: D2Q9 f      */
+  int flow_op;     /* 0 BGK, 1 MRT                                             */
+  int thermal;     /* 0 none, 5: D2Q5 g                                        */
+  int thermal_op;  /* 0 BGK, 1 MRT                                             */
+  int phase;       /* 0 single phase, 5: two-phase, h on D2Q5 and z on D2Q9    */
+  int z_op;        /* 0 BGK, 1 MRT for z                                       */
+  int nu_rule;     /* 0: nu linear in phi, 1: nu = zeta/rho, zeta linear in phi*/
+  int literal;     /* bit0: S_g with momentum tau (as printed),
+                      bit1: multiphase q_y relaxed at 1/dt (as printed)        */
+  double dx, dt;
+  double rho0, nu, cp, k, T0;
+  double rho_l, rho_g, nu_l, nu_g, sigma, W, mobility;
+  double omega_e_dt, omega_eps_dt;  /* free MRT rates times dt                 */
+  double Fb[2];                     /* uniform body force, N m^-3              */
+  double u_prescribed[2];           /* velocity used when flow == 0            */
+  double conv_coef, T_inf;          /* lagged sink: qdot -= conv_coef (T_prev - T_inf) */
+} orc_params;
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3 };
+enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3 };
+
+/* ------------------------------------------------------------------------- */
+/* Velocity sets                                                             */
+/* ------------------------------------------------------------------------- */
+/* D2Q9, Eqs. velocity_D2Q9 / weights_D2Q9 */
+static const int CX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+/* D2Q5 (extension) */
+static const int CX5[5] = {0, 1, 0, -1, 0};
+static const int CY5[5] = {0, 0, 1, 0, -1};
+static const double W5[5] = {1.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+
+/* Lattice transformation matrix, Eq. M_matrix (rows rho,e,eps,jx,qx,jy,qy,pxx,pxy) */
+static const double M9_LATTICE[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+/* moment order of each row: c^n scaling of Eq. M_matrix_dim */
+static const int ORDER9[9] = {0, 2, 4, 1, 3, 1, 3, 2, 2};
+
+/* Lattice inverse of App. A, Eq. Minv_matrix; the dimensional inverse of
+   Eq. Minv_matrix_dim divides column k by c^(order k).  One printed entry is
+   corrected: row i = 2, column q_y is printed +1/6 but M M^-1 = I needs -1/6
+   (reading R27; the test-suite checks both facts). */
+static const double MINV9_LATTICE[9][9] = {
+    {1.0 / 9, -1.0 / 9, 1.0 / 9, 0, 0, 0, 0, 0, 0},
+    {1.0 / 9, -1.0 / 36, -1.0 / 18, 1.0 / 6, -1.0 / 6, 0, 0, 1.0 / 4, 0},
+    {1.0 / 9, -1.0 / 36, -1.0 / 18, 0, 0, 1.0 / 6, -1.0 / 6, -1.0 / 4, 0},
+    {1.0 / 9, -1.0 / 36, -1.0 / 18, -1.0 / 6, 1.0 / 6, 0, 0, 1.0 / 4, 0},
+    {1.0 / 9, -1.0 / 36, -1.0 / 18, 0, 0, -1.0 / 6, 1.0 / 6, -1.0 / 4, 0},
+    {1.0 / 9, 1.0 / 18, 1.0 / 36, 1.0 / 6, 1.0 / 12, 1.0 / 6, 1.0 / 12, 0, 1.0 / 4},
+    {1.0 / 9, 1.0 / 18, 1.0 / 36, -1.0 / 6, -1.0 / 12, 1.0 / 6, 1.0 / 12, 0, -1.0 / 4},
+    {1.0 / 9, 1.0 / 18, 1.0 / 36, -1.0 / 6, -1.0 / 12, -1.0 / 6, -1.0 / 12, 0, 1.0 / 4},
+    {1.0 / 9, 1.0 / 18, 1.0 / 36, 1.0 / 6, 1.0 / 12, -1.0 / 6, -1.0 / 12, 0, -1.0 / 4}};
+
+/* D2Q5 moments (1, c_x, c_y, 5|c|^2 - 4, c_x^2 - c_y^2) in lattice units */
+static const double M5_LATTICE[5][5] = {
+    {1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0},
+    {0, 0, 1, 0, -1},
+    {-4, 1, 1, 1, 1},
+    {0, 1, -1, 1, -1}};
+static const int ORDER5[5] = {0, 1, 1, 2, 2};
+
+/* ------------------------------------------------------------------------- */
+/* Oracle state                                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  orc_params p;
+  int N;
+  double c, cs2;                 /* lattice speed dx/dt and c_s^2 = c^2/3          */
+  double tau, tauT, tauphi;      /* relaxation times in seconds                    */
+  double Md[81], Mdinv[81];      /* dimensional D2Q9 M and inverse                 */
+  double M5d[25], M5dinv[25];    /* dimensional D2Q5 M and inverse                 */
+  double *f, *fn, *fpost;
+  double *g, *gn, *gpost;
+  double *h, *hn, *hpost;
+  double *z, *zn, *zpost;
+  double *rho, *ux, *uy, *T, *pr, *phi, *Tprev, *phiux_prev, *phiuy_prev;
+  double *q3;                    /* q''' field in W m^-3, or NULL                   */
+  double *force;                 /* per-cell force (2N) in N m^-3, or NULL          */
+  int bc[4], tbc[4];
+  double rho_w[4];
+  double *bcu[4];                /* per side: 2*len (u_x then u_y)                 */
+  double *bct[4];                /* per side: len (q'' in W m^-2 or T_w in K)      */
+  long steps;
+} orc_t;
+
+static int side_len(const orc_t *o, int side) { return side < 2 ? o->p.ny : o->p.nx; }
+static int idx(const orc_t *o, int i, int j) { return j * o->p.nx + i; }
+
+/* Gauss-Jordan inverse with partial pivoting of an n x n matrix (row-major). */
+static int invert(int n, const double *a_in, double *inv) {
+  double a[81];
+  memcpy(a, a_in, sizeof(double) * n * n);
+  for (int r = 0; r < n; r++)
+    for (int s = 0; s < n; s++) inv[r * n + s] = (r == s) ? 1.0 : 0.0;
+  for (int col = 0; col < n; col++) {
+    int piv = col;
+    for (int r = col + 1; r < n; r++)
+      if (fabs(a[r * n + col]) > fabs(a[piv * n + col])) piv = r;
+    if (a[piv * n + col] == 0.0) return -1;
+    for (int s = 0; s < n; s++) {
+      double t = a[col * n + s]; a[col * n + s] = a[piv * n + s]; a[piv * n + s] = t;
+      t = inv[col * n + s]; inv[col * n + s] = inv[piv * n + s]; inv[piv * n + s] = t;
+    }
+    double d = a[col * n + col];
+    for (int s = 0; s < n; s++) { a[col * n + s] /= d; inv[col * n + s] /= d; }
+    for (int r = 0; r < n; r++) {
+      if (r == col) continue;
+      double m = a[r * n + col];
+      if (m == 0.0) continue;
+      for (int s = 0; s < n; s++) {
+        a[r * n + s] -= m * a[col * n + s];
+        inv[r * n + s] -= m * inv[col * n + s];
+      }
+    }
+  }
+  return 0;
+}
+
+/* y = A x for an n x n row-major matrix */
+static void matvec(int n, const double *A, const double *x, double *y) {
+  for (int r = 0; r < n; r++) {
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s += A[r * n + k] * x[k];
+    y[r] = s;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Creation                                                                  */
+/* ------------------------------------------------------------------------- */
+void *orc_create(const orc_params *prm) {
+  orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
+  if (!o) return NULL;
+  o->p = *prm;
+  int N = o->N = prm->nx * prm->ny;
+  o->c = prm->dx / prm->dt;                  /* c = dx/dt, Sec. 2.1 */
+  o->cs2 = o->c * o->c / 3.0;                /* c_s = c/sqrt(3)     */
+  /* tau from nu = (tau - dt/2) c_s^2, Eq. eq_kinematic_viscosity */
+  o->tau = prm->nu / o->cs2 + 0.5 * prm->dt;
+  /* tau_T from alpha = (tau_T - dt/2) c_s^2, alpha = k/(rho c_p), Sec. 2.2 */
+  if (prm->thermal) o->tauT = (prm->k / (prm->rho0 * prm->cp)) / o->cs2 + 0.5 * prm->dt;
+  /* tau_phi from M = (tau_phi - dt/2) c_s^2, Sec. 2.3 */
+  if (prm->phase) o->tauphi = prm->mobility / o->cs2 + 0.5 * prm->dt;
+
+  /* [M]_dim: row k of Eq. M_matrix times c^(order k), Eq. M_matrix_dim */
+  for (int r = 0; r < 9; r++)
+    for (int s = 0; s < 9; s++) o->Md[r * 9 + s] = M9_LATTICE[r][s] * pow(o->c, ORDER9[r]);
+  /* [M]_dim^-1 of App. A, Eq. Minv_matrix_dim */
+  for (int r = 0; r < 9; r++)
+    for (int s = 0; s < 9; s++) o->Mdinv[r * 9 + s] = MINV9_LATTICE[r][s] / pow(o->c, ORDER9[s]);
+  /* D2Q5 inverse "obtained naturally, just performing the inversion" (Sec. 3):
+     [M]_dim = D [M] with D = diag(c^n), so [M]_dim^-1 = [M]^-1 D^-1; the lattice
+     matrix is inverted by Gauss-Jordan and column k divided by c^(order k). */
+  for (int r = 0; r < 5; r++)
+    for (int s = 0; s < 5; s++) o->M5d[r * 5 + s] = M5_LATTICE[r][s] * pow(o->c, ORDER5[r]);
+  {
+    double lat[25], latinv[25];
+    for (int r = 0; r < 5; r++)
+      for (int s = 0; s < 5; s++) lat[r * 5 + s] = M5_LATTICE[r][s];
+    invert(5, lat, latinv);
+    for (int r = 0; r < 5; r++)
+      for (int s = 0; s < 5; s++) o->M5dinv[r * 5 + s] = latinv[r * 5 + s] / pow(o->c, ORDER5[s]);
+  }
+
+  o->f = calloc(9 * N, sizeof(double)); o->fn = calloc(9 * N, sizeof(double));
+  o->fpost = calloc(9 * N, sizeof(double));
+  o->g = calloc(5 * N, sizeof(double)); o->gn = calloc(5 * N, sizeof(double));
+  o->gpost = calloc(5 * N, sizeof(double));
+  o->h = calloc(5 * N, sizeof(double)); o->hn = calloc(5 * N, sizeof(double));
+  o->hpost = calloc(5 * N, sizeof(double));
+  o->z = calloc(9 * N, sizeof(double)); o->zn = calloc(9 * N, sizeof(double));
+  o->zpost = calloc(9 * N, sizeof(double));
+  o->rho = calloc(N, sizeof(double)); o->ux = calloc(N, sizeof(double));
+  o->uy = calloc(N, sizeof(double)); o->T = calloc(N, sizeof(double));
+  o->pr = calloc(N, sizeof(double)); o->phi = calloc(N, sizeof(double));
+  o->Tprev = calloc(N, sizeof(double));
+  o->phiux_prev = calloc(N, sizeof(double)); o->phiuy_prev = calloc(N, sizeof(double));
+  for (int s = 0; s < 4; s++) {
+    o->bc[s] = BC_PERIODIC; o->tbc[s] = TBC_NONE; o->rho_w[s] = prm->rho0;
+    o->bcu[s] = calloc(2 * side_len(o, s), sizeof(double));
+    o->bct[s] = calloc(side_len(o, s), sizeof(double));
+  }
+  return o;
+}
+
+void orc_destroy(void *handle) {
+  orc_t *o = (orc_t *)handle;
+  if (!o) return;
+  double *bufs[] = {o->f, o->fn, o->fpost, o->g, o->gn, o->gpost, o->h, o->hn, o->hpost,
+                    o->z, o->zn, o->zpost, o->rho, o->ux, o->uy, o->T, o->pr, o->phi,
+                    o->Tprev, o->phiux_prev, o->phiuy_prev, o->q3, o->force};
+  for (unsigned b = 0; b < sizeof(bufs) / sizeof(bufs[0]); b++) free(bufs[b]);
+  for (int s = 0; s < 4; s++) { free(o->bcu[s]); free(o->bct[s]); }
+  free(o);
+}
+
+/* Derived quantities for the tests: c, c_s^2, tau, tau_T, tau_phi */
+void orc_constants(void *handle, double *out5) {
+  orc_t *o = (orc_t *)handle;
+  out5[0] = o->c; out5[1] = o->cs2; out5[2] = o->tau; out5[3] = o->tauT; out5[4] = o->tauphi;
+}
+
+/* The dimensional matrices, for the App. A pins. which: 0 M9, 1 M9^-1 (App. A),
+   2 M5, 3 M5^-1, 4 Gauss-Jordan inverse of M9 (checks the inversion routine) */
+void orc_matrix(void *handle, int which, double *out) {
+  orc_t *o = (orc_t *)handle;
+  if (which == 4) { invert(9, o->Md, out); return; }
+  const double *src = which == 0 ? o->Md : which == 1 ? o->Mdinv : which == 2 ? o->M5d : o->M5dinv;
+  memcpy(out, src, sizeof(double) * (which < 2 ? 81 : 25));
+}
+
+void orc_set_bc(void *handle, int side, int kind, const double *uw, double rho_w, int tkind,
+                const double *tw) {
+  orc_t *o = (orc_t *)handle;
+  int len = side_len(o, side);
+  o->bc[side] = kind; o->tbc[side] = tkind; o->rho_w[side] = rho_w;
+  if (uw) memcpy(o->bcu[side], uw, sizeof(double) * 2 * len);
+  else memset(o->bcu[side], 0, sizeof(double) * 2 * len);
+  if (tw) memcpy(o->bct[side], tw, sizeof(double) * len);
+  else memset(o->bct[side], 0, sizeof(double) * len);
+}
+
+void orc_set_source(void *handle, const double *q3, const double *force) {
+  orc_t *o = (orc_t *)handle;
+  free(o->q3); o->q3 = NULL; free(o->force); o->force = NULL;
+  if (q3) { o->q3 = malloc(sizeof(double) * o->N); memcpy(o->q3, q3, sizeof(double) * o->N); }
+  if (force) {
+    o->force = malloc(sizeof(double) * 2 * o->N);
+    memcpy(o->force, force, sizeof(double) * 2 * o->N);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Equilibria and source terms                                               */
+/* ------------------------------------------------------------------------- */
+/* f_eq, Eq. feq_geral */
+static double feq9(const orc_t *o, int i, double rho, double ux, double uy) {
+  double cu = o->c * (CX9[i] * ux + CY9[i] * uy);
+  double uu = ux * ux + uy * uy;
+  return W9[i] * rho * (1.0 + cu / o->cs2 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
+}
+/* Guo forcing term F_hat_i, Eq. forcing_term */
+static double fhat9(const orc_t *o, int i, double ux, double uy, double Fx, double Fy) {
+  double cx = o->c * CX9[i], cy = o->c * CY9[i];
+  double cu = cx * ux + cy * uy;
+  double ax = (cx - ux) / o->cs2 + cu * cx / (o->cs2 * o->cs2);
+  double ay = (cy - uy) / o->cs2 + cu * cy / (o->cs2 * o->cs2);
+  return W9[i] * (ax * Fx + ay * Fy);
+}
+/* linear g_eq, Eq. geq_geral (D2Q5) */
+static double geq5(const orc_t *o, int i, double T, double ux, double uy) {
+  double cu = o->c * (CX5[i] * ux + CY5[i] * uy);
+  return W5[i] * T * (1.0 + cu / o->cs2);
+}
+/* s_i(u), Eq. s_i_Liang (D2Q9) */
+static double s9(const orc_t *o, int i, double ux, double uy) {
+  double cu = o->c * (CX9[i] * ux + CY9[i] * uy);
+  double uu = ux * ux + uy * uy;
+  return W9[i] * (cu / o->cs2 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Boundary rules (link-wise, halfway).  For an outgoing direction i at the  */
+/* boundary node the rule returns the incoming population opposite to i.     */
+/* ------------------------------------------------------------------------- */
+static int opp9(int i) { static const int o9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6}; return o9[i]; }
+static int opp5(int i) { static const int o5[5] = {0, 3, 4, 1, 2}; return o5[i]; }
+
+/* Which side a link leaving node (x,y) along (cx,cy) crosses, or -1 when it stays
+   inside (after periodic wrap).  An axis is periodic for the momentum lattice when
+   both its sides are BC_PERIODIC, for the thermal lattice when both are TBC_NONE.
+   A link leaving through a corner counts as crossing the y-side (reading R10). */
+static int crossed_side(const orc_t *o, int thermal, int x, int y, int cx, int cy) {
+  int tx = x + cx, ty = y + cy;
+  int yper = thermal ? (o->tbc[2] == TBC_NONE && o->tbc[3] == TBC_NONE)
+                     : (o->bc[2] == BC_PERIODIC && o->bc[3] == BC_PERIODIC);
+  int xper = thermal ? (o->tbc[0] == TBC_NONE && o->tbc[1] == TBC_NONE)
+                     : (o->bc[0] == BC_PERIODIC && o->bc[1] == BC_PERIODIC);
+  if (!yper) {
+    if (ty < 0) return 2;
+    if (ty >= o->p.ny) return 3;
+  }
+  if (!xper) {
+    if (tx < 0) return 0;
+    if (tx >= o->p.nx) return 1;
+  }
+  return -1;
+}
+
+/* position of node (x,y) along a side: row index for x-sides, column for y-sides */
+static int along(int side, int x, int y) { return side < 2 ? y : x; }
+
+/* ------------------------------------------------------------------------- */
+/* Single-phase step                                                         */
+/* ------------------------------------------------------------------------- */
+static void moments_single(orc_t *o) {
+  const orc_params *p = &o->p;
+  int N = o->N;
+#pragma omp parallel for schedule(static)
+  for (int n = 0; n < N; n++) {
+    double Fx = p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
+    double Fy = p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+    if (p->flow) {
+      /* Eqs. zero_moment_f, first_moment_f */
+      double rho = 0, jx = 0, jy = 0;
+      for (int i = 0; i < 9; i++) {
+        double fi = o->f[i * N + n];
+        rho += fi;
+        jx += o->c * CX9[i] * fi;
+        jy += o->c * CY9[i] * fi;
+      }
+      o->rho[n] = rho;
+      o->ux[n] = (jx + 0.5 * p->dt * Fx) / rho;
+      o->uy[n] = (jy + 0.5 * p->dt * Fy) / rho;
+    }
+    if (p->thermal) {
+      double qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;   /* qdot = q'''/(rho c_p) */
+      /* lagged convective sink of the fuse problem: uses T of the previous step (R24) */
+      if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->Tprev[n] - p->T_inf);
+      double s = 0;
+      for (int i = 0; i < 5; i++) s += o->g[i * N + n];
+      o->T[n] = s + 0.5 * p->dt * qd;                          /* Eq. zero_moment_g */
+    }
+  }
+}
+
+static double qdot_at(const orc_t *o, int n) {
+  double qd = o->q3 ? o->q3[n] / (o->p.rho0 * o->p.cp) : 0.0;
+  if (o->p.conv_coef != 0.0) qd -= o->p.conv_coef * (o->Tprev[n] - o->p.T_inf);
+  return qd;
+}
+
+static void collide_single(orc_t *o) {
+  const orc_params *p = &o->p;
+  int N = o->N;
+  double dt = p->dt;
+  /* momentum MRT rates, Sec. 2.1 and Sec. 3: omega_nu = 1/tau,
+     omega_q = (3/dt)(2/dt - omega_nu)/(3/dt - omega_nu), free rates in [1/dt, 2/dt] */
+  double wnu = 1.0 / o->tau;
+  double wq = (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu);
+  double Lam[9] = {0.0, p->omega_e_dt / dt, p->omega_eps_dt / dt, 0.0, wq, 0.0, wq, wnu, wnu};
+  /* thermal D2Q5 MRT rates, analogue of [Lambda_T]_dim (reading R4) */
+  double wT = 1.0 / o->tauT;
+  double LamT[5] = {0.0, wT, wT, 1.0 / dt, 1.0 / dt};
+  /* S_g prefactor uses tau_T (reading R1); literal print uses tau */
+  double tau_sg = (p->literal & 1) ? o->tau : o->tauT;
+#pragma omp parallel for schedule(static)
+  for (int n = 0; n < N; n++) {
+    double ux = o->ux[n], uy = o->uy[n];
+    if (p->flow) {
+      double rho = o->rho[n];
+      double Fx = p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
+      double Fy = p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+      double fv[9], fe[9], fh[9];
+      for (int i = 0; i < 9; i++) {
+        fv[i] = o->f[i * N + n];
+        fe[i] = feq9(o, i, rho, ux, uy);
+        fh[i] = fhat9(o, i, ux, uy, Fx, Fy);
+      }
+      if (p->flow_op == 0) {
+        /* BGK with Guo source, Eqs. eq_lattice_boltzmann_BGK and forcing_term */
+        for (int i = 0; i < 9; i++)
+          o->fpost[i * N + n] = fv[i] - dt / o->tau * (fv[i] - fe[i]) + dt * (1.0 - dt / (2.0 * o->tau)) * fh[i];
+      } else {
+        /* MRT in moment space, Eq. colisao_MRT with [M]_dim */
+        double m[9], me[9], Fm[9], ms[9], fs[9];
+        matvec(9, o->Md, fv, m);
+        matvec(9, o->Md, fe, me);
+        matvec(9, o->Md, fh, Fm);
+        for (int k = 0; k < 9; k++)
+          ms[k] = m[k] - dt * Lam[k] * (m[k] - me[k]) + dt * (1.0 - 0.5 * dt * Lam[k]) * Fm[k];
+        matvec(9, o->Mdinv, ms, fs);
+        for (int i = 0; i < 9; i++) o->fpost[i * N + n] = fs[i];
+      }
+    }
+    if (p->thermal) {
+      double T = o->T[n];
+      double qd = qdot_at(o, n);
+      double gv[5], ge[5];
+      for (int i = 0; i < 5; i++) { gv[i] = o->g[i * N + n]; ge[i] = geq5(o, i, T, ux, uy); }
+      if (p->thermal_op == 0) {
+        /* Eqs. eq_lattice_boltzmann_BGK_T and forcing_term_g */
+        for (int i = 0; i < 5; i++)
+          o->gpost[i * N + n] = gv[i] - dt / o->tauT * (gv[i] - ge[i]) + dt * (1.0 - dt / (2.0 * tau_sg)) * W5[i] * qd;
+      } else {
+        /* D2Q5 MRT analogue of Eq. colisao_MRT with source w_i qdot (reading R4) */
+        double sv[5], m[5], me[5], Sm[5], ms[5], gs[5];
+        for (int i = 0; i < 5; i++) sv[i] = W5[i] * qd;
+        matvec(5, o->M5d, gv, m);
+        matvec(5, o->M5d, ge, me);
+        matvec(5, o->M5d, sv, Sm);
+        for (int k = 0; k < 5; k++)
+          ms[k] = m[k] - dt * LamT[k] * (m[k] - me[k]) + dt * (1.0 - 0.5 * dt * LamT[k]) * Sm[k];
+        matvec(5, o->M5dinv, ms, gs);
+        for (int i = 0; i < 5; i++) o->gpost[i * N + n] = gs[i];
+      }
+    }
+  }
+}
+
+/* Momentum: value entering node (x,y) opposite to outgoing direction i through `side`. */
+static double flow_boundary_value(const orc_t *o, int side, int x, int y, int i) {
+  int n = idx(o, x, y);
+  int N = o->N;
+  double fs = o->fpost[i * N + n];
+  int a = along(side, x, y);
+  int len = side_len(o, side);
+  double cix = o->c * CX9[i], ciy = o->c * CY9[i];
+  double rw = o->rho_w[side];
+  switch (o->bc[side]) {
+    case BC_WALL:
+    case BC_VELOCITY: {
+      /* Eq. BB_vel; the wall / inlet velocity is taken at the node's row or column */
+      double uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
+      return fs - 2.0 * W9[i] * rw * (cix * uwx + ciy * uwy) / o->cs2;
+    }
+    case BC_PRESSURE: {
+      /* Eq. anti_BB_vel; u_w = u(x_b) + (u(x_b) - u(x_{b-1}))/2 with the
+         pre-collision velocities of time t (reading R8) */
+      int nx_in = x, ny_in = y;
+      if (side == 0) nx_in = x + 1;
+      else if (side == 1) nx_in = x - 1;
+      else if (side == 2) ny_in = y + 1;
+      else ny_in = y - 1;
+      int m = idx(o, nx_in, ny_in);
+      double uwx = o->ux[n] + 0.5 * (o->ux[n] - o->ux[m]);
+      double uwy = o->uy[n] + 0.5 * (o->uy[n] - o->uy[m]);
+      double cu = cix * uwx + ciy * uwy;
+      double uu = uwx * uwx + uwy * uwy;
+      return -fs + 2.0 * W9[i] * rw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
+    }
+    default:
+      return fs; /* not reached: periodic links never cross */
+  }
+}
+
+/* Thermal (D2Q5): value entering node opposite to outgoing i through `side`;
+   OUTFLOW is resolved after streaming. */
+static double thermal_boundary_value(const orc_t *o, int side, int x, int y, int i) {
+  int n = idx(o, x, y);
+  int N = o->N;
+  double gs = o->gpost[i * N + n];
+  int a = along(side, x, y);
+  int len = side_len(o, side);
+  switch (o->tbc[side]) {
+    case TBC_FLUX: {
+      /* Eq. BB_T, lambda for the single unknown of D2Q5 = 1 (reading R5), rho = rho0 */
+      double qflux = o->bct[side][a];
+      return gs + 1.0 * (o->p.dt / o->p.dx) * qflux / (o->p.rho0 * o->p.cp);
+    }
+    case TBC_TEMP: {
+      /* Eq. anti_BB_T with the side's velocity (zero at a wall) */
+      double Tw = o->bct[side][a];
+      double uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
+      double cu = o->c * (CX5[i] * uwx + CY5[i] * uwy);
+      double uu = uwx * uwx + uwy * uwy;
+      return -gs + 2.0 * W5[i] * Tw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
+    }
+    default:
+      return gs; /* OUTFLOW placeholder, overwritten after streaming */
+  }
+}
+
+static void stream_single(orc_t *o) {
+  const orc_params *p = &o->p;
+  int N = o->N, nx = p->nx, ny = p->ny;
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      int n = idx(o, x, y);
+      if (p->flow) {
+        for (int i = 0; i < 9; i++) {
+          int side = crossed_side(o, 0, x, y, CX9[i], CY9[i]);
+          if (side < 0) {
+            int tx = (x + CX9[i] + nx) % nx, ty = (y + CY9[i] + ny) % ny;  /* periodic wrap */
+            o->fn[i * N + idx(o, tx, ty)] = o->fpost[i * N + n];
+          } else {
+            o->fn[opp9(i) * N + n] = flow_boundary_value(o, side, x, y, i);
+          }
+        }
+      }
+      if (p->thermal) {
+        for (int i = 0; i < 5; i++) {
+          int side = crossed_side(o, 1, x, y, CX5[i], CY5[i]);
+          if (side < 0) {
+            int tx = (x + CX5[i] + nx) % nx, ty = (y + CY5[i] + ny) % ny;
+            o->gn[i * N + idx(o, tx, ty)] = o->gpost[i * N + n];
+          } else {
+            o->gn[opp5(i) * N + n] = thermal_boundary_value(o, side, x, y, i);
+          }
+        }
+      }
+    }
+  /* thermal outlet: first-order extrapolation of the unknown populations,
+     g_i(x_b, t+dt) = g_i(x_{b-1}, t+dt) (Sec. 2.2; reading R9) */
+  if (p->thermal) {
+    for (int side = 0; side < 4; side++) {
+      if (o->tbc[side] != TBC_OUTFLOW) continue;
+      int len = side_len(o, side);
+      for (int a = 0; a < len; a++) {
+        int x, y, xi, yi, q;
+        if (side == 0) { x = 0; y = a; xi = 1; yi = a; q = 1; }
+        else if (side == 1) { x = nx - 1; y = a; xi = nx - 2; yi = a; q = 3; }
+        else if (side == 2) { x = a; y = 0; xi = a; yi = 1; q = 2; }
+        else { x = a; y = ny - 1; xi = a; yi = ny - 2; q = 4; }
+        o->gn[q * N + idx(o, x, y)] = o->gn[q * N + idx(o, xi, yi)];
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Two-phase step (Liang et al. model as written in Sec. 2.3)                */
+/* ------------------------------------------------------------------------- */
+static void moments_two_phase(orc_t *o, double *gx, double *gy, double *lap) {
+  const orc_params *p = &o->p;
+  int N = o->N, nx = p->nx, ny = p->ny;
+  /* phi = sum h_i, Eq. zero_moment_h */
+  for (int n = 0; n < N; n++) {
+    double s = 0;
+    for (int i = 0; i < 5; i++) s += o->h[i * N + n];
+    o->phi[n] = s;
+  }
+  /* isotropic gradient and Laplacian with D2Q9 weights, Eqs. gradient and
+     laplacian (reading R23); periodic neighbours */
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      int n = idx(o, x, y);
+      double sx = 0, sy = 0, sl = 0;
+      for (int i = 1; i < 9; i++) {
+        int tx = (x + CX9[i] + nx) % nx, ty = (y + CY9[i] + ny) % ny;
+        double pn = o->phi[idx(o, tx, ty)];
+        sx += W9[i] * o->c * CX9[i] * pn;
+        sy += W9[i] * o->c * CY9[i] * pn;
+        sl += 2.0 * W9[i] * (pn - o->phi[n]);
+      }
+      gx[n] = sx / (o->cs2 * p->dt);
+      gy[n] = sy / (o->cs2 * p->dt);
+      lap[n] = sl / (o->cs2 * p->dt * p->dt);
+    }
+}
+
+static void step_two_phase(orc_t *o) {
+  const orc_params *p = &o->p;
+  int N = o->N, nx = p->nx, ny = p->ny;
+  double dt = p->dt, cs2 = o->cs2;
+  double *gx = malloc(sizeof(double) * N), *gy = malloc(sizeof(double) * N);
+  double *lap = malloc(sizeof(double) * N);
+  moments_two_phase(o, gx, gy, lap);
+  double kappa = 1.5 * p->sigma * p->W;   /* kappa = 3 sigma W / 2 */
+  double beta = 12.0 * p->sigma / p->W;   /* beta = 12 sigma / W  */
+  double tphi = o->tauphi;
+#pragma omp parallel for schedule(static)
+  for (int n = 0; n < N; n++) {
+    double phi = o->phi[n];
+    /* chemical potential, Eq. chemical_potential */
+    double mu = 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) - kappa * lap[n];
+    /* normal, guarded where |grad phi| = 0 */
+    double gnorm = sqrt(gx[n] * gx[n] + gy[n] * gy[n]);
+    double nxv = 0.0, nyv = 0.0;
+    if (gnorm != 0.0) { nxv = gx[n] / gnorm; nyv = gy[n] / gnorm; }
+    /* rho and nu linear in phi; grad rho = (rho_l - rho_g) grad phi */
+    double rho = p->rho_g + phi * (p->rho_l - p->rho_g);
+    double nu;
+    if (p->nu_rule == 0) nu = p->nu_g + phi * (p->nu_l - p->nu_g);
+    else {
+      double zeta = p->rho_g * p->nu_g + phi * (p->rho_l * p->nu_l - p->rho_g * p->nu_g);
+      nu = zeta / rho;
+    }
+    double tau = nu / cs2 + 0.5 * dt;
+    double drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
+    double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
+    double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+    /* u from Eq. u_Liang, then p from Eq. p_Liang */
+    double jx = 0, jy = 0, zs = 0;
+    for (int i = 0; i < 9; i++) {
+      double zi = o->z[i * N + n];
+      jx += o->c * CX9[i] * zi;
+      jy += o->c * CY9[i] * zi;
+      if (i >= 1) zs += zi;
+    }
+    double ux = (jx + 0.5 * dt * Fx) / rho;
+    double uy = (jy + 0.5 * dt * Fy) / rho;
+    double pr = cs2 / (1.0 - W9[0]) * (zs + 0.5 * dt * (ux * drx + uy * dry) + rho * s9(o, 0, ux, uy));
+    o->rho[n] = rho; o->ux[n] = ux; o->uy[n] = uy; o->pr[n] = pr;
+    /* d_t(phi u) by explicit Euler against the stored previous value */
+    double dtpux = (phi * ux - o->phiux_prev[n]) / dt;
+    double dtpuy = (phi * uy - o->phiuy_prev[n]) / dt;
+    /* h collision (BGK), Eqs. eq_lattice_boltzmann_interface, heq_liang, source_term_interface */
+    double ax = dtpux + cs2 * 4.0 * phi * (1.0 - phi) / p->W * nxv;
+    double ay = dtpuy + cs2 * 4.0 * phi * (1.0 - phi) / p->W * nyv;
+    for (int i = 0; i < 5; i++) {
+      double cx = o->c * CX5[i], cy = o->c * CY5[i];
+      double heq = phi * W5[i] * (1.0 + (cx * ux + cy * uy) / cs2);
+      double Sh = (1.0 - dt / (2.0 * tphi)) * W5[i] * (cx * ax + cy * ay) / cs2;
+      double hi = o->h[i * N + n];
+      o->hpost[i * N + n] = hi - dt / tphi * (hi - heq) + dt * Sh;
+    }
+    /* z collision: equilibrium Eq. zeq_liang, forcing Eq. forcing_term_pressure_evolution */
+    double zv[9], ze[9], zf[9];
+    for (int i = 0; i < 9; i++) {
+      double cx = o->c * CX9[i], cy = o->c * CY9[i];
+      zv[i] = o->z[i * N + n];
+      ze[i] = (i == 0 ? pr / cs2 * (W9[0] - 1.0) : pr / cs2 * W9[i]) + rho * s9(o, i, ux, uy);
+      double cu = cx * ux + cy * uy, cdr = cx * drx + cy * dry;
+      zf[i] = W9[i] * ((cx * Fx + cy * Fy) / cs2 + cu * cdr / cs2);
+    }
+    if (p->z_op == 0) {
+      for (int i = 0; i < 9; i++)
+        o->zpost[i * N + n] = zv[i] - dt / tau * (zv[i] - ze[i]) + dt * (1.0 - dt / (2.0 * tau)) * zf[i];
+    } else {
+      /* MRT with the multiphase [Lambda]_dim of Sec. 3; q_y uses omega_q2 like q_x
+         (reading R2), literal flag relaxes q_y at 1/dt as printed */
+      double wnu = 1.0 / tau;
+      double wq2 = (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu);
+      double Lam[9] = {1.0 / dt, 1.0 / dt, 1.0 / dt, 1.0 / dt, wq2, 1.0 / dt,
+                       (p->literal & 2) ? 1.0 / dt : wq2, wnu, wnu};
+      double m[9], me[9], Fm[9], ms[9], zs2[9];
+      matvec(9, o->Md, zv, m);
+      matvec(9, o->Md, ze, me);
+      matvec(9, o->Md, zf, Fm);
+      for (int k = 0; k < 9; k++)
+        ms[k] = m[k] - dt * Lam[k] * (m[k] - me[k]) + dt * (1.0 - 0.5 * dt * Lam[k]) * Fm[k];
+      matvec(9, o->Mdinv, ms, zs2);
+      for (int i = 0; i < 9; i++) o->zpost[i * N + n] = zs2[i];
+    }
+    o->phiux_prev[n] = phi * ux;
+    o->phiuy_prev[n] = phi * uy;
+  }
+  /* push streaming, periodic in both directions */
+  for (int y = 0; y < ny; y++)
+    for (int x = 0; x < nx; x++) {
+      int n = idx(o, x, y);
+      for (int i = 0; i < 5; i++) {
+        int tx = (x + CX5[i] + nx) % nx, ty = (y + CY5[i] + ny) % ny;
+        o->hn[i * N + idx(o, tx, ty)] = o->hpost[i * N + n];
+      }
+      for (int i = 0; i < 9; i++) {
+        int tx = (x + CX9[i] + nx) % nx, ty = (y + CY9[i] + ny) % ny;
+        o->zn[i * N + idx(o, tx, ty)] = o->zpost[i * N + n];
+      }
+    }
+  double *t;
+  t = o->h; o->h = o->hn; o->hn = t;
+  t = o->z; o->z = o->zn; o->zn = t;
+  free(gx); free(gy); free(lap);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Initialisation at equilibrium (reading R21) and stepping                  */
+/* ------------------------------------------------------------------------- */
+/* Fields (NULL = defaults): a = rho (single phase) or phi (two-phase);
+   ux, uy; b = T (thermal) or p (two-phase).  Defaults: rho0, 0, 0, T0, 0. */
+void orc_init(void *handle, const double *a, const double *ux, const double *uy, const double *b) {
+  orc_t *o = (orc_t *)handle;
+  const orc_params *p = &o->p;
+  int N = o->N;
+  for (int n = 0; n < N; n++) {
+    double u0 = ux ? ux[n] : (p->flow ? 0.0 : p->u_prescribed[0]);
+    double v0 = uy ? uy[n] : (p->flow ? 0.0 : p->u_prescribed[1]);
+    o->ux[n] = u0; o->uy[n] = v0;
+    if (p->phase) {
+      double phi = a ? a[n] : 1.0;
+      double pr = b ? b[n] : 0.0;
+      double rho = p->rho_g + phi * (p->rho_l - p->rho_g);
+      for (int i = 0; i < 5; i++) {
+        double cu = o->c * (CX5[i] * u0 + CY5[i] * v0);
+        o->h[i * N + n] = phi * W5[i] * (1.0 + cu / o->cs2);
+      }
+      for (int i = 0; i < 9; i++)
+        o->z[i * N + n] = (i == 0 ? pr / o->cs2 * (W9[0] - 1.0) : pr / o->cs2 * W9[i]) + rho * s9(o, i, u0, v0);
+      o->phiux_prev[n] = phi * u0;
+      o->phiuy_prev[n] = phi * v0;
+      o->phi[n] = phi; o->rho[n] = rho; o->pr[n] = pr;
+      continue;
+    }
+    double rho = a ? a[n] : p->rho0;
+    o->rho[n] = rho;
+    if (p->flow)
+      for (int i = 0; i < 9; i++) o->f[i * N + n] = feq9(o, i, rho, u0, v0);
+    if (p->thermal) {
+      double T = b ? b[n] : p->T0;
+      o->T[n] = T; o->Tprev[n] = T;
+      for (int i = 0; i < 5; i++) o->g[i * N + n] = geq5(o, i, T, u0, v0);
+    }
+  }
+  o->steps = 0;
+}
+
+void orc_step(void *handle, long nsteps) {
+  orc_t *o = (orc_t *)handle;
+  for (long s = 0; s < nsteps; s++) {
+    if (o->p.phase) {
+      step_two_phase(o);
+    } else {
+      moments_single(o);
+      collide_single(o);
+      stream_single(o);
+      double *t;
+      t = o->f; o->f = o->fn; o->fn = t;
+      t = o->g; o->g = o->gn; o->gn = t;
+      if (o->p.thermal && o->p.conv_coef != 0.0) memcpy(o->Tprev, o->T, sizeof(double) * o->N);
+    }
+    o->steps++;
+  }
+}
+
+/* Macroscopic fields of the CURRENT pre-collision state (time t = steps*dt).
+   Any output pointer may be NULL. */
+void orc_moments(void *handle, double *rho, double *ux, double *uy, double *T, double *pr,
+                 double *phi) {
+  orc_t *o = (orc_t *)handle;
+  int N = o->N;
+  if (o->p.phase) {
+    const orc_params *p = &o->p;
+    double *gx = malloc(sizeof(double) * N), *gy = malloc(sizeof(double) * N);
+    double *lap = malloc(sizeof(double) * N);
+    moments_two_phase(o, gx, gy, lap);
+    double kappa = 1.5 * p->sigma * p->W, beta = 12.0 * p->sigma / p->W;
+    for (int n = 0; n < N; n++) {
+      double ph = o->phi[n];
+      double mu = 4.0 * beta * ph * (ph - 1.0) * (ph - 0.5) - kappa * lap[n];
+      double r = p->rho_g + ph * (p->rho_l - p->rho_g);
+      double drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
+      double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
+      double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+      double jx = 0, jy = 0, zs = 0;
+      for (int i = 0; i < 9; i++) {
+        double zi = o->z[i * N + n];
+        jx += o->c * CX9[i] * zi;
+        jy += o->c * CY9[i] * zi;
+        if (i >= 1) zs += zi;
+      }
+      double u = (jx + 0.5 * p->dt * Fx) / r, v = (jy + 0.5 * p->dt * Fy) / r;
+      double pp = o->cs2 / (1.0 - W9[0]) * (zs + 0.5 * p->dt * (u * drx + v * dry) + r * s9(o, 0, u, v));
+      if (rho) rho[n] = r;
+      if (ux) ux[n] = u;
+      if (uy) uy[n] = v;
+      if (pr) pr[n] = pp;
+      if (phi) phi[n] = ph;
+      if (T) T[n] = 0.0;
+    }
+    free(gx); free(gy); free(lap);
+    return;
+  }
+  /* single phase: recompute from the current distributions (the next step
+     recomputes the same values, so overwriting the work arrays is harmless) */
+  moments_single(o);
+  for (int n = 0; n < N; n++) {
+    if (rho) rho[n] = o->p.flow ? o->rho[n] : o->p.rho0;
+    if (ux) ux[n] = o->ux[n];
+    if (uy) uy[n] = o->uy[n];
+    if (T) T[n] = o->p.thermal ? o->T[n] : 0.0;
+    /* single-phase pressure deviation p - p0 = c_s^2 (rho - rho0) */
+    if (pr) pr[n] = o->p.flow ? o->cs2 * (o->rho[n] - o->p.rho0) : 0.0;
+    if (phi) phi[n] = 0.0;
+  }
+}
+
+/* Distributions: which 0 f, 1 g, 2 h, 3 z; post = 0 current pre-collision state,
+   1 post-collision values of the last step (valid after >= 1 step). */
+void orc_get_dist(void *handle, int which, int post, double *out) {
+  orc_t *o = (orc_t *)handle;
+  int q = (which == 0 || which == 3) ? 9 : 5;
+  double *src;
+  if (which == 0) src = post ? o->fpost : o->f;
+  else if (which == 1) src = post ? o->gpost : o->g;
+  else if (which == 2) src = post ? o->hpost : o->h;
+  else src = post ? o->zpost : o->z;
+  memcpy(out, src, sizeof(double) * q * o->N);
+}
+
+/* Overwrite the current pre-collision distributions (for planted-mistake tests). */
+void orc_set_dist(void *handle, int which, const double *in) {
+  orc_t *o = (orc_t *)handle;
+  int q = (which == 0 || which == 3) ? 9 : 5;
+  double *dst = which == 0 ? o->f : which == 1 ? o->g : which == 2 ? o->h : o->z;
+  memcpy(dst, in, sizeof(double) * q * o->N);
+}
+
+long orc_steps(void *handle) { return ((orc_t *)handle)->steps; }
