@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the fused dimensional-LBM step on GB300.
+
+Workload: the forced-convection channel, D2Q9 MRT momentum + D2Q5 MRT thermal,
+2048 x 256 nodes, water, Re = 100, Pr = 7, parabolic inflow, constant wall heat
+flux.  One bench step = one LBM time step of the whole grid (one fused
+pull-stream + boundary + moments + collide launch).
+
+Main line (JSON, rank 0): MLUPS of the FP32-deviation ("mixed") form with the
+state already in HBM; per-step CUDA-event timing on the solver's stream with an
+L2 flush (a read of a 512 MiB buffer) between steps, because the two ping-pong
+buffers (117 MB) would otherwise sit in the 129 MB L2.  Extra keys: the FP64
+form's MLUPS on the same grid, the roofline of the step kernel, the oracle on
+the host cores, and an end-to-end figure through the C ABI with host buffers.
+
+--impl reference: the FP64 CPU oracle (the reference arm of this project) on a
+bounded sample of the same workload on the host cores.
+--gpus N > 1 (torchrun): N independent replicas, one per GPU (replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CELLS_NX, CELLS_NY = 2048, 256
+BYTES_PER_CELL = {0: 224, 1: 112}   # (9 + 5) populations read + written, FP64 / FP32
+WORKLOAD = "channel_d2q9mrt_d2q5mrt_2048x256"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 7 for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def _gpu_run(prec, steps, warmup, stream, torch):
+    """Per-step event timing of the fused step with an L2 flush between steps."""
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    w = wl.channel(nx=CELLS_NX, ny=CELLS_NY, steps=0)
+    s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
+    s.apply_workload(w)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush.fill_(1.0)
+    sink = torch.empty(1, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            s.step(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            sink.copy_(flush.sum())          # evict the state from L2 (read-only pass)
+            ev[k][0].record(stream)
+            s.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    times_ms = [a.elapsed_time(b) for a, b in ev]
+    chk = s.check()
+    s.close()
+    del flush
+    return times_ms, chk
+
+
+def _e2e(prec, steps, warmup, stream, torch):
+    """End to end through the C ABI: every step uploads both walls' heat-flux
+    profiles from pinned host memory (lbm_set_bc), advances one step and reads
+    the integrals (mass, max |u|, health flag) back to the host (lbm_integrals)."""
+    import numpy as np
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    w = wl.channel(nx=CELLS_NX, ny=CELLS_NY, steps=0)
+    s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
+    s.apply_workload(w)
+    qf = torch.empty(CELLS_NX, dtype=torch.float64, pin_memory=True).numpy()
+    qf[:] = w["qflux"]
+    for k in range(warmup):
+        lbm.lbm_set_bc(s.h, 2, lbm.LBM_BC_WALL, None, 1000.0, lbm.LBM_TBC_FLUX, qf)
+        s.step(1)
+        s.integrals()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        lbm.lbm_set_bc(s.h, 2, lbm.LBM_BC_WALL, None, 1000.0, lbm.LBM_TBC_FLUX, qf)
+        lbm.lbm_set_bc(s.h, 3, lbm.LBM_BC_WALL, None, 1000.0, lbm.LBM_TBC_FLUX, qf)
+        s.step(1)
+        s.integrals()
+    el = time.perf_counter() - t0
+    s.close()
+    return el, 2 * qf.nbytes, 4 * 8
+
+
+def _cpu_baseline(budget_s=12.0):
+    """The FP64 oracle as it stands, on the host cores, on a 256-column slice of the
+    same channel (inlet section, all 256 rows), as many steps as fit ~12 s."""
+    import oracle
+    from paper_2302_04120_gb300 import workloads as wl
+    oracle.build()
+    w = wl.channel(nx=256, ny=CELLS_NY, steps=0)
+    o = oracle.Oracle(w["params"])
+    for bc in w["bcs"]:
+        o.set_bc(*bc)
+    o.init(**w["init"])
+    o.step(1)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        o.step(5)
+        n += 5
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=256 * CELLS_NY * n / el / 1e6, unit="MLUPS", cores=cores, kind="oracle",
+                sample=f"channel 256x{CELLS_NY} slice of the 2048x{CELLS_NY} workload, {n} steps, FP64, OpenMP")
+
+
+def _traffic_from_profile(kernel_tag):
+    """Per-launch DRAM bytes recorded from an ncu capture, if the kernel source is
+    unchanged since (profiles/dram_traffic.txt: tag bytes source_hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha1()
+    for f in ("step_sp.cu", "lattice.cuh", "lbm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2302_04120_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    cur = h.hexdigest()[:12]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_tag and parts[2] == cur:
+            return float(parts[1])
+    return None
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2302_04120_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream()
+    cells = CELLS_NX * CELLS_NY
+    # FP64 plain form (same grid), fewer steps: it is ALU-bound on GB300
+    t64, chk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t32, chk32 = _gpu_run(1, args.steps, args.warmup, stream, torch)
+    torch.cuda.synchronize()
+    total_s = sum(t32) / 1e3
+    if ws > 1:
+        tt = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    e2e_s, h2d, d2h = _e2e(1, min(args.steps, 500), args.warmup, stream, torch)
+    e2e_steps = min(args.steps, 500)
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    avg32 = statistics.mean(t32) / 1e3
+    avg64 = statistics.mean(t64) / 1e3
+    ach32 = BYTES_PER_CELL[1] * cells / avg32 / 1e9
+    ach64 = BYTES_PER_CELL[0] * cells / avg64 / 1e9
+    mlups = ws * cells * args.steps / total_s / 1e6
+    line = {
+        "metric": "MLUPS (FP32-deviation mixed form) & % HBM roofline; FP64 plain form beside it",
+        "value": round(mlups, 1),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_s / args.steps * 1e3, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded channel inflow/heat-flux inputs; no dataset)",
+        "config": {"workload": WORKLOAD, "nx": CELLS_NX, "ny": CELLS_NY, "lattice": "D2Q9 MRT + D2Q5 MRT",
+                   "precision": "FP32 deviation storage, FP32 arithmetic",
+                   "l2": "flushed between timed steps (read of a 512 MiB buffer)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(ach32 / peak, 4), "peak_source": peak_kind,
+                     "traffic": _traffic_from_profile("k_step_fp32_mrt_mrt_2048x256"),
+                     "kernel": "k_step<1,FLOW_MRT,TH_MRT>", "algorithmic_bytes_per_launch": BYTES_PER_CELL[1] * cells},
+        "fp64": {"value": round(cells / avg64 / 1e6, 1), "unit": "MLUPS", "steps": len(t64),
+                 "achieved_GBps": round(ach64, 1), "frac": round(ach64 / peak, 4), "dtype": "f64",
+                 "status": int(chk64)},
+        "mixed_over_fp64": round(avg64 / avg32, 2),
+        "e2e": {"value": round(cells * e2e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "api": "lbm_set_bc x2 (pinned host q'') + lbm_step(1) + lbm_integrals (host)"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "status": int(chk32),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: each step = one oracle step of a
+    256 x 256 slice of the workload (bounded so K steps end within minutes)."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2302_04120_gb300 import workloads as wl
+    oracle.build()
+    w = wl.channel(nx=256, ny=CELLS_NY, steps=0)
+    o = oracle.Oracle(w["params"])
+    for bc in w["bcs"]:
+        o.set_bc(*bc)
+    o.init(**w["init"])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    cells = 256 * CELLS_NY
+    mlups = cells * args.steps / el / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference",
+        "metric": "MLUPS (FP32-deviation mixed form) & % HBM roofline; FP64 plain form beside it",
+        "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": CELLS_NX, "ny": CELLS_NY, "sample": "256-column slice"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"channel 256x{CELLS_NY} slice, {args.steps} steps, FP64 OpenMP"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * lbm.h -- C ABI of the GB300 dimensional lattice Boltzmann library.
+ *
+ * Method: Martins, Alvarino & Cabezas-Gomez, "Dimensional lattice Boltzmann
+ * method for transport phenomena simulation without conversion to lattice
+ * units" (arXiv:2302.04120).  The lattice Boltzmann equation is integrated
+ * directly in SI units: dx [m], dt [s], c = dx/dt [m/s], f_i [kg m^-3],
+ * T [K], forces [N m^-3], heat sources [W m^-3], heat fluxes [W m^-2]
+ * (Sec. 3).  Every call below takes and returns SI quantities.
+ *
+ * Conventions
+ *  - Grids are nx columns (x index i) by ny rows (y index j).  Host and device
+ *    field arrays are row-major doubles, element (j, i) at j*nx + i, node
+ *    (i, j) located at ((i+1/2) dx, (j+1/2) dx).  Half-way walls lie on cell
+ *    faces (link-wise boundaries, Sec. 2.1).
+ *  - The caller owns every array it passes; set/init calls copy before they
+ *    return.  The handle owns its device state and frees it in lbm_destroy.
+ *  - All work runs asynchronously on the CUDA stream bound at lbm_create
+ *    (NULL = the legacy default stream).  Calls that write to host memory
+ *    synchronise that stream before returning.
+ *  - Every call returns an lbm_status; lbm_last_error() gives the text of the
+ *    last failure on that handle.  No call aborts the process.
+ *  - Pointer arguments flagged "on_device" are device pointers when the flag is
+ *    non-zero, host pointers otherwise.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_s *lbm_t;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,           /* bad argument, size or combination           */
+  LBM_ERR_UNSTABLE_TAU = -2,  /* a relaxation time tau <= dt/2 (Sec. 4 intro)  */
+  LBM_ERR_NOMEM = -3,         /* device or host allocation failed            */
+  LBM_ERR_CUDA = -4,          /* a CUDA runtime call failed                  */
+  LBM_ERR_DIVERGED = -5,      /* NaN/Inf or |u| >= c found by lbm_check       */
+  LBM_ERR_TIMEOUT = -6,       /* a bounded device wait gave up                */
+  LBM_ERR_STATE = -7          /* call not valid in the handle's current state */
+} lbm_status;
+
+/* lattices */
+enum { LBM_NONE = 0, LBM_D2Q5 = 5, LBM_D2Q9 = 9 };
+/* collision operators */
+enum { LBM_BGK = 0, LBM_MRT = 1 };
+/* storage/arithmetic precision */
+enum {
+  LBM_FP64 = 0,   /* FP64 storage and arithmetic                                      */
+  LBM_FP32DEV = 1 /* FP32 storage of deviations f_i - w_i rho0, g_i - w_i T0; FP32 math */
+};
+/* momentum boundary kinds, per side */
+enum {
+  LBM_BC_PERIODIC = 0, /* Sec. 2.1: f_i(x_b) = f_i*(x_b + L - c_i dt); both sides of an axis */
+  LBM_BC_WALL = 1,     /* half-way bounce-back with wall velocity, Eq. BB_vel               */
+  LBM_BC_VELOCITY = 2, /* velocity inlet, Eq. BB_vel with u_w = inlet velocity              */
+  LBM_BC_PRESSURE = 3  /* outlet, Eq. anti_BB_vel; u_w = u(x_b) + (u(x_b) - u(x_b-1))/2      */
+};
+/* thermal boundary kinds, per side (LBM_TBC_NONE = periodic for the thermal lattice) */
+enum {
+  LBM_TBC_NONE = 0,
+  LBM_TBC_FLUX = 1,    /* prescribed heat flux into the fluid, Eq. BB_T                     */
+  LBM_TBC_TEMP = 2,    /* prescribed temperature, Eq. anti_BB_T                             */
+  LBM_TBC_OUTFLOW = 3  /* first-order extrapolation of the unknown populations (Sec. 2.2)   */
+};
+/* sides */
+enum { LBM_SIDE_XMIN = 0, LBM_SIDE_XMAX = 1, LBM_SIDE_YMIN = 2, LBM_SIDE_YMAX = 3 };
+/* moment selection bits for lbm_moments */
+enum { LBM_RHO = 1, LBM_UX = 2, LBM_UY = 4, LBM_T = 8, LBM_P = 16, LBM_PHI = 32 };
+
+/*
+ * Solver parameters, all SI.
+ *  flow       LBM_D2Q9 (momentum LBE, Sec. 2.1) or LBM_NONE (velocity prescribed
+ *             by u_prescribed; thermal-only problems).
+ *  flow_op    LBM_BGK (Eq. eq_lattice_boltzmann_BGK) or LBM_MRT (Eq. colisao_MRT with
+ *             [M]_dim of Eq. M_matrix_dim and the dimensional rates of Sec. 3:
+ *             omega_nu = 1/tau, omega_q = (3/dt)(2/dt - omega_nu)/(3/dt - omega_nu),
+ *             omega_e = omega_e_dt/dt, omega_eps = omega_eps_dt/dt).
+ *  thermal    LBM_NONE or LBM_D2Q5 (double-distribution thermal LBE, Sec. 2.2, on D2Q5:
+ *             w = 1/3, 1/6 x4, c_s^2 = c^2/3; linear g_eq of Eq. geq_geral).
+ *  thermal_op LBM_BGK (Eq. eq_lattice_boltzmann_BGK_T) or LBM_MRT (D2Q5 analogue of
+ *             [Lambda_T]_dim: moments (1, c_x, c_y, 5|c|^2-4c^2, c_x^2-c_y^2) relaxed at
+ *             (0, 1/tau_T, 1/tau_T, 1/dt, 1/dt)).
+ *  phase      LBM_NONE (single phase) or LBM_D2Q5 (two-phase model of Sec. 2.3: Allen-Cahn
+ *             h_i on D2Q5, pressure-evolution z_i on D2Q9 with operator z_op).
+ *  nu_rule    two-phase viscosity: 0 linear in phi, 1 nu = zeta/rho with zeta linear in phi.
+ *  literal    bit 0: thermal source prefactor with the momentum tau as printed in
+ *             Eq. forcing_term_g (default uses tau_T); bit 1: multiphase q_y moment
+ *             relaxed at 1/dt as printed in Sec. 3 (default uses omega_q2 for q_x and q_y).
+ *  precision  LBM_FP64 or LBM_FP32DEV.
+ *  nx, ny     grid size, each >= 1 (>= 2 along an axis with a pressure/outflow side).
+ *  dx, dt     lattice spacing [m] and time step [s]; c = dx/dt.
+ *  rho0       reference density [kg m^-3] (single phase; storage offset for FP32DEV).
+ *  nu         kinematic viscosity [m^2 s^-1]; tau = nu/c_s^2 + dt/2 (Eq. eq_kinematic_viscosity).
+ *  cp, k      specific heat [J kg^-1 K^-1] and conductivity [W m^-1 K^-1];
+ *             alpha = k/(rho0 cp) = (tau_T - dt/2) c_s^2.
+ *  T0         reference temperature [K] (default initial T; storage offset for FP32DEV).
+ *  rho_l, rho_g, nu_l, nu_g, sigma, W, mobility: two-phase properties (Sec. 2.3);
+ *             kappa = 3 sigma W/2, beta = 12 sigma/W, M = (tau_phi - dt/2) c_s^2.
+ *  omega_e_dt, omega_eps_dt: free MRT rates times dt (paper: between 1 and 2; default 1).
+ *  body_force uniform body force F_b [N m^-3].
+ *  u_prescribed velocity used when flow == LBM_NONE [m s^-1].
+ */
+typedef struct {
+  int flow, flow_op, thermal, thermal_op, phase, z_op, nu_rule, literal, precision;
+  int nx, ny;
+  double dx, dt;
+  double rho0, nu, cp, k, T0;
+  double rho_l, rho_g, nu_l, nu_g, sigma, W, mobility;
+  double omega_e_dt, omega_eps_dt;
+  double body_force[2];
+  double u_prescribed[2];
+} lbm_params;
+
+/* Fill *p with defaults: D2Q9 BGK, no thermal, single phase, FP64, water-like
+   rho0 = 1000, nu = 1e-6, cp = 4180, k = 0.6, T0 = 300, free MRT rates 1/dt. */
+void lbm_params_default(lbm_params *p);
+
+/*
+ * Create a solver.  Validates the parameters (tau, tau_T, tau_phi > dt/2 as required
+ * by Eq. eq_kinematic_viscosity and the stability remark of Sec. 4; sizes; lattice
+ * combinations), derives c, c_s^2 and the relaxation times, allocates the device
+ * state (two ping-pong structure-of-arrays buffers) and leaves it uninitialised until
+ * lbm_init_fields.  All sides start periodic.  stream: a cudaStream_t or NULL.
+ * Errors: LBM_ERR_ARG, LBM_ERR_UNSTABLE_TAU, LBM_ERR_NOMEM, LBM_ERR_CUDA; *out = NULL then.
+ */
+lbm_status lbm_create(const lbm_params *p, void *stream, lbm_t *out);
+
+/*
+ * Boundary of one side (0 x-, 1 x+, 2 y-, 3 y+), both lattices at once.
+ *  kind  momentum rule (LBM_BC_*); rho_w the boundary density of Eqs. BB_vel/anti_BB_vel.
+ *  uw    host array of 2*len doubles (u_x[len] then u_y[len]), len = ny for x-sides and
+ *        nx for y-sides: wall/inlet velocity at each boundary node, also used by the
+ *        thermal anti-bounce-back; NULL = zero.
+ *  tkind thermal rule (LBM_TBC_*); tw host array of len doubles: q'' [W m^-2, positive
+ *        into the fluid] for FLUX, T_w [K] for TEMP, ignored otherwise; NULL = zero.
+ * Both sides of an axis must be periodic together, for each lattice.  A link that
+ * leaves through a corner takes the y-side rule.
+ * Errors: LBM_ERR_ARG (side, kind, pairing), LBM_ERR_CUDA.
+ */
+lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, double rho_w, int tkind,
+                      const double *tw);
+
+/*
+ * Per-cell sources.  q3: nx*ny volumetric heat generation q''' [W m^-3]; the thermal
+ * source is qdot = q'''/(rho0 cp) [K s^-1] (Eqs. forcing_term_g, zero_moment_g).
+ * force: 2*nx*ny doubles (F_x plane then F_y plane) [N m^-3], added to body_force
+ * (Eqs. forcing_term, first_moment_f).  NULL removes the field.  on_device: pointers
+ * are device pointers.  Errors: LBM_ERR_ARG, LBM_ERR_NOMEM, LBM_ERR_CUDA.
+ */
+lbm_status lbm_set_source(lbm_t h, const double *q3, const double *force, int on_device);
+
+/*
+ * Initialise every distribution at its equilibrium (Eqs. feq_geral, geq_geral,
+ * heq_liang, zeq_liang) from nx*ny fields; NULL takes the default.
+ *  single phase: a = rho (default rho0), ux, uy (default 0), b = T (default T0);
+ *  two-phase:    a = phi (default 1), ux, uy, b = p (default 0); (phi u)_prev = phi u.
+ * The first step then collides this state (the pull kernel stores post-collision
+ * values, so the initial collision is folded into this call).
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA.
+ */
+lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux, const double *uy,
+                           const double *b, int on_device);
+
+/*
+ * Advance n >= 0 time steps: fused pull-stream + boundary links + moments + collision
+ * (Eqs. eq_lattice_boltzmann_geral, colisao_MRT, ...), one kernel launch per step
+ * for single-phase solves and two for two-phase solves, asynchronous on the stream.
+ * Errors: LBM_ERR_STATE (not initialised), LBM_ERR_CUDA.
+ */
+lbm_status lbm_step(lbm_t h, long n);
+
+/* Steps taken since lbm_init_fields (time = steps * dt). */
+long lbm_steps_done(lbm_t h);
+
+/*
+ * Macroscopic fields at the current time (pulled from the stored post-collision
+ * populations, so they include the boundary rules):
+ *  LBM_RHO rho (Eq. zero_moment_f, or rho(phi)), LBM_UX / LBM_UY velocity
+ *  (Eq. first_moment_f or Eq. u_Liang), LBM_T temperature (Eq. zero_moment_g),
+ *  LBM_P pressure (two-phase: Eq. p_Liang; single phase: c_s^2 (rho - rho0)),
+ *  LBM_PHI order parameter (Eq. zero_moment_h).
+ * out receives one nx*ny row-major plane per selected bit, in bit order.
+ * Host output synchronises the stream.  Errors: LBM_ERR_ARG, LBM_ERR_STATE, LBM_ERR_CUDA.
+ */
+lbm_status lbm_moments(lbm_t h, unsigned mask, double *out, int on_device);
+
+/*
+ * Integrals with deterministic FP64 reductions (fixed tree order):
+ *  out[0] = sum rho dx^2 (mass per unit depth, kg/m), out[1] = sum phi (two-phase,
+ *  else 0), out[2] = max |u| [m/s], out[3] = number of cells with a non-finite value
+ *  or |u| >= c.  out is host memory of 4 doubles; the call synchronises the stream.
+ * Errors: LBM_ERR_STATE, LBM_ERR_CUDA.
+ */
+lbm_status lbm_integrals(lbm_t h, double out[4]);
+
+/* lbm_integrals + status: LBM_ERR_DIVERGED when out[3] > 0. */
+lbm_status lbm_check(lbm_t h);
+
+/*
+ * Raw state for checkpoint/restart: the current post-collision buffer, the step
+ * counter excluded.  lbm_state_bytes gives the size; get copies device -> host,
+ * set copies host -> device.  Layout: planes of ny*nx values (no padding) in the
+ * order f_0..8, g_0..4 (single phase) or z_0..8, h_0..4, (phi u)_x, (phi u)_y
+ * (two-phase); FP32DEV stores deviations f_i - w_i rho0 and g_i - w_i T0 as float.
+ * Errors: LBM_ERR_ARG (size), LBM_ERR_STATE, LBM_ERR_CUDA.
+ */
+size_t lbm_state_bytes(lbm_t h);
+lbm_status lbm_get_state(lbm_t h, void *dst, size_t bytes);
+lbm_status lbm_set_state(lbm_t h, const void *src, size_t bytes);
+
+/* Derived constants: out[0] c, [1] c_s^2, [2] tau, [3] tau_T, [4] tau_phi (seconds). */
+lbm_status lbm_constants(lbm_t h, double out[5]);
+
+/* Wait for all work on the handle's stream. */
+lbm_status lbm_synchronize(lbm_t h);
+
+/* Text of the last error on h (or of the last failed lbm_create when h is NULL). */
+const char *lbm_last_error(lbm_t h);
+
+/* Free the device state.  NULL is ignored. */
+void lbm_destroy(lbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

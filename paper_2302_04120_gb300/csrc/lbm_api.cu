@@ -1,0 +1,525 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation,
+// derived constants (Sec. 3 of the paper), device buffer ownership, boundary
+// upload, launches and status reporting.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+#include "lbm_mp.cuh"
+
+using lbmk::SpParams;
+
+struct lbm_s {
+  lbm_params p;
+  cudaStream_t stream;
+  // derived SI constants
+  double c, cs2, tau, tauT, tauphi;
+  int pitch;
+  long long plane;
+  int nq;          // planes in one state buffer
+  size_t elem;     // bytes per stored value
+  void *buf[2];    // ping-pong post-collision buffers
+  int cur;         // index of the buffer holding the latest state
+  int pre;         // 1: buf[cur] holds the pre-collision state f(t) itself (after init)
+  int initialised;
+  long steps;
+  // boundaries
+  int bc[4], tbc[4];
+  double rho_w[4];
+  double *d_uw[4], *d_tw[4];
+  // sources (storage precision, pitched)
+  void *d_qdot, *d_force;
+  // two-phase work arrays
+  void *d_phi;     // order parameter plane (storage precision)
+  // reductions
+  double *d_partials;
+  int max_blocks;
+  double *d_out4;
+  double *h_out4;  // pinned
+  dim3 block;
+  char err[512];
+};
+
+static char g_create_err[512];
+
+static lbm_status fail(lbm_t h, lbm_status st, const char *fmt, ...) {
+  char *dst = h ? h->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CU(h, call)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(h, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" void lbm_params_default(lbm_params *p) {
+  memset(p, 0, sizeof(*p));
+  p->flow = LBM_D2Q9;
+  p->flow_op = LBM_BGK;
+  p->thermal = LBM_NONE;
+  p->thermal_op = LBM_BGK;
+  p->phase = LBM_NONE;
+  p->z_op = LBM_MRT;
+  p->precision = LBM_FP64;
+  p->nx = p->ny = 1;
+  p->dx = 1.0;
+  p->dt = 1.0;
+  p->rho0 = 1000.0;
+  p->nu = 1e-6;
+  p->cp = 4180.0;
+  p->k = 0.6;
+  p->T0 = 300.0;
+  p->W = 1.0;
+  p->omega_e_dt = 1.0;
+  p->omega_eps_dt = 1.0;
+}
+
+static int two_phase(const lbm_t h) { return h->p.phase != LBM_NONE; }
+
+static int axis_periodic(const lbm_t h, int axis, int thermal) {
+  int a = axis == 0 ? 0 : 2, b = a + 1;
+  if (thermal) return h->tbc[a] == LBM_TBC_NONE && h->tbc[b] == LBM_TBC_NONE;
+  return h->bc[a] == LBM_BC_PERIODIC && h->bc[b] == LBM_BC_PERIODIC;
+}
+
+static SpParams sp_params(const lbm_t h, int from_buf) {
+  SpParams P;
+  memset(&P, 0, sizeof(P));
+  const lbm_params &p = h->p;
+  P.nx = p.nx; P.ny = p.ny; P.pitch = h->pitch; P.plane = h->plane;
+  P.xper = axis_periodic(h, 0, 0); P.yper = axis_periodic(h, 1, 0);
+  P.txper = axis_periodic(h, 0, 1); P.typer = axis_periodic(h, 1, 1);
+  P.gbase = p.flow == LBM_D2Q9 ? 9 : 0;
+  for (int s = 0; s < 4; s++) {
+    P.side[s].kind = h->bc[s];
+    P.side[s].tkind = h->tbc[s];
+    P.side[s].rho_w = h->rho_w[s];
+    P.side[s].uw = h->d_uw[s];
+    P.side[s].tw = h->d_tw[s];
+  }
+  P.c = h->c; P.cs2 = h->cs2; P.dt = p.dt; P.dx = p.dx;
+  P.rho0 = p.rho0; P.T0 = p.T0;
+  P.Fx = p.body_force[0]; P.Fy = p.body_force[1];
+  P.ux_pres = p.u_prescribed[0]; P.uy_pres = p.u_prescribed[1];
+  P.omega = p.dt / h->tau;
+  // dimensional MRT rates (Sec. 3) times dt
+  const double wnu = 1.0 / h->tau;
+  const double wq = (3.0 / p.dt) * (2.0 / p.dt - wnu) / (3.0 / p.dt - wnu);
+  P.s_e = p.omega_e_dt; P.s_eps = p.omega_eps_dt; P.s_q = wq * p.dt; P.s_nu = wnu * p.dt;
+  if (p.thermal) {
+    P.omegaT = p.dt / h->tauT;
+    const double tau_sg = (p.literal & 1) ? h->tau : h->tauT;  // reading R1
+    P.tsrc_fac = 1.0 - p.dt / (2.0 * tau_sg);
+    P.flux_coef = p.dt / (p.dx * p.rho0 * p.cp);
+  }
+  P.qdot = h->d_qdot;
+  P.force = h->d_force;
+  P.local = h->pre;
+  P.src = h->buf[from_buf];
+  P.dst = h->buf[1 - from_buf];
+  return P;
+}
+
+static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {
+  lbmk::MpParams P;
+  memset(&P, 0, sizeof(P));
+  const lbm_params &p = h->p;
+  P.nx = p.nx; P.ny = p.ny; P.pitch = h->pitch; P.plane = h->plane;
+  P.c = h->c; P.cs2 = h->cs2; P.dt = p.dt; P.dx = p.dx;
+  P.rho_l = p.rho_l; P.rho_g = p.rho_g; P.nu_l = p.nu_l; P.nu_g = p.nu_g;
+  P.kappa = 1.5 * p.sigma * p.W;   // kappa = 3 sigma W / 2
+  P.beta = 12.0 * p.sigma / p.W;   // beta = 12 sigma / W
+  P.W = p.W;
+  P.tauphi = h->tauphi;
+  P.nu_rule = p.nu_rule;
+  P.z_mrt = p.z_op == LBM_MRT;
+  P.qy_literal = (p.literal & 2) ? 1 : 0;
+  P.Fx = p.body_force[0]; P.Fy = p.body_force[1];
+  P.force = h->d_force;
+  P.local = h->pre;
+  P.src = h->buf[from_buf];
+  P.dst = h->buf[1 - from_buf];
+  P.phi = h->d_phi;
+  return P;
+}
+
+extern "C" const char *lbm_last_error(lbm_t h) { return h ? h->err : g_create_err; }
+
+extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out) {
+  if (!out) return fail(NULL, LBM_ERR_ARG, "out is NULL");
+  *out = NULL;
+  if (!pin) return fail(NULL, LBM_ERR_ARG, "params is NULL");
+  const lbm_params p = *pin;
+  if (p.nx < 1 || p.ny < 1) return fail(NULL, LBM_ERR_ARG, "nx, ny must be >= 1 (got %d, %d)", p.nx, p.ny);
+  if ((long long)p.nx * p.ny > (1ll << 31)) return fail(NULL, LBM_ERR_ARG, "grid too large");
+  if (!(p.dx > 0) || !(p.dt > 0)) return fail(NULL, LBM_ERR_ARG, "dx and dt must be positive");
+  if (p.precision != LBM_FP64 && p.precision != LBM_FP32DEV) return fail(NULL, LBM_ERR_ARG, "precision");
+  if (p.flow != LBM_D2Q9 && p.flow != LBM_NONE) return fail(NULL, LBM_ERR_ARG, "flow lattice must be D2Q9 or NONE");
+  if (p.thermal != LBM_D2Q5 && p.thermal != LBM_NONE) return fail(NULL, LBM_ERR_ARG, "thermal lattice must be D2Q5 or NONE");
+  if (p.phase != LBM_D2Q5 && p.phase != LBM_NONE) return fail(NULL, LBM_ERR_ARG, "phase lattice must be D2Q5 or NONE");
+  if (p.flow_op != LBM_BGK && p.flow_op != LBM_MRT) return fail(NULL, LBM_ERR_ARG, "flow_op");
+  if (p.thermal_op != LBM_BGK && p.thermal_op != LBM_MRT) return fail(NULL, LBM_ERR_ARG, "thermal_op");
+  if (p.flow == LBM_NONE && p.thermal == LBM_NONE) return fail(NULL, LBM_ERR_ARG, "nothing to solve");
+  if (p.phase != LBM_NONE) {
+    if (p.flow != LBM_D2Q9 || p.thermal != LBM_NONE)
+      return fail(NULL, LBM_ERR_ARG, "two-phase solves need flow = D2Q9 (z_i) and no thermal LBE");
+    if (!(p.rho_l > 0) || !(p.rho_g > 0) || !(p.nu_l > 0) || !(p.nu_g > 0) || !(p.W > 0) || !(p.mobility > 0) ||
+        !(p.sigma >= 0))
+      return fail(NULL, LBM_ERR_ARG, "two-phase properties rho_l, rho_g, nu_l, nu_g, W, mobility must be positive");
+  } else if (!(p.rho0 > 0)) {
+    return fail(NULL, LBM_ERR_ARG, "rho0 must be positive");
+  }
+  if (!(p.omega_e_dt > 0 && p.omega_e_dt < 2) || !(p.omega_eps_dt > 0 && p.omega_eps_dt < 2))
+    return fail(NULL, LBM_ERR_ARG, "free MRT rates times dt must lie in (0, 2)");
+
+  lbm_t h = (lbm_t)calloc(1, sizeof(struct lbm_s));
+  if (!h) return fail(NULL, LBM_ERR_NOMEM, "host allocation failed");
+  h->p = p;
+  h->stream = (cudaStream_t)stream;
+  h->c = p.dx / p.dt;                   // c = dx/dt (Sec. 2.1)
+  h->cs2 = h->c * h->c / 3.0;           // c_s = c/sqrt(3)
+  const double eps = 1e-12 * p.dt;
+  if (p.flow == LBM_D2Q9 && p.phase == LBM_NONE) {
+    if (!(p.nu > 0)) { free(h); return fail(NULL, LBM_ERR_UNSTABLE_TAU, "nu must be positive (tau > dt/2)"); }
+    h->tau = p.nu / h->cs2 + 0.5 * p.dt;  // Eq. eq_kinematic_viscosity
+    if (!(h->tau > 0.5 * p.dt + eps)) { free(h); return fail(NULL, LBM_ERR_UNSTABLE_TAU, "tau <= dt/2"); }
+  } else {
+    h->tau = 1.0;
+  }
+  if (p.thermal) {
+    if (!(p.k > 0) || !(p.cp > 0)) { free(h); return fail(NULL, LBM_ERR_UNSTABLE_TAU, "k and cp must be positive (tau_T > dt/2)"); }
+    h->tauT = (p.k / (p.rho0 * p.cp)) / h->cs2 + 0.5 * p.dt;
+  }
+  if (p.phase) {
+    h->tauphi = p.mobility / h->cs2 + 0.5 * p.dt;  // M = (tau_phi - dt/2) c_s^2
+    h->tau = p.nu_l / h->cs2 + 0.5 * p.dt;         // liquid tau, reported only
+  }
+  // storage layout: pitch rounded to 32 elements (128 B FP32 / 256 B FP64 rows)
+  h->elem = p.precision == LBM_FP64 ? 8 : 4;
+  h->pitch = (p.nx + 31) / 32 * 32;
+  h->plane = (long long)h->pitch * p.ny;
+  if (p.phase) h->nq = 9 + 5 + 2;   // z, h, (phi u)_prev
+  else h->nq = (p.flow ? 9 : 0) + (p.thermal ? 5 : 0);
+  h->block = dim3(64, 4);
+  for (int s = 0; s < 4; s++) {
+    h->bc[s] = LBM_BC_PERIODIC;
+    h->tbc[s] = LBM_TBC_NONE;
+    h->rho_w[s] = p.phase ? p.rho_l : p.rho0;
+  }
+  size_t bytes = (size_t)h->nq * h->plane * h->elem;
+  cudaError_t e;
+  for (int b = 0; b < 2; b++) {
+    e = cudaMalloc(&h->buf[b], bytes);
+    if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc state (%zu B): %s", bytes, cudaGetErrorString(e)); }
+    cudaMemsetAsync(h->buf[b], 0, bytes, h->stream);
+  }
+  for (int s = 0; s < 4; s++) {
+    int len = s < 2 ? p.ny : p.nx;
+    e = cudaMalloc(&h->d_uw[s], sizeof(double) * 2 * len);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_tw[s], sizeof(double) * len);
+    if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc boundary arrays"); }
+    cudaMemsetAsync(h->d_uw[s], 0, sizeof(double) * 2 * len, h->stream);
+    cudaMemsetAsync(h->d_tw[s], 0, sizeof(double) * len, h->stream);
+  }
+  if (p.phase) {
+    e = cudaMalloc(&h->d_phi, (size_t)h->plane * h->elem);
+    if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc phi"); }
+    cudaMemsetAsync(h->d_phi, 0, (size_t)h->plane * h->elem, h->stream);
+  }
+  h->max_blocks = lbmk::sp_integral_blocks(p.nx, p.ny);
+  int mpb = lbmk::mp_integral_blocks(p.nx, p.ny);
+  if (mpb > h->max_blocks) h->max_blocks = mpb;
+  e = cudaMalloc(&h->d_partials, sizeof(double) * 4 * h->max_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_out4, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_out4, sizeof(double) * 4);
+  if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc reduction scratch"); }
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_CUDA, "create: %s", cudaGetErrorString(e)); }
+  *out = h;
+  h->err[0] = 0;
+  // advisory: lattice Mach number of the prescribed velocity (not an error)
+  return LBM_OK;
+}
+
+extern "C" void lbm_destroy(lbm_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (int b = 0; b < 2; b++) cudaFree(h->buf[b]);
+  for (int s = 0; s < 4; s++) { cudaFree(h->d_uw[s]); cudaFree(h->d_tw[s]); }
+  cudaFree(h->d_qdot);
+  cudaFree(h->d_force);
+  cudaFree(h->d_phi);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_out4);
+  if (h->h_out4) cudaFreeHost(h->h_out4);
+  free(h);
+}
+
+extern "C" lbm_status lbm_constants(lbm_t h, double out[5]) {
+  if (!h || !out) return fail(h, LBM_ERR_ARG, "NULL argument");
+  out[0] = h->c; out[1] = h->cs2; out[2] = h->tau; out[3] = h->tauT; out[4] = h->tauphi;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, double rho_w, int tkind,
+                                 const double *tw) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  if (side < 0 || side > 3) return fail(h, LBM_ERR_ARG, "side must be 0..3");
+  if (kind < LBM_BC_PERIODIC || kind > LBM_BC_PRESSURE) return fail(h, LBM_ERR_ARG, "kind");
+  if (tkind < LBM_TBC_NONE || tkind > LBM_TBC_OUTFLOW) return fail(h, LBM_ERR_ARG, "tkind");
+  if (two_phase(h) && (kind != LBM_BC_PERIODIC || tkind != LBM_TBC_NONE))
+    return fail(h, LBM_ERR_ARG, "two-phase solves support periodic sides only");
+  const int len = side < 2 ? h->p.ny : h->p.nx;
+  const int normal_len = side < 2 ? h->p.nx : h->p.ny;
+  if ((kind == LBM_BC_PRESSURE || tkind == LBM_TBC_OUTFLOW) && normal_len < 2)
+    return fail(h, LBM_ERR_ARG, "pressure/outflow sides need at least 2 nodes along the normal");
+  if (!(rho_w > 0) && kind != LBM_BC_PERIODIC) return fail(h, LBM_ERR_ARG, "rho_w must be positive");
+  h->bc[side] = kind;
+  h->tbc[side] = tkind;
+  h->rho_w[side] = rho_w > 0 ? rho_w : h->p.rho0;
+  if (uw) CU(h, cudaMemcpyAsync(h->d_uw[side], uw, sizeof(double) * 2 * len, cudaMemcpyHostToDevice, h->stream));
+  else CU(h, cudaMemsetAsync(h->d_uw[side], 0, sizeof(double) * 2 * len, h->stream));
+  if (tw) CU(h, cudaMemcpyAsync(h->d_tw[side], tw, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
+  else CU(h, cudaMemsetAsync(h->d_tw[side], 0, sizeof(double) * len, h->stream));
+  // host arrays may be reused by the caller after return
+  CU(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+// Copy an nx*ny*nplanes double field (host or device) into a pitched storage array.
+static lbm_status upload_field(lbm_t h, const double *src, int nplanes, int on_device, void **dst, double scale) {
+  const size_t n = (size_t)h->p.nx * h->p.ny * nplanes;
+  if (!*dst) {
+    cudaError_t e = cudaMalloc(dst, (size_t)nplanes * h->plane * h->elem);
+    if (e != cudaSuccess) return fail(h, LBM_ERR_NOMEM, "cudaMalloc source field");
+    CU(h, cudaMemsetAsync(*dst, 0, (size_t)nplanes * h->plane * h->elem, h->stream));
+  }
+  const double *dsrc = src;
+  double *tmp = NULL;
+  if (!on_device) {
+    CU(h, cudaMalloc(&tmp, n * sizeof(double)));
+    CU(h, cudaMemcpyAsync(tmp, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    dsrc = tmp;
+  }
+  cudaError_t e = lbmk::to_storage(dsrc, *dst, h->p.nx, h->p.ny, h->pitch, nplanes, h->plane, h->p.precision, scale, h->stream);
+  if (tmp) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+  }
+  if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "to_storage: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_source(lbm_t h, const double *q3, const double *force, int on_device) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  lbm_status st;
+  if (q3) {
+    if (!h->p.thermal) return fail(h, LBM_ERR_ARG, "heat source needs a thermal LBE");
+    // qdot = q'''/(rho c_p) in K/s (Sec. 2.2)
+    st = upload_field(h, q3, 1, on_device, &h->d_qdot, 1.0 / (h->p.rho0 * h->p.cp));
+    if (st != LBM_OK) return st;
+  } else if (h->d_qdot) {
+    CU(h, cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_qdot);
+    h->d_qdot = NULL;
+  }
+  if (force) {
+    if (!h->p.flow) return fail(h, LBM_ERR_ARG, "force field needs a momentum LBE");
+    st = upload_field(h, force, 2, on_device, &h->d_force, 1.0);
+    if (st != LBM_OK) return st;
+  } else if (h->d_force) {
+    CU(h, cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_force);
+    h->d_force = NULL;
+  }
+  CU(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux, const double *uy,
+                                      const double *b, int on_device) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  const double *in[4] = {a, ux, uy, b};
+  const double *d_in[4] = {NULL, NULL, NULL, NULL};
+  double *tmp = NULL;
+  if (!on_device) {
+    int cnt = 0;
+    for (int k = 0; k < 4; k++) cnt += in[k] != NULL;
+    if (cnt) {
+      CU(h, cudaMalloc(&tmp, n * sizeof(double) * cnt));
+      int slot = 0;
+      for (int k = 0; k < 4; k++) {
+        if (!in[k]) continue;
+        CU(h, cudaMemcpyAsync(tmp + slot * n, in[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        d_in[k] = tmp + slot * n;
+        slot++;
+      }
+    }
+  } else {
+    for (int k = 0; k < 4; k++) d_in[k] = in[k];
+  }
+  cudaError_t e;
+  h->cur = 1;  // init writes buffer 0 (dst of a launch reading buffer 1)
+  h->pre = 0;
+  if (two_phase(h)) {
+    lbmk::MpParams P = mp_params(h, 1);
+    e = lbmk::mp_init(P, h->p.precision, d_in[0], d_in[1], d_in[2], d_in[3], h->stream);
+  } else {
+    SpParams P = sp_params(h, 1);
+    int flow = h->p.flow ? (h->p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
+    int th = h->p.thermal ? (h->p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
+    e = lbmk::sp_init(P, h->p.precision, flow, th, d_in[0], d_in[1], d_in[2], d_in[3], h->block, h->stream);
+  }
+  if (tmp) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+  }
+  if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "init launch: %s", cudaGetErrorString(e));
+  h->cur = 0;
+  h->pre = 1;  // buffer 0 holds f(0) itself; the first step collides it in place
+  h->steps = 0;
+  h->initialised = 1;
+  if (!on_device) CU(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+static void sp_kinds(const lbm_t h, int *flow, int *th) {
+  *flow = h->p.flow ? (h->p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
+  *th = h->p.thermal ? (h->p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
+}
+
+extern "C" lbm_status lbm_step(lbm_t h, long n) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
+  if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_init_fields has not been called");
+  int flow, th;
+  sp_kinds(h, &flow, &th);
+  for (long s = 0; s < n; s++) {
+    cudaError_t e;
+    if (two_phase(h)) {
+      lbmk::MpParams P = mp_params(h, h->cur);
+      e = lbmk::mp_step(P, h->p.precision, h->stream);
+    } else {
+      SpParams P = sp_params(h, h->cur);
+      e = lbmk::sp_step(P, h->p.precision, flow, th, h->block, h->stream);
+    }
+    if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    h->cur = 1 - h->cur;
+    h->pre = 0;
+    h->steps++;
+  }
+  return LBM_OK;
+}
+
+extern "C" long lbm_steps_done(lbm_t h) { return h ? h->steps : -1; }
+
+extern "C" lbm_status lbm_moments(lbm_t h, unsigned mask, double *out, int on_device) {
+  if (!h || !out) return fail(h, LBM_ERR_ARG, "NULL argument");
+  if (!h->initialised) return fail(h, LBM_ERR_STATE, "not initialised");
+  if (mask == 0 || mask > 63u) return fail(h, LBM_ERR_ARG, "mask must select 1..6 of RHO|UX|UY|T|P|PHI");
+  int nsel = 0;
+  for (int b = 0; b < 6; b++) nsel += (mask >> b) & 1u;
+  const size_t n = (size_t)h->p.nx * h->p.ny;
+  double *dout = out;
+  if (!on_device) CU(h, cudaMalloc(&dout, n * nsel * sizeof(double)));
+  cudaError_t e;
+  if (two_phase(h)) {
+    lbmk::MpParams P = mp_params(h, h->cur);
+    e = lbmk::mp_moments(P, h->p.precision, mask, dout, h->stream);
+  } else {
+    int flow, th;
+    sp_kinds(h, &flow, &th);
+    SpParams P = sp_params(h, h->cur);
+    e = lbmk::sp_moments(P, h->p.precision, flow, th, mask, dout, h->stream);
+  }
+  if (e != cudaSuccess) {
+    if (!on_device) cudaFree(dout);
+    return fail(h, LBM_ERR_CUDA, "moments launch: %s", cudaGetErrorString(e));
+  }
+  if (!on_device) {
+    cudaError_t e2 = cudaMemcpyAsync(out, dout, n * nsel * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e3 = cudaStreamSynchronize(h->stream);
+    cudaFree(dout);
+    if (e2 != cudaSuccess || e3 != cudaSuccess)
+      return fail(h, LBM_ERR_CUDA, "moments copy: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_integrals(lbm_t h, double out[4]) {
+  if (!h || !out) return fail(h, LBM_ERR_ARG, "NULL argument");
+  if (!h->initialised) return fail(h, LBM_ERR_STATE, "not initialised");
+  cudaError_t e;
+  if (two_phase(h)) {
+    lbmk::MpParams P = mp_params(h, h->cur);
+    e = lbmk::mp_integrals(P, h->p.precision, h->d_partials, h->max_blocks, h->d_out4, h->stream);
+  } else {
+    int flow, th;
+    sp_kinds(h, &flow, &th);
+    SpParams P = sp_params(h, h->cur);
+    e = lbmk::sp_integrals(P, h->p.precision, flow, th, h->d_partials, h->max_blocks, h->d_out4, h->stream);
+  }
+  if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "integrals launch: %s", cudaGetErrorString(e));
+  CU(h, cudaMemcpyAsync(h->h_out4, h->d_out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  memcpy(out, h->h_out4, 4 * sizeof(double));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_check(lbm_t h) {
+  double v[4];
+  lbm_status st = lbm_integrals(h, v);
+  if (st != LBM_OK) return st;
+  if (v[3] > 0) return fail(h, LBM_ERR_DIVERGED, "%.0f cells non-finite or |u| >= c after %ld steps", v[3], h->steps);
+  return LBM_OK;
+}
+
+extern "C" size_t lbm_state_bytes(lbm_t h) {
+  if (!h) return 0;
+  return (size_t)h->nq * h->p.nx * h->p.ny * h->elem;
+}
+
+static lbm_status state_copy(lbm_t h, void *host, size_t bytes, int unpack) {
+  if (!h || !host) return fail(h, LBM_ERR_ARG, "NULL argument");
+  if (bytes != lbm_state_bytes(h)) return fail(h, LBM_ERR_ARG, "state size is %zu bytes", lbm_state_bytes(h));
+  if (!unpack && !h->initialised) return fail(h, LBM_ERR_STATE, "not initialised");
+  if (!unpack && h->pre) return fail(h, LBM_ERR_STATE, "no step taken since lbm_init_fields: no post-collision state yet");
+  void *tmp = NULL;
+  CU(h, cudaMalloc(&tmp, bytes));
+  cudaError_t e = cudaSuccess;
+  if (unpack) {
+    e = cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = lbmk::pack_state(h->buf[h->cur], tmp, h->p.nx, h->p.ny, h->pitch, h->nq, h->plane, (int)h->elem, 1, h->stream);
+  } else {
+    e = lbmk::pack_state(h->buf[h->cur], tmp, h->p.nx, h->p.ny, h->pitch, h->nq, h->plane, (int)h->elem, 0, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(h, LBM_ERR_CUDA, "state copy: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  if (unpack) { h->initialised = 1; h->pre = 0; }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_state(lbm_t h, void *dst, size_t bytes) { return state_copy(h, dst, bytes, 0); }
+extern "C" lbm_status lbm_set_state(lbm_t h, const void *src, size_t bytes) { return state_copy(h, (void *)src, bytes, 1); }
+
+extern "C" lbm_status lbm_synchronize(lbm_t h) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  CU(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}

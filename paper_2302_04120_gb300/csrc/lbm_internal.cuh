@@ -1,0 +1,71 @@
+// Internal declarations shared by the host C-ABI (lbm_api.cu) and the kernels.
+// Not part of the public interface (include/lbm.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+// Boundary description of one side, device pointers.
+struct DevSide {
+  int kind;          // LBM_BC_*
+  int tkind;         // LBM_TBC_*
+  double rho_w;      // boundary density of Eqs. BB_vel / anti_BB_vel
+  const double *uw;  // 2*len: u_x then u_y at each boundary node
+  const double *tw;  // len: q'' (FLUX) or T_w (TEMP)
+};
+
+// Everything a single-phase kernel needs; passed by value.
+struct SpParams {
+  int nx, ny, pitch;
+  long long plane;        // elements per population plane (ny * pitch)
+  int xper, yper;         // momentum lattice periodic along x / y
+  int txper, typer;       // thermal lattice periodic along x / y
+  int gbase;              // plane index of g_0 (9 with a momentum LBE, else 0)
+  DevSide side[4];
+  // SI constants
+  double c, cs2, dt, dx;
+  double rho0, T0;        // storage offsets (deviation form)
+  double Fx, Fy;          // uniform body force
+  double ux_pres, uy_pres;
+  // momentum collision
+  double omega;           // BGK: dt/tau
+  double s_e, s_eps, s_q, s_nu;  // MRT: dt * Lambda_k for e, eps, q, nu moments
+  // thermal collision
+  double omegaT;          // dt/tau_T
+  double tsrc_fac;        // BGK thermal source prefactor (1 - dt/(2 tau_sg))
+  double flux_coef;       // dt / (dx rho0 cp): q'' -> K per step (Eq. BB_T, lambda = 1)
+  // optional per-cell fields (storage precision, pitched planes)
+  const void *qdot;       // thermal source qdot [K/s], or null
+  const void *force;      // 2 planes F_x, F_y [N m^-3], or null
+  // state
+  int local;              // 1: src holds pre-collision f(t) itself (right after init)
+  const void *src;        // post-collision populations of the previous step
+  void *dst;              // post-collision populations written by this step
+};
+
+enum { FLOW_NONE = 0, FLOW_BGK = 1, FLOW_MRT = 2 };
+enum { TH_NONE = 0, TH_BGK = 1, TH_MRT = 2 };
+
+// Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
+cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
+// Equilibrium initialisation (pre-collision state of time 0) from double fields (device).
+cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double *a,
+                    const double *ux, const double *uy, const double *b, dim3 block,
+                    cudaStream_t s);
+// Macroscopic fields of the current state into nx*ny double planes (mask bit order).
+cudaError_t sp_moments(const SpParams &P, int prec, int flow, int th, unsigned mask,
+                       double *out, cudaStream_t s);
+// Per-block partial integrals (4 doubles per block) then a fixed-order final reduction.
+cudaError_t sp_integrals(const SpParams &P, int prec, int flow, int th, double *partials,
+                         int max_blocks, double *out4, cudaStream_t s);
+int sp_integral_blocks(int nx, int ny);
+
+// Convert nx*ny double planes into pitched storage planes (sources, forces).
+cudaError_t to_storage(const double *in, void *out, int nx, int ny, int pitch, int nplanes,
+                       long long plane, int prec, double scale, cudaStream_t s);
+// State <-> packed (unpitched) copies for checkpointing.
+cudaError_t pack_state(const void *state, void *packed, int nx, int ny, int pitch, int nq,
+                       long long plane, int elem, int unpack, cudaStream_t s);
+
+}  // namespace lbmk

@@ -1,0 +1,33 @@
+// Internal declarations of the two-phase kernels (step_mp.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lbmk {
+
+// Two-phase solve on a fully periodic grid.  State planes: z_0..8, h_0..4,
+// (phi u)_x, (phi u)_y of the previous step.
+struct MpParams {
+  int nx, ny, pitch;
+  long long plane;
+  double c, cs2, dt, dx;
+  double rho_l, rho_g, nu_l, nu_g;
+  double kappa, beta, W, tauphi;
+  int nu_rule, z_mrt, qy_literal;
+  double Fx, Fy;
+  const void *force;  // 2 planes or null
+  int local;          // 1: src holds the pre-collision state itself (after init)
+  const void *src;
+  void *dst;
+  void *phi;          // order-parameter plane
+};
+
+cudaError_t mp_step(const MpParams &P, int prec, cudaStream_t s);
+// Equilibria of the given fields (pre-collision state of time 0) into P.dst.
+cudaError_t mp_init(const MpParams &P, int prec, const double *phi0, const double *ux0, const double *uy0,
+                    const double *p0, cudaStream_t s);
+cudaError_t mp_moments(const MpParams &P, int prec, unsigned mask, double *out, cudaStream_t s);
+cudaError_t mp_integrals(const MpParams &P, int prec, double *partials, int max_blocks, double *out4,
+                         cudaStream_t s);
+int mp_integral_blocks(int nx, int ny);
+
+}  // namespace lbmk

@@ -1,0 +1,417 @@
+// Two-phase kernels: conservative Allen-Cahn h_i (D2Q5, BGK) coupled to the
+// pressure-evolution z_i (D2Q9, MRT or BGK) of the model described in Sec. 2.3
+// of Martins, Alvarino & Cabezas-Gomez (arXiv:2302.04120), all in SI units.
+//
+// A step is two launches:
+//   pass 1 (k_mp_phi):     pull h_i from the post-collision buffer and write
+//                          phi = sum h_i (Eq. zero_moment_h);
+//   pass 2 (k_mp_collide): stage a (BX+2) x (BY+2) tile of phi with a one-node
+//                          periodic halo in shared memory, take the isotropic
+//                          gradient and Laplacian (Eqs. gradient, laplacian, D2Q9
+//                          weights), the chemical potential (Eq. chemical_potential),
+//                          the guarded normal, F_s = mu grad phi, grad rho; pull z_i
+//                          and h_i again; recover u (Eq. u_Liang) and p (Eq. p_Liang)
+//                          in FP64; collide h (Eqs. eq_lattice_boltzmann_interface,
+//                          heq_liang, source_term_interface) and z (Eq. colisao_MRT
+//                          with the multiphase [Lambda]_dim of Sec. 3, Eqs. zeq_liang,
+//                          s_i_Liang, forcing_term_pressure_evolution); store h*, z*
+//                          and phi u for the next explicit d_t(phi u).
+// In the FP32 form the populations, phi and (phi u) are stored in FP32 and the
+// collision runs in FP32, while rho(phi), u and p are recovered in FP64: at the
+// ~43000 density ratio of saturated water u = j / rho divides by rho_g = 0.023.
+#include <cuda_runtime.h>
+
+#include "lattice.cuh"
+#include "lbm_mp.cuh"
+
+namespace lbmk {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ int modi(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+template <typename S, typename R>
+__device__ __forceinline__ void pull_h(const MpParams &P, const S *src, int i, int j, R h[5]) {
+  const S *hs = src + 9ll * P.plane;
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    int si = P.local ? i : wrapi(i - cx5(q), P.nx), sj = P.local ? j : wrapi(j - cy5(q), P.ny);
+    h[q] = (R)hs[q * P.plane + (long long)sj * P.pitch + si];
+  }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void pull_z(const MpParams &P, const S *src, int i, int j, R z[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    int si = P.local ? i : wrapi(i - cx9(q), P.nx), sj = P.local ? j : wrapi(j - cy9(q), P.ny);
+    z[q] = (R)src[q * P.plane + (long long)sj * P.pitch + si];
+  }
+}
+
+// pass 1: phi = sum_i h_i (Eq. zero_moment_h)
+template <int PREC>
+__global__ void __launch_bounds__(256) k_mp_phi(const MpParams P) {
+  typedef typename Prec<PREC>::S S;
+  typedef typename Prec<PREC>::R R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.nx || j >= P.ny) return;
+  R h[5];
+  pull_h<S, R>(P, (const S *)P.src, i, j, h);
+  ((S *)P.phi)[(long long)j * P.pitch + i] = (S)((h[0] + h[1]) + (h[2] + h[3]) + h[4]);
+}
+
+// Macroscopic state of a node (the FP64 recovery of rho, u, p).
+struct MpMacro {
+  double phi, rho, ux, uy, p, mu, gx, gy, nxv, nyv, Fx, Fy, drx, dry, tau;
+};
+
+// Gradient/Laplacian from the shared tile, then rho, nu, tau, F, u, p.
+template <typename R>
+__device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX + 2], int tx, int ty,
+                                         const double zsum_x, const double zsum_y, const double zsum_nz,
+                                         double fext_x, double fext_y, MpMacro &m) {
+  // D2Q9 neighbours phi(x + c_i dt)
+  const double pc = (double)tile[ty][tx];
+  const double pE = (double)tile[ty][tx + 1], pW = (double)tile[ty][tx - 1];
+  const double pN = (double)tile[ty + 1][tx], pS = (double)tile[ty - 1][tx];
+  const double pNE = (double)tile[ty + 1][tx + 1], pNW = (double)tile[ty + 1][tx - 1];
+  const double pSW = (double)tile[ty - 1][tx - 1], pSE = (double)tile[ty - 1][tx + 1];
+  // Eq. gradient: sum_i w_i c_i phi_i / (c_s^2 dt) = (3/dx) sum_i w_i e_i phi_i
+  const double g3 = 3.0 / P.dx;
+  m.gx = g3 * ((pE - pW) * (1.0 / 9.0) + ((pNE - pNW) + (pSE - pSW)) * (1.0 / 36.0));
+  m.gy = g3 * ((pN - pS) * (1.0 / 9.0) + ((pNE - pSE) + (pNW - pSW)) * (1.0 / 36.0));
+  // Eq. laplacian: sum_i 2 w_i (phi_i - phi) / (c_s^2 dt^2) = (6/dx^2) sum_i w_i (phi_i - phi)
+  const double l6 = 6.0 / (P.dx * P.dx);
+  const double lap = l6 * (((pE + pW) + (pN + pS) - 4.0 * pc) * (1.0 / 9.0) +
+                           ((pNE + pNW) + (pSE + pSW) - 4.0 * pc) * (1.0 / 36.0));
+  m.phi = pc;
+  // Eq. chemical_potential
+  m.mu = 4.0 * P.beta * pc * (pc - 1.0) * (pc - 0.5) - P.kappa * lap;
+  const double gn = sqrt(m.gx * m.gx + m.gy * m.gy);
+  m.nxv = gn != 0.0 ? m.gx / gn : 0.0;  // normal only where |grad phi| != 0
+  m.nyv = gn != 0.0 ? m.gy / gn : 0.0;
+  const double drl = P.rho_l - P.rho_g;
+  m.rho = P.rho_g + pc * drl;
+  double nu;
+  if (P.nu_rule == 0) nu = P.nu_g + pc * (P.nu_l - P.nu_g);
+  else nu = (P.rho_g * P.nu_g + pc * (P.rho_l * P.nu_l - P.rho_g * P.nu_g)) / m.rho;
+  m.tau = nu / P.cs2 + 0.5 * P.dt;
+  m.drx = drl * m.gx;
+  m.dry = drl * m.gy;
+  m.Fx = m.mu * m.gx + P.Fx + fext_x;
+  m.Fy = m.mu * m.gy + P.Fy + fext_y;
+  // Eq. u_Liang, then Eq. p_Liang (u first)
+  m.ux = (zsum_x + 0.5 * P.dt * m.Fx) / m.rho;
+  m.uy = (zsum_y + 0.5 * P.dt * m.Fy) / m.rho;
+  const double usq = m.ux * m.ux + m.uy * m.uy;
+  const double s0 = (4.0 / 9.0) * (-0.5 * usq / P.cs2);  // s_0(u), Eq. s_i_Liang
+  m.p = P.cs2 / (1.0 - 4.0 / 9.0) * (zsum_nz + 0.5 * P.dt * (m.ux * m.drx + m.uy * m.dry) + m.rho * s0);
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro &m, double dpux, double dpuy, R h[5]) {
+  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c);
+  const R om = (R)(P.dt / P.tauphi);
+  const R sfac = (R)((1.0 - P.dt / (2.0 * P.tauphi)) * P.dt);
+  const double a_int = P.cs2 * 4.0 * m.phi * (1.0 - m.phi) / P.W;
+  const R ax = (R)(dpux + a_int * m.nxv), ay = (R)(dpuy + a_int * m.nyv);
+  const R phi = (R)m.phi, ux = (R)m.ux, uy = (R)m.uy;
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    const R cxq = c * (R)cx5(q), cyq = c * (R)cy5(q);
+    const R heq = phi * w5<R>(q) * ((R)1 + (cxq * ux + cyq * uy) * inv_cs2);  // Eq. heq_liang
+    const R Sh = w5<R>(q) * (cxq * ax + cyq * ay) * inv_cs2;                    // Eq. source_term_interface
+    h[q] = h[q] - om * (h[q] - heq) + sfac * Sh;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro &m, R z[9]) {
+  const double dt = P.dt;
+  const R c = (R)P.c;
+  const R rho = (R)m.rho, ux = (R)m.ux, uy = (R)m.uy;
+  const R Fx = (R)m.Fx, Fy = (R)m.Fy, gx = (R)m.drx, gy = (R)m.dry;
+  if (!P.z_mrt) {
+    // BGK, Eq. eq_lattice_boltzmann_pressure
+    const R inv_cs2 = (R)(1.0 / P.cs2);
+    const R om = (R)(dt / m.tau), sfac = (R)((1.0 - dt / (2.0 * m.tau)) * dt);
+    const R Pp = (R)(m.p / P.cs2);
+    const R hu = (R)0.5 * (ux * ux + uy * uy) * inv_cs2;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      const R cxq = c * (R)cx9(q), cyq = c * (R)cy9(q);
+      const R cu = cxq * ux + cyq * uy;
+      const R si = w9<R>(q) * (cu * inv_cs2 * ((R)1 + (R)0.5 * cu * inv_cs2) - hu);
+      const R zeq = Pp * (w9<R>(q) - (q == 0 ? (R)1 : (R)0)) + rho * si;  // Eq. zeq_liang
+      const R Fz = w9<R>(q) * ((cxq * Fx + cyq * Fy) + cu * (cxq * gx + cyq * gy)) * inv_cs2;
+      z[q] = z[q] - om * (z[q] - zeq) + sfac * Fz;
+    }
+    return;
+  }
+  // MRT on lattice-scaled moments (see step_sp.cu): equilibrium moments of z_eq
+  // are M f_eq(rho, u) - rho M w + (p/c_s^2)(M w - M e_0); forcing moments of
+  // F_hat^z = w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2.
+  const R ic = (R)1 / c;
+  const R hx = ux * ic, hy = uy * ic, usq = hx * hx + hy * hy;
+  const R Pp = (R)(m.p / P.cs2);
+  const R s14 = (z[1] + z[2]) + (z[3] + z[4]);
+  const R s58 = (z[5] + z[6]) + (z[7] + z[8]);
+  const R m0 = z[0] + s14 + s58;
+  const R m_e = -(R)4 * z[0] - s14 + (R)2 * s58;
+  const R m_ep = (R)4 * z[0] - (R)2 * s14 + s58;
+  const R d58 = z[5] - z[7], d68 = z[6] - z[8];
+  const R m_jx = (z[1] - z[3]) + d58 - d68;
+  const R m_jy = (z[2] - z[4]) + d58 + d68;
+  const R m_qx = (R)2 * (z[3] - z[1]) + d58 - d68;
+  const R m_qy = (R)2 * (z[4] - z[2]) + d58 + d68;
+  const R m_xx = (z[1] + z[3]) - (z[2] + z[4]);
+  const R m_xy = (z[5] + z[7]) - (z[6] + z[8]);
+  const R eq_e = (R)3 * rho * usq + (R)2 * Pp;
+  const R eq_ep = -(R)3 * rho * usq - (R)3 * Pp;
+  const R eq_jx = rho * hx, eq_jy = rho * hy;
+  const R eq_xx = rho * (hx * hx - hy * hy), eq_xy = rho * hx * hy;
+  const R ug = ux * gx + uy * gy;
+  const R F0 = ug, Fep = -ug;
+  const R Fjx = Fx * ic, Fjy = Fy * ic;
+  const R Fxx = (R)(2.0 / 3.0) * (ux * gx - uy * gy), Fxy = (R)(1.0 / 3.0) * (ux * gy + uy * gx);
+  // multiphase [Lambda]_dim (Sec. 3): 1/dt everywhere except omega_q2 (q_x, and
+  // q_y by the isotropic reading) and 1/tau for the stress moments
+  const double wnu = 1.0 / m.tau;
+  const R sq = (R)(dt * (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu));
+  const R sqy = P.qy_literal ? (R)1 : sq;
+  const R snu = (R)(dt * wnu);
+  const R rdt = (R)dt, one = (R)1, half = (R)0.5;
+  const R d0 = m0 - half * rdt * F0;                 // s = 1: (m - 0) - (1 - 1/2) dt F
+  const R d_e = (m_e - eq_e);                        // F_e = 0
+  const R d_ep = (m_ep - eq_ep) - half * rdt * Fep;
+  const R d_jx = (m_jx - eq_jx) - half * rdt * Fjx;
+  const R d_jy = (m_jy - eq_jy) - half * rdt * Fjy;
+  const R d_qx = sq * (m_qx + eq_jx) + (one - half * sq) * rdt * Fjx;   // eq_qx = -rho u_x/c, F_qx = -F_x/c
+  const R d_qy = sqy * (m_qy + eq_jy) + (one - half * sqy) * rdt * Fjy;
+  const R d_xx = snu * (m_xx - eq_xx) - (one - half * snu) * rdt * Fxx;
+  const R d_xy = snu * (m_xy - eq_xy) - (one - half * snu) * rdt * Fxy;
+  const R a0 = d0 * ((R)1 / (R)9);
+  const R a1 = d_e * ((R)1 / (R)36), a2 = d_ep * ((R)1 / (R)36);
+  const R a3 = d_jx * ((R)1 / (R)6), a4 = d_qx * ((R)1 / (R)12);
+  const R a5 = d_jy * ((R)1 / (R)6), a6 = d_qy * ((R)1 / (R)12);
+  const R a7 = d_xx * (R)0.25, a8 = d_xy * (R)0.25;
+  const R ax = a0 - a1 - (R)2 * a2;
+  const R dg = a0 + (R)2 * a1 + a2;
+  z[0] -= a0 + (R)4 * (a2 - a1);
+  z[1] -= ax + a3 - (R)2 * a4 + a7;
+  z[2] -= ax + a5 - (R)2 * a6 - a7;
+  z[3] -= ax - a3 + (R)2 * a4 + a7;
+  z[4] -= ax - a5 + (R)2 * a6 - a7;
+  const R p34 = a3 + a4, p56 = a5 + a6;
+  z[5] -= dg + p34 + p56 + a8;
+  z[6] -= dg - p34 + p56 - a8;
+  z[7] -= dg - p34 - p56 + a8;
+  z[8] -= dg + p34 - p56 - a8;
+}
+
+enum { MODE_STEP = 0, MODE_MOMENTS = 2, MODE_INTEGRALS = 3 };
+
+__device__ __forceinline__ void reduce4_block(double v[4], double *out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+  }
+  __shared__ double sh[8][4];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) { sh[tid >> 5][0] = v[0]; sh[tid >> 5][1] = v[1]; sh[tid >> 5][2] = v[2]; sh[tid >> 5][3] = v[3]; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0, mx = 0, cnt = 0;
+    for (int w = 0; w < (BX * BY) / 32; w++) { a += sh[w][0]; b += sh[w][1]; mx = fmax(mx, sh[w][2]); cnt += sh[w][3]; }
+    out[0] = a; out[1] = b; out[2] = mx; out[3] = cnt;
+  }
+}
+
+// pass 2 (and its init / moments / integrals variants)
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const double *A, const double *UX,
+                                                         const double *UY, const double *B, unsigned mask,
+                                                         double *out) {
+  typedef typename Prec<PREC>::S S;
+  typedef typename Prec<PREC>::R R;
+  __shared__ R tile[BY + 2][BX + 2];
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const S *phi = (const S *)P.phi;
+  // stage phi with a one-node periodic halo
+  for (int t = tid; t < (BX + 2) * (BY + 2); t += BX * BY) {
+    const int ty = t / (BX + 2), tx = t - ty * (BX + 2);
+    const int gi = modi(i0 + tx - 1, P.nx), gj = modi(j0 + ty - 1, P.ny);
+    tile[ty][tx] = (R)phi[(long long)gj * P.pitch + gi];
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  const bool live = (i < P.nx) && (j < P.ny);
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  if (live) {
+    const long long n = (long long)j * P.pitch + i;
+    const S *src = (const S *)P.src;
+    R z[9], h[5];
+    double prevx, prevy;
+    const double c = P.c;
+    double fex = 0.0, fey = 0.0;
+    if (P.force) {
+      fex = (double)((const S *)P.force)[n];
+      fey = (double)((const S *)P.force)[P.plane + n];
+    }
+    pull_z<S, R>(P, src, i, j, z);
+    pull_h<S, R>(P, src, i, j, h);
+    prevx = (double)src[14ll * P.plane + n];
+    prevy = (double)src[15ll * P.plane + n];
+    // FP64 sums for the u and p recovery (Eqs. u_Liang, p_Liang)
+    double zd[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) zd[q] = (double)z[q];
+    const double jx = c * ((zd[1] - zd[3]) + (zd[5] - zd[6]) + (zd[8] - zd[7]));
+    const double jy = c * ((zd[2] - zd[4]) + (zd[5] - zd[8]) + (zd[6] - zd[7]));
+    const double znz = ((zd[1] + zd[2]) + (zd[3] + zd[4])) + ((zd[5] + zd[6]) + (zd[7] + zd[8]));
+    MpMacro m;
+    mp_macro<R>(P, tile, threadIdx.x + 1, threadIdx.y + 1, jx, jy, znz, fex, fey, m);
+    if (MODE == MODE_STEP) {
+      const double pux = m.phi * m.ux, puy = m.phi * m.uy;
+      const double dpux = (pux - prevx) / P.dt, dpuy = (puy - prevy) / P.dt;  // explicit Euler d_t(phi u)
+      collide_h<R>(P, m, dpux, dpuy, h);
+      collide_z<R>(P, m, z);
+      S *dst = (S *)P.dst;
+#pragma unroll
+      for (int q = 0; q < 9; q++) dst[q * P.plane + n] = (S)z[q];
+#pragma unroll
+      for (int q = 0; q < 5; q++) dst[(9 + q) * P.plane + n] = (S)h[q];
+      dst[14ll * P.plane + n] = (S)pux;
+      dst[15ll * P.plane + n] = (S)puy;
+    } else if (MODE == MODE_MOMENTS) {
+      const long long N = (long long)P.nx * P.ny, k = (long long)j * P.nx + i;
+      int slot = 0;
+      if (mask & 1u) out[(slot++) * N + k] = m.rho;
+      if (mask & 2u) out[(slot++) * N + k] = m.ux;
+      if (mask & 4u) out[(slot++) * N + k] = m.uy;
+      if (mask & 8u) out[(slot++) * N + k] = 0.0;
+      if (mask & 16u) out[(slot++) * N + k] = m.p;
+      if (mask & 32u) out[(slot++) * N + k] = m.phi;
+    } else {
+      const double umag = sqrt(m.ux * m.ux + m.uy * m.uy);
+      const bool bad = !isfinite(m.rho) || !isfinite(umag) || !isfinite(m.p) || umag >= P.c;
+      red[0] = m.rho * P.dx * P.dx;
+      red[1] = m.phi;
+      red[2] = bad ? 0.0 : umag;
+      red[3] = bad ? 1.0 : 0.0;
+    }
+  }
+  if (MODE == MODE_INTEGRALS) reduce4_block(red, out + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+__global__ void k_mp_final(const double *partials, int nb, double *out4) {
+  const int lane = threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = lane; b < nb; b += 32) {
+    v[0] += partials[4 * b + 0];
+    v[1] += partials[4 * b + 1];
+    v[2] = fmax(v[2], partials[4 * b + 2]);
+    v[3] += partials[4 * b + 3];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+  }
+  if (lane == 0) { out4[0] = v[0]; out4[1] = v[1]; out4[2] = v[2]; out4[3] = v[3]; }
+}
+
+// Equilibria of the given fields (Eqs. heq_liang, zeq_liang, s_i_Liang) as the
+// pre-collision state of time 0; (phi u)_prev = phi0 u0.  Defaults: phi 1, u 0, p 0.
+template <typename S>
+__global__ void k_mp_init(const MpParams P, const double *A, const double *UX, const double *UY, const double *B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.nx || j >= P.ny) return;
+  const long long n = (long long)j * P.pitch + i;
+  const int k = j * P.nx + i;
+  S *dst = (S *)P.dst;
+  const double c = P.c;
+  const double ph = A ? A[k] : 1.0, u0 = UX ? UX[k] : 0.0, v0 = UY ? UY[k] : 0.0, p0 = B ? B[k] : 0.0;
+  const double rho = P.rho_g + ph * (P.rho_l - P.rho_g);
+  const double usq = u0 * u0 + v0 * v0;
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    const double cu = c * (cx9(q) * u0 + cy9(q) * v0);
+    const double si = w9<double>(q) * (cu / P.cs2 + 0.5 * cu * cu / (P.cs2 * P.cs2) - 0.5 * usq / P.cs2);
+    dst[q * P.plane + n] = (S)(p0 / P.cs2 * (w9<double>(q) - (q == 0 ? 1.0 : 0.0)) + rho * si);
+  }
+#pragma unroll
+  for (int q = 0; q < 5; q++)
+    dst[(9 + q) * P.plane + n] = (S)(ph * w5<double>(q) * (1.0 + c * (cx5(q) * u0 + cy5(q) * v0) / P.cs2));
+  dst[14ll * P.plane + n] = (S)(ph * u0);
+  dst[15ll * P.plane + n] = (S)(ph * v0);
+}
+
+dim3 mp_grid(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
+
+}  // namespace
+
+int mp_integral_blocks(int nx, int ny) {
+  dim3 g = mp_grid(nx, ny);
+  return (int)(g.x * g.y);
+}
+
+cudaError_t mp_step(const MpParams &P, int prec, cudaStream_t s) {
+  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
+  if (prec == 0) {
+    k_mp_phi<0><<<g, b, 0, s>>>(P);
+    k_mp_collide<0, MODE_STEP><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
+  } else {
+    k_mp_phi<1><<<g, b, 0, s>>>(P);
+    k_mp_collide<1, MODE_STEP><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mp_init(const MpParams &P, int prec, const double *phi0, const double *ux0, const double *uy0,
+                    const double *p0, cudaStream_t s) {
+  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
+  if (prec == 0) k_mp_init<double><<<g, b, 0, s>>>(P, phi0, ux0, uy0, p0);
+  else k_mp_init<float><<<g, b, 0, s>>>(P, phi0, ux0, uy0, p0);
+  return cudaGetLastError();
+}
+
+cudaError_t mp_moments(const MpParams &P, int prec, unsigned mask, double *out, cudaStream_t s) {
+  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
+  if (prec == 0) {
+    k_mp_phi<0><<<g, b, 0, s>>>(P);
+    k_mp_collide<0, MODE_MOMENTS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
+  } else {
+    k_mp_phi<1><<<g, b, 0, s>>>(P);
+    k_mp_collide<1, MODE_MOMENTS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t mp_integrals(const MpParams &P, int prec, double *partials, int max_blocks, double *out4, cudaStream_t s) {
+  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
+  if ((int)(g.x * g.y) > max_blocks) return cudaErrorInvalidValue;
+  if (prec == 0) {
+    k_mp_phi<0><<<g, b, 0, s>>>(P);
+    k_mp_collide<0, MODE_INTEGRALS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, partials);
+  } else {
+    k_mp_phi<1><<<g, b, 0, s>>>(P);
+    k_mp_collide<1, MODE_INTEGRALS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, partials);
+  }
+  k_mp_final<<<1, 32, 0, s>>>(partials, (int)(g.x * g.y), out4);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -1,0 +1,644 @@
+// Single-phase kernels of the dimensional lattice Boltzmann method
+// (Martins, Alvarino & Cabezas-Gomez, arXiv:2302.04120) for sm_103a.
+//
+// One thread = one lattice node.  Each step is ONE kernel launch that
+//   1. pulls f_i(x, t) = f_i*(x - c_i dt, t - dt) from the post-collision buffer
+//      of the previous step (Eq. eq_lattice_boltzmann_geral, streaming part),
+//      replacing links that leave the domain by the link-wise boundary rules
+//      (Eqs. BB_vel, anti_BB_vel, anti_BB_T, BB_T, periodic and outlet
+//      extrapolation of Sec. 2.1/2.2);
+//   2. takes the moments (Eqs. zero_moment_f, first_moment_f, zero_moment_g);
+//   3. collides: BGK (Eq. eq_lattice_boltzmann_BGK with Guo forcing, Eq.
+//      forcing_term) or MRT (Eq. colisao_MRT with [M]_dim, Eq. M_matrix_dim,
+//      and the dimensional rates of Sec. 3), and the D2Q5 thermal LBE (Eqs.
+//      eq_lattice_boltzmann_BGK_T, forcing_term_g, geq_geral);
+//   4. stores the post-collision values into the other ping-pong buffer.
+//
+// Storage is structure-of-arrays: plane q holds population q on an ny x pitch
+// grid, so the 32 lanes of a warp touch 32 consecutive nodes of one plane.
+// Populations are stored as deviations from the rest equilibrium
+// (f_i - w_i rho0, g_i - w_i T0): in FP32 this keeps the non-equilibrium
+// digits of f_i ~ 1e3 kg m^-3; in FP64 it costs nothing because the deviation
+// form of every formula has the same operation count.
+//
+// MRT without matrices: [M]_dim = D [M] with D = diag(c^n), so the relaxation
+// is done on the lattice-scaled moments M f (integer combinations) with the
+// equilibrium and forcing moments divided by c^n, and [M]_dim^-1 is applied as
+// M^T diag(1/|row|^2) D^-1 -- the same arithmetic as the matrices of Sec. 3 /
+// App. A up to rounding order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+#include "lbm_internal.cuh"
+
+namespace lbmk {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3 };
+enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3 };
+
+__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Position of node (i, j) along a side, and the side's length.
+__device__ __forceinline__ int along(int side, int i, int j) { return side < 2 ? j : i; }
+__device__ __forceinline__ int side_len(const SpParams &P, int side) { return side < 2 ? P.ny : P.nx; }
+
+// Which side the link arriving at (i, j) along c = (cx, cy) comes through (source
+// node (i - cx, j - cy) outside the domain), or -1.  y-sides win at corners.
+__device__ __forceinline__ int entry_side(int i, int j, int cx, int cy, int nx, int ny, int xper, int yper) {
+  int si = i - cx, sj = j - cy;
+  if (!yper) {
+    if (sj < 0) return 2;
+    if (sj >= ny) return 3;
+  }
+  if (!xper) {
+    if (si < 0) return 0;
+    if (si >= nx) return 1;
+  }
+  return -1;
+}
+
+// Pre-collision velocity of time t at node n rebuilt from its post-collision
+// populations: rho = sum f*, rho u = sum c f* - dt F / 2 (the collision adds dt F
+// to the momentum, Eqs. first_moment_f and forcing_term).
+template <typename S, typename R>
+__device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, int i, int j, R &ux, R &uy) {
+  long long n = (long long)j * P.pitch + i;
+  R f[9];
+#pragma unroll
+  for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
+  R drho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+  R rho = (R)P.rho0 + drho;
+  R c = (R)P.c;
+  R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
+  R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
+  R Fx = (R)P.Fx, Fy = (R)P.Fy;
+  if (P.force) {
+    const S *fo = (const S *)P.force;
+    Fx += (R)fo[n];
+    Fy += (R)fo[P.plane + n];
+  }
+  ux = (jx - (R)0.5 * (R)P.dt * Fx) / rho;
+  uy = (jy - (R)0.5 * (R)P.dt * Fy) / rho;
+}
+
+// Pull of all momentum populations at node (i, j), with boundary links.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, int j, bool interior, R f[9]) {
+  const long long n = (long long)j * P.pitch + i;
+  if (interior) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n - (long long)cy9(q) * P.pitch - cx9(q)];
+    return;
+  }
+  if (P.local) {  // src holds f(t) itself (first step after initialisation)
+#pragma unroll
+    for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
+    return;
+  }
+  const R c = (R)P.c, inv_cs2 = (R)1 / (R)P.cs2;
+  // outlet velocity extrapolation, Eq. anti_BB_vel and the rule below it (reading:
+  // pre-collision velocities of time t at the boundary node and its inner neighbour)
+  R uwp[4][2];
+#pragma unroll
+  for (int s = 0; s < 4; s++) { uwp[s][0] = 0; uwp[s][1] = 0; }
+#pragma unroll
+  for (int s = 0; s < 4; s++) {
+    bool on = (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
+    if (on && P.side[s].kind == BC_PRESSURE) {
+      int ii = i + (s == 0) - (s == 1), jj = j + (s == 2) - (s == 3);
+      R ub, vb, ui, vi;
+      post_velocity<S, R>(P, src, i, j, ub, vb);
+      post_velocity<S, R>(P, src, ii, jj, ui, vi);
+      uwp[s][0] = ub + (R)0.5 * (ub - ui);
+      uwp[s][1] = vb + (R)0.5 * (vb - vi);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    const int side = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper);
+    if (side < 0) {
+      int si = wrap(i - cx9(q), P.nx), sj = wrap(j - cy9(q), P.ny);
+      f[q] = (R)src[q * P.plane + (long long)sj * P.pitch + si];
+      continue;
+    }
+    // outgoing direction o = opp(q) leaves node (i, j) through `side`
+    const int o = opp9(q);
+    const R fo = (R)src[o * P.plane + n];
+    const DevSide &sd = P.side[side];
+    const int a = along(side, i, j), len = side_len(P, side);
+    const R rw = (R)sd.rho_w;
+    const R cox = c * (R)cx9(o), coy = c * (R)cy9(o);
+    if (sd.kind == BC_PRESSURE) {
+      // Eq. anti_BB_vel in deviation form: f_q - w rho0 = -(f_o* - w rho0) + 2 w [rho_w(...) - rho0]
+      R ux = uwp[side][0], uy = uwp[side][1];
+      R cu = cox * ux + coy * uy;
+      R uu = ux * ux + uy * uy;
+      f[q] = -fo + (R)2 * w9<R>(o) * (rw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - (R)P.rho0);
+    } else {
+      // Eq. BB_vel (walls and velocity inlet): f_q = f_o* - 2 w_o rho_w c_o.u_w / c_s^2
+      R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
+      f[q] = fo - (R)2 * w9<R>(o) * rw * (cox * ux + coy * uy) * inv_cs2;
+    }
+  }
+}
+
+// Pull of the D2Q5 thermal populations at node (i, j) with boundary links.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, int j, bool interior, R g[5]) {
+  const long long n = (long long)j * P.pitch + i;
+  const S *gsrc = src + (long long)P.gbase * P.plane;
+  if (interior) {
+#pragma unroll
+    for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n - (long long)cy5(q) * P.pitch - cx5(q)];
+    return;
+  }
+  if (P.local) {
+#pragma unroll
+    for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n];
+    return;
+  }
+  const R c = (R)P.c, inv_cs2 = (R)1 / (R)P.cs2;
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    const int side = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
+    if (side < 0) {
+      int si = wrap(i - cx5(q), P.nx), sj = wrap(j - cy5(q), P.ny);
+      g[q] = (R)gsrc[q * P.plane + (long long)sj * P.pitch + si];
+      continue;
+    }
+    const int o = opp5(q);
+    const DevSide &sd = P.side[side];
+    const int a = along(side, i, j), len = side_len(P, side);
+    if (sd.tkind == TBC_OUTFLOW) {
+      // g_q(x_b, t+dt) = g_q(x_b-1, t+dt) = g_q*(x_b-1 - c_q dt, t) (Sec. 2.2, outlet)
+      int ii = i + (side == 0) - (side == 1), jj = j + (side == 2) - (side == 3);
+      int si = min(max(ii - cx5(q), 0), P.nx - 1), sj = min(max(jj - cy5(q), 0), P.ny - 1);
+      g[q] = (R)gsrc[q * P.plane + (long long)sj * P.pitch + si];
+    } else if (sd.tkind == TBC_TEMP) {
+      // Eq. anti_BB_T in deviation form
+      const R go = (R)gsrc[o * P.plane + n];
+      R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
+      R cu = c * ((R)cx5(o) * ux + (R)cy5(o) * uy);
+      R uu = ux * ux + uy * uy;
+      R Tw = sd.tw ? (R)sd.tw[a] : (R)0;
+      g[q] = -go + (R)2 * w5<R>(o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - (R)P.T0);
+    } else {
+      // Eq. BB_T with lambda = 1 for the single unknown (FLUX; zero flux = adiabatic)
+      const R go = (R)gsrc[o * P.plane + n];
+      R qf = sd.tw ? (R)sd.tw[a] : (R)0;
+      g[q] = go + (R)P.flux_coef * qf;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Moments and collisions (deviation form)
+// ----------------------------------------------------------------------------
+template <typename R>
+struct Macro {
+  R drho, rho, ux, uy, Fx, Fy;  // momentum
+  R sumg, qd, T;                // thermal
+};
+
+template <typename S, typename R>
+__device__ __forceinline__ void load_sources(const SpParams &P, long long n, Macro<R> &m) {
+  m.Fx = (R)P.Fx;
+  m.Fy = (R)P.Fy;
+  if (P.force) {
+    const S *fo = (const S *)P.force;
+    m.Fx += (R)fo[n];
+    m.Fy += (R)fo[P.plane + n];
+  }
+  m.qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
+}
+
+template <typename R, int FLOW, int TH>
+__device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R g[5], Macro<R> &m) {
+  if (FLOW != FLOW_NONE) {
+    // Eqs. zero_moment_f and first_moment_f
+    m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    m.rho = (R)P.rho0 + m.drho;
+    const R c = (R)P.c, hdt = (R)0.5 * (R)P.dt;
+    const R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
+    const R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
+    const R inv = (R)1 / m.rho;
+    m.ux = (jx + hdt * m.Fx) * inv;
+    m.uy = (jy + hdt * m.Fy) * inv;
+  } else {
+    m.drho = 0;
+    m.rho = (R)P.rho0;
+    m.ux = (R)P.ux_pres;
+    m.uy = (R)P.uy_pres;
+  }
+  if (TH != TH_NONE) {
+    // Eq. zero_moment_g
+    m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    m.T = (R)P.T0 + m.sumg + (R)0.5 * (R)P.dt * m.qd;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &m, R f[9]) {
+  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c), inv_cs4 = inv_cs2 * inv_cs2;
+  const R om = (R)P.omega;
+  const R fac = ((R)1 - (R)0.5 * om) * (R)P.dt;  // (1 - dt/(2 tau)) dt
+  const R hu = (R)0.5 * (m.ux * m.ux + m.uy * m.uy) * inv_cs2;  // u^2 / (2 c_s^2)
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    const R cxq = c * (R)cx9(q), cyq = c * (R)cy9(q);
+    const R cu = cxq * m.ux + cyq * m.uy;
+    // f_eq - w rho0 (Eq. feq_geral, deviation form: no O(rho0) cancellation)
+    const R feq = w9<R>(q) * (m.drho + m.rho * (cu * inv_cs2 * ((R)1 + (R)0.5 * cu * inv_cs2) - hu));
+    // Guo forcing F_hat (Eq. forcing_term)
+    const R cF = cxq * m.Fx + cyq * m.Fy;
+    const R uF = m.ux * m.Fx + m.uy * m.Fy;
+    const R Fh = w9<R>(q) * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
+    f[q] = f[q] - om * (f[q] - feq) + fac * Fh;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &m, R f[9]) {
+  const R c = (R)P.c, ic = (R)1 / c;
+  const R dt = (R)P.dt;
+  // lattice-scaled moments of the deviations (rows of Eq. M_matrix)
+  const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
+  const R s58 = (f[5] + f[6]) + (f[7] + f[8]);
+  const R m_e = -(R)4 * f[0] - s14 + (R)2 * s58;
+  const R m_ep = (R)4 * f[0] - (R)2 * s14 + s58;
+  const R d58 = (f[5] - f[7]), d68 = (f[6] - f[8]);
+  const R m_qx = (R)2 * (f[3] - f[1]) + d58 - d68;
+  const R m_qy = (R)2 * (f[4] - f[2]) + d58 + d68;
+  const R m_xx = (f[1] + f[3]) - (f[2] + f[4]);
+  const R m_xy = (f[5] + f[7]) - (f[6] + f[8]);
+  // equilibrium and forcing moments divided by c^n (Eq. M_matrix_dim row orders)
+  const R ux = m.ux * ic, uy = m.uy * ic, usq = ux * ux + uy * uy;
+  const R Fx = m.Fx * ic, Fy = m.Fy * ic, uF = ux * Fx + uy * Fy;
+  const R eq_e = -(R)2 * m.drho + (R)3 * m.rho * usq;
+  const R eq_ep = m.drho - (R)3 * m.rho * usq;
+  const R eq_qx = -m.rho * ux, eq_qy = -m.rho * uy;
+  const R eq_xx = m.rho * (ux * ux - uy * uy), eq_xy = m.rho * ux * uy;
+  const R s_e = (R)P.s_e, s_ep = (R)P.s_eps, s_q = (R)P.s_q, s_nu = (R)P.s_nu;
+  // Delta m_k = dt Lambda_k (m_k - m_k^eq) - dt (1 - dt Lambda_k / 2) F_k  (Eq. colisao_MRT)
+  const R d_e = s_e * (m_e - eq_e) - ((R)1 - (R)0.5 * s_e) * dt * ((R)6 * uF);
+  const R d_ep = s_ep * (m_ep - eq_ep) + ((R)1 - (R)0.5 * s_ep) * dt * ((R)6 * uF);
+  const R d_jx = -dt * Fx, d_jy = -dt * Fy;
+  const R d_qx = s_q * (m_qx - eq_qx) + ((R)1 - (R)0.5 * s_q) * dt * Fx;
+  const R d_qy = s_q * (m_qy - eq_qy) + ((R)1 - (R)0.5 * s_q) * dt * Fy;
+  const R d_xx = s_nu * (m_xx - eq_xx) - ((R)1 - (R)0.5 * s_nu) * dt * ((R)2 * (ux * Fx - uy * Fy));
+  const R d_xy = s_nu * (m_xy - eq_xy) - ((R)1 - (R)0.5 * s_nu) * dt * (ux * Fy + uy * Fx);
+  // back to populations: M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  const R a1 = d_e * ((R)1 / (R)36), a2 = d_ep * ((R)1 / (R)36);
+  const R a3 = d_jx * ((R)1 / (R)6), a4 = d_qx * ((R)1 / (R)12);
+  const R a5 = d_jy * ((R)1 / (R)6), a6 = d_qy * ((R)1 / (R)12);
+  const R a7 = d_xx * (R)0.25, a8 = d_xy * (R)0.25;
+  const R ax = -a1 - (R)2 * a2;   // common to i = 1..4
+  const R dg = (R)2 * a1 + a2;    // common to i = 5..8
+  f[0] -= (R)4 * (a2 - a1);
+  f[1] -= ax + a3 - (R)2 * a4 + a7;
+  f[2] -= ax + a5 - (R)2 * a6 - a7;
+  f[3] -= ax - a3 + (R)2 * a4 + a7;
+  f[4] -= ax - a5 + (R)2 * a6 - a7;
+  const R p34 = a3 + a4, p56 = a5 + a6;
+  f[5] -= dg + p34 + p56 + a8;
+  f[6] -= dg - p34 + p56 - a8;
+  f[7] -= dg - p34 - p56 + a8;
+  f[8] -= dg + p34 - p56 - a8;
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &m, R g[5]) {
+  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c);
+  const R om = (R)P.omegaT;
+  const R src = (R)P.tsrc_fac * (R)P.dt * m.qd;
+  const R dT = m.T - (R)P.T0;
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    const R cu = c * ((R)cx5(q) * m.ux + (R)cy5(q) * m.uy);
+    const R geq = w5<R>(q) * (dT + m.T * cu * inv_cs2);  // Eq. geq_geral minus w T0
+    g[q] = g[q] - om * (g[q] - geq) + w5<R>(q) * src;    // Eq. forcing_term_g
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void collide_mrt5(const SpParams &P, const Macro<R> &m, R g[5]) {
+  // D2Q5 moments (1, c_x, c_y, 5|c|^2 - 4c^2, c_x^2 - c_y^2) scaled by c^-n; rates
+  // (0, 1/tau_T, 1/tau_T, 1/dt, 1/dt); source Delta t (I - dt Lambda/2) M (w qdot).
+  const R ic = (R)1 / (R)P.c, dt = (R)P.dt;
+  const R dT = m.T - (R)P.T0;
+  const R m1 = g[1] - g[3], m2 = g[2] - g[4];
+  const R m3 = -(R)4 * g[0] + ((g[1] + g[2]) + (g[3] + g[4]));
+  const R m4 = (g[1] + g[3]) - (g[2] + g[4]);
+  const R sT = (R)P.omegaT;
+  const R d0 = -dt * m.qd;
+  const R d1 = sT * (m1 - m.T * m.ux * ic);
+  const R d2 = sT * (m2 - m.T * m.uy * ic);
+  // e-moment: rate 1/dt, equilibrium -(2/3) dT, source -(2/3) qdot with factor 1/2
+  const R d3 = (m3 + (R)(2.0 / 3.0) * dT) - (R)0.5 * dt * (-(R)(2.0 / 3.0) * m.qd);
+  const R d4 = m4;
+  const R a0 = d0 * (R)0.2, a1 = d1 * (R)0.5, a2 = d2 * (R)0.5, a3 = d3 * (R)0.05, a4 = d4 * (R)0.25;
+  g[0] -= a0 - (R)4 * a3;
+  g[1] -= a0 + a1 + a3 + a4;
+  g[2] -= a0 + a2 + a3 - a4;
+  g[3] -= a0 - a1 + a3 + a4;
+  g[4] -= a0 - a2 + a3 - a4;
+}
+
+template <typename R, int FLOW, int TH>
+__device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R f[9], R g[5]) {
+  if (FLOW == FLOW_BGK) collide_bgk9<R>(P, m, f);
+  if (FLOW == FLOW_MRT) collide_mrt9<R>(P, m, f);
+  if (TH == TH_BGK) collide_bgk5<R>(P, m, g);
+  if (TH == TH_MRT) collide_mrt5<R>(P, m, g);
+}
+
+// ----------------------------------------------------------------------------
+// Kernels
+// ----------------------------------------------------------------------------
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256) k_step(const SpParams P) {
+  typedef typename Prec<PREC>::S S;
+  typedef typename Prec<PREC>::R R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.nx || j >= P.ny) return;
+  const long long n = (long long)j * P.pitch + i;
+  const S *src = (const S *)P.src;
+  S *dst = (S *)P.dst;
+  const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
+  R f[9], g[5];
+  if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
+  if (TH != TH_NONE) pull_g<S, R>(P, src, i, j, interior, g);
+  Macro<R> m;
+  load_sources<S, R>(P, n, m);
+  moments<R, FLOW, TH>(P, f, g, m);
+  collide<R, FLOW, TH>(P, m, f, g);
+  if (FLOW != FLOW_NONE) {
+#pragma unroll
+    for (int q = 0; q < 9; q++) dst[q * P.plane + n] = (S)f[q];
+  }
+  if (TH != TH_NONE) {
+    S *gd = dst + (long long)P.gbase * P.plane;
+#pragma unroll
+    for (int q = 0; q < 5; q++) gd[q * P.plane + n] = (S)g[q];
+  }
+}
+
+// Equilibrium from fields (Eqs. feq_geral, geq_geral): the pre-collision state of
+// time 0, stored in deviation form; the first step collides it in place.
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256) k_init(const SpParams P, const double *A, const double *UX,
+                                               const double *UY, const double *B) {
+  typedef typename Prec<PREC>::S S;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.nx || j >= P.ny) return;
+  const long long n = (long long)j * P.pitch + i;
+  const int k = j * P.nx + i;
+  S *dst = (S *)P.dst;
+  const double rho = A ? A[k] : P.rho0;
+  const double u0 = (FLOW != FLOW_NONE) ? (UX ? UX[k] : 0.0) : P.ux_pres;
+  const double v0 = (FLOW != FLOW_NONE) ? (UY ? UY[k] : 0.0) : P.uy_pres;
+  const double T = B ? B[k] : P.T0;
+  const double c = P.c, inv_cs2 = 3.0 / (c * c);
+  if (FLOW != FLOW_NONE) {
+    const double usq = u0 * u0 + v0 * v0;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      double cu = c * (cx9(q) * u0 + cy9(q) * v0);
+      dst[q * P.plane + n] = (S)(w9<double>(q) * ((rho - P.rho0) + rho * (cu * inv_cs2 + 0.5 * cu * cu * inv_cs2 * inv_cs2 - 0.5 * usq * inv_cs2)));
+    }
+  }
+  if (TH != TH_NONE) {
+    S *gd = dst + (long long)P.gbase * P.plane;
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      double cu = c * (cx5(q) * u0 + cy5(q) * v0);
+      gd[q * P.plane + n] = (S)(w5<double>(q) * ((T - P.T0) + T * cu * inv_cs2));
+    }
+  }
+}
+
+// Macroscopic fields of the current time: pull (with boundary rules) + moments.
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256) k_moments(const SpParams P, unsigned mask, double *out) {
+  typedef typename Prec<PREC>::S S;
+  typedef typename Prec<PREC>::R R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.nx || j >= P.ny) return;
+  const long long n = (long long)j * P.pitch + i;
+  const S *src = (const S *)P.src;
+  const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
+  R f[9], g[5];
+  if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
+  if (TH != TH_NONE) pull_g<S, R>(P, src, i, j, interior, g);
+  Macro<R> m;
+  load_sources<S, R>(P, n, m);
+  moments<R, FLOW, TH>(P, f, g, m);
+  const long long N = (long long)P.nx * P.ny;
+  const long long k = (long long)j * P.nx + i;
+  int slot = 0;
+  // rho, ux, uy, T, p (= c_s^2 (rho - rho0)), phi (0)
+  if (mask & 1u) out[(slot++) * N + k] = (double)P.rho0 + (double)m.drho;
+  if (mask & 2u) out[(slot++) * N + k] = (double)m.ux;
+  if (mask & 4u) out[(slot++) * N + k] = (double)m.uy;
+  if (mask & 8u) out[(slot++) * N + k] = (TH != TH_NONE) ? (double)P.T0 + (double)m.sumg + 0.5 * P.dt * (double)m.qd : 0.0;
+  if (mask & 16u) out[(slot++) * N + k] = P.cs2 * (double)m.drho;
+  if (mask & 32u) out[(slot++) * N + k] = 0.0;
+}
+
+// Deterministic integrals: per-block FP64 partials in a fixed shuffle-tree order.
+__device__ __forceinline__ void block_reduce4(double v[4], double *out) {
+  // v[0], v[1], v[3] summed; v[2] max
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+  }
+  __shared__ double sh[8][4];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) {
+    sh[warp][0] = v[0]; sh[warp][1] = v[1]; sh[warp][2] = v[2]; sh[warp][3] = v[3];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0, mx = 0, cnt = 0;
+    for (int w = 0; w < nw; w++) { a += sh[w][0]; b += sh[w][1]; mx = fmax(mx, sh[w][2]); cnt += sh[w][3]; }
+    out[0] = a; out[1] = b; out[2] = mx; out[3] = cnt;
+  }
+}
+
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *partials) {
+  typedef typename Prec<PREC>::S S;
+  typedef typename Prec<PREC>::R R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < P.nx && j < P.ny) {
+    const long long n = (long long)j * P.pitch + i;
+    const S *src = (const S *)P.src;
+    const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
+    R f[9], g[5];
+    if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
+    if (TH != TH_NONE) pull_g<S, R>(P, src, i, j, interior, g);
+    Macro<R> m;
+    load_sources<S, R>(P, n, m);
+    moments<R, FLOW, TH>(P, f, g, m);
+    const double rho = P.rho0 + (double)m.drho;
+    const double ux = (double)m.ux, uy = (double)m.uy;
+    const double umag = sqrt(ux * ux + uy * uy);
+    const double T = (TH != TH_NONE) ? (double)m.T : 0.0;
+    v[0] = rho * P.dx * P.dx;
+    v[2] = umag;
+    const bool bad = !isfinite(rho) || !isfinite(umag) || !isfinite(T) || umag >= P.c;
+    v[3] = bad ? 1.0 : 0.0;
+    if (bad) v[2] = 0.0;
+  }
+  block_reduce4(v, partials + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+__global__ void k_final_reduce(const double *partials, int nb, double *out4) {
+  // one warp; lane l sums blocks l, l+32, ... then a fixed shuffle tree
+  const int lane = threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = lane; b < nb; b += 32) {
+    v[0] += partials[4 * b + 0];
+    v[1] += partials[4 * b + 1];
+    v[2] = fmax(v[2], partials[4 * b + 2]);
+    v[3] += partials[4 * b + 3];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
+    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+  }
+  if (lane == 0) { out4[0] = v[0]; out4[1] = v[1]; out4[2] = v[2]; out4[3] = v[3]; }
+}
+
+// ----------------------------------------------------------------------------
+// Dispatch
+// ----------------------------------------------------------------------------
+static dim3 grid_for(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
+
+#define LBM_SP_DISPATCH(PREC_, FLOW_, TH_, CALL)                                      \
+  do {                                                                                \
+    if (PREC_ == 0) {                                                                 \
+      if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(0, FLOW_BGK, TH_NONE); }        \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK) { CALL(0, FLOW_BGK, TH_BGK); }     \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT) { CALL(0, FLOW_BGK, TH_MRT); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_NONE) { CALL(0, FLOW_MRT, TH_NONE); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK) { CALL(0, FLOW_MRT, TH_BGK); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(0, FLOW_MRT, TH_MRT); }     \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(0, FLOW_NONE, TH_BGK); }   \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(0, FLOW_NONE, TH_MRT); }   \
+      else return cudaErrorInvalidValue;                                              \
+    } else {                                                                          \
+      if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(1, FLOW_BGK, TH_NONE); }        \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK) { CALL(1, FLOW_BGK, TH_BGK); }     \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT) { CALL(1, FLOW_BGK, TH_MRT); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_NONE) { CALL(1, FLOW_MRT, TH_NONE); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK) { CALL(1, FLOW_MRT, TH_BGK); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(1, FLOW_MRT, TH_MRT); }     \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(1, FLOW_NONE, TH_BGK); }   \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(1, FLOW_NONE, TH_MRT); }   \
+      else return cudaErrorInvalidValue;                                              \
+    }                                                                                 \
+  } while (0)
+
+cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
+  dim3 grid = grid_for(P.nx, P.ny, block);
+#define CALL_STEP(A, B, C) k_step<A, B, C><<<grid, block, 0, s>>>(P)
+  LBM_SP_DISPATCH(prec, flow, th, CALL_STEP);
+#undef CALL_STEP
+  return cudaGetLastError();
+}
+
+cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double *a, const double *ux,
+                    const double *uy, const double *b, dim3 block, cudaStream_t s) {
+  dim3 grid = grid_for(P.nx, P.ny, block);
+#define CALL_INIT(A, B, C) k_init<A, B, C><<<grid, block, 0, s>>>(P, a, ux, uy, b)
+  LBM_SP_DISPATCH(prec, flow, th, CALL_INIT);
+#undef CALL_INIT
+  return cudaGetLastError();
+}
+
+cudaError_t sp_moments(const SpParams &P, int prec, int flow, int th, unsigned mask, double *out,
+                       cudaStream_t s) {
+  dim3 block(64, 4);
+  dim3 grid = grid_for(P.nx, P.ny, block);
+#define CALL_MOM(A, B, C) k_moments<A, B, C><<<grid, block, 0, s>>>(P, mask, out)
+  LBM_SP_DISPATCH(prec, flow, th, CALL_MOM);
+#undef CALL_MOM
+  return cudaGetLastError();
+}
+
+static const dim3 kRedBlock(64, 4);
+
+int sp_integral_blocks(int nx, int ny) {
+  dim3 g = grid_for(nx, ny, kRedBlock);
+  return (int)(g.x * g.y);
+}
+
+cudaError_t sp_integrals(const SpParams &P, int prec, int flow, int th, double *partials, int max_blocks,
+                         double *out4, cudaStream_t s) {
+  dim3 grid = grid_for(P.nx, P.ny, kRedBlock);
+  if ((int)(grid.x * grid.y) > max_blocks) return cudaErrorInvalidValue;
+#define CALL_INT(A, B, C) k_integrals<A, B, C><<<grid, kRedBlock, 0, s>>>(P, partials)
+  LBM_SP_DISPATCH(prec, flow, th, CALL_INT);
+#undef CALL_INT
+  k_final_reduce<<<1, 32, 0, s>>>(partials, (int)(grid.x * grid.y), out4);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Layout helpers
+// ----------------------------------------------------------------------------
+template <typename S>
+__global__ void k_to_storage(const double *in, S *out, int nx, int ny, int pitch, int nplanes,
+                             long long plane, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  for (int p = 0; p < nplanes; p++)
+    out[p * plane + (long long)j * pitch + i] = (S)(scale * in[(long long)p * nx * ny + (long long)j * nx + i]);
+}
+
+cudaError_t to_storage(const double *in, void *out, int nx, int ny, int pitch, int nplanes, long long plane,
+                       int prec, double scale, cudaStream_t s) {
+  dim3 b(64, 4), g = grid_for(nx, ny, b);
+  if (prec == 0) k_to_storage<double><<<g, b, 0, s>>>(in, (double *)out, nx, ny, pitch, nplanes, plane, scale);
+  else k_to_storage<float><<<g, b, 0, s>>>(in, (float *)out, nx, ny, pitch, nplanes, plane, scale);
+  return cudaGetLastError();
+}
+
+template <typename S>
+__global__ void k_pack(const S *state, S *packed, int nx, int ny, int pitch, int nq, long long plane, int unpack) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  for (int q = 0; q < nq; q++) {
+    long long a = q * plane + (long long)j * pitch + i;
+    long long b = ((long long)q * ny + j) * nx + i;
+    if (unpack) ((S *)state)[a] = packed[b];
+    else packed[b] = state[a];
+  }
+}
+
+cudaError_t pack_state(const void *state, void *packed, int nx, int ny, int pitch, int nq, long long plane,
+                       int elem, int unpack, cudaStream_t s) {
+  dim3 b(64, 4), g = grid_for(nx, ny, b);
+  if (elem == 8) k_pack<double><<<g, b, 0, s>>>((const double *)state, (double *)packed, nx, ny, pitch, nq, plane, unpack);
+  else k_pack<float><<<g, b, 0, s>>>((const float *)state, (float *)packed, nx, ny, pitch, nq, plane, unpack);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmk

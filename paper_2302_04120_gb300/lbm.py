@@ -1,0 +1,337 @@
+"""Thin Python binding of the C ABI in ``include/lbm.h`` (ctypes).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels of
+``liblbm.so``.  Functions carry the C names; ``Solver`` wraps a handle for
+convenience.  Host arrays are numpy float64 arrays of shape (ny, nx); device
+arrays may be torch CUDA float64 tensors (their data pointer is passed with
+``on_device=1``).  There is no CPU fallback: if the library is missing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm.so")
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_UNSTABLE_TAU, LBM_ERR_NOMEM = 0, -1, -2, -3
+LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6, -7
+LBM_NONE, LBM_D2Q5, LBM_D2Q9 = 0, 5, 9
+LBM_BGK, LBM_MRT = 0, 1
+LBM_FP64, LBM_FP32DEV = 0, 1
+LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE = 0, 1, 2, 3
+LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW = 0, 1, 2, 3
+LBM_RHO, LBM_UX, LBM_UY, LBM_T, LBM_P, LBM_PHI = 1, 2, 4, 8, 16, 32
+_MOMENT_BITS = [("rho", 1), ("ux", 2), ("uy", 4), ("T", 8), ("p", 16), ("phi", 32)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lbm status {status}: {msg}")
+        self.status = status
+
+
+class lbm_params(C.Structure):
+    _fields_ = [
+        ("flow", C.c_int), ("flow_op", C.c_int), ("thermal", C.c_int), ("thermal_op", C.c_int),
+        ("phase", C.c_int), ("z_op", C.c_int), ("nu_rule", C.c_int), ("literal", C.c_int),
+        ("precision", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+        ("dx", C.c_double), ("dt", C.c_double),
+        ("rho0", C.c_double), ("nu", C.c_double), ("cp", C.c_double), ("k", C.c_double),
+        ("T0", C.c_double),
+        ("rho_l", C.c_double), ("rho_g", C.c_double), ("nu_l", C.c_double), ("nu_g", C.c_double),
+        ("sigma", C.c_double), ("W", C.c_double), ("mobility", C.c_double),
+        ("omega_e_dt", C.c_double), ("omega_eps_dt", C.c_double),
+        ("body_force", C.c_double * 2), ("u_prescribed", C.c_double * 2),
+    ]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load liblbm.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2302_04120_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        L.lbm_params_default.argtypes = [C.POINTER(lbm_params)]
+        L.lbm_params_default.restype = None
+        L.lbm_create.argtypes = [C.POINTER(lbm_params), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.lbm_set_bc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_int, C.c_void_p]
+        L.lbm_set_source.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.lbm_init_fields.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.lbm_step.argtypes = [C.c_void_p, C.c_long]
+        L.lbm_steps_done.argtypes = [C.c_void_p]
+        L.lbm_steps_done.restype = C.c_long
+        L.lbm_moments.argtypes = [C.c_void_p, C.c_uint, C.c_void_p, C.c_int]
+        L.lbm_integrals.argtypes = [C.c_void_p, _dp]
+        L.lbm_check.argtypes = [C.c_void_p]
+        L.lbm_state_bytes.argtypes = [C.c_void_p]
+        L.lbm_state_bytes.restype = C.c_size_t
+        L.lbm_get_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.lbm_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+        L.lbm_constants.argtypes = [C.c_void_p, _dp]
+        L.lbm_synchronize.argtypes = [C.c_void_p]
+        L.lbm_last_error.argtypes = [C.c_void_p]
+        L.lbm_last_error.restype = C.c_char_p
+        L.lbm_destroy.argtypes = [C.c_void_p]
+        L.lbm_destroy.restype = None
+        for name in ("lbm_create", "lbm_set_bc", "lbm_set_source", "lbm_init_fields", "lbm_step",
+                     "lbm_moments", "lbm_integrals", "lbm_check", "lbm_get_state", "lbm_set_state",
+                     "lbm_constants", "lbm_synchronize"):
+            getattr(L, name).restype = C.c_int
+        _extra_signatures(L)
+        _lib = L
+    return _lib
+
+
+def _extra_signatures(L):
+    """Signatures of the batched and adjoint entry points (when built)."""
+    if hasattr(L, "lbm_batch_create"):
+        L.lbm_batch_create.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.lbm_batch_create.restype = C.c_int
+
+
+def _check(h, st):
+    if st != LBM_OK:
+        msg = lib().lbm_last_error(h)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+def _host(a, n=None):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and arr.size != n:
+        raise ValueError(f"expected {n} values, got {arr.size}")
+    return arr, arr.ctypes.data_as(C.c_void_p)
+
+
+def _ptr(a, n=None):
+    """(keepalive, pointer, on_device) for a numpy array or a torch CUDA tensor."""
+    if a is None:
+        return None, None, 0
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device arrays must be contiguous float64 tensors")
+        if n is not None and a.numel() != n:
+            raise ValueError(f"expected {n} values, got {a.numel()}")
+        return a, C.c_void_p(a.data_ptr()), 1
+    arr, p = _host(a, n)
+    return arr, p, 0
+
+
+# --- C-named functions ------------------------------------------------------
+def lbm_params_default():
+    p = lbm_params()
+    lib().lbm_params_default(C.byref(p))
+    return p
+
+
+def lbm_create(params: lbm_params, stream=None):
+    h = C.c_void_p()
+    st = lib().lbm_create(C.byref(params), stream, C.byref(h))
+    _check(None, st)
+    return h
+
+
+def lbm_set_bc(h, side, kind, uw=None, rho_w=0.0, tkind=LBM_TBC_NONE, tw=None):
+    a, pa = _host(uw)
+    b, pb = _host(tw)
+    _check(h, lib().lbm_set_bc(h, side, kind, pa, float(rho_w), tkind, pb))
+
+
+def lbm_set_source(h, q3=None, force=None, n=None):
+    a, pa, da = _ptr(q3, n)
+    b, pb, db = _ptr(force, None if n is None else 2 * n)
+    on_dev = da or db
+    if (q3 is not None and force is not None) and da != db:
+        raise ValueError("q3 and force must both be host or both be device arrays")
+    _check(h, lib().lbm_set_source(h, pa, pb, on_dev))
+
+
+def lbm_init_fields(h, a=None, ux=None, uy=None, b=None, n=None):
+    keep = [_ptr(x, n) for x in (a, ux, uy, b)]
+    devs = {k[2] for k in keep if k[0] is not None}
+    if len(devs) > 1:
+        raise ValueError("fields must all be host or all be device arrays")
+    on_dev = devs.pop() if devs else 0
+    _check(h, lib().lbm_init_fields(h, keep[0][1], keep[1][1], keep[2][1], keep[3][1], on_dev))
+
+
+def lbm_step(h, n):
+    _check(h, lib().lbm_step(h, int(n)))
+
+
+def lbm_steps_done(h):
+    return lib().lbm_steps_done(h)
+
+
+def lbm_moments(h, mask, out, on_device=None):
+    if hasattr(out, "is_cuda") and out.is_cuda:
+        _check(h, lib().lbm_moments(h, mask, C.c_void_p(out.data_ptr()), 1))
+    else:
+        assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+        _check(h, lib().lbm_moments(h, mask, out.ctypes.data_as(C.c_void_p), 0))
+    return out
+
+
+def lbm_integrals(h):
+    out = (C.c_double * 4)()
+    _check(h, lib().lbm_integrals(h, out))
+    return [out[i] for i in range(4)]
+
+
+def lbm_check(h):
+    return lib().lbm_check(h)
+
+
+def lbm_state_bytes(h):
+    return lib().lbm_state_bytes(h)
+
+
+def lbm_get_state(h):
+    nb = lbm_state_bytes(h)
+    buf = np.empty(nb, dtype=np.uint8)
+    _check(h, lib().lbm_get_state(h, buf.ctypes.data_as(C.c_void_p), nb))
+    return buf
+
+
+def lbm_set_state(h, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(h, lib().lbm_set_state(h, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+
+def lbm_constants(h):
+    out = (C.c_double * 5)()
+    _check(h, lib().lbm_constants(h, out))
+    return dict(c=out[0], cs2=out[1], tau=out[2], tauT=out[3], tauphi=out[4])
+
+
+def lbm_synchronize(h):
+    _check(h, lib().lbm_synchronize(h))
+
+
+def lbm_last_error(h=None):
+    m = lib().lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def lbm_destroy(h):
+    lib().lbm_destroy(h)
+
+
+# --- convenience wrapper -----------------------------------------------------
+_PARAM_NAMES = [f[0] for f in lbm_params._fields_]
+
+
+def make_params(d: dict, precision=LBM_FP64) -> lbm_params:
+    """lbm_params from an SI dict (workload keys; Fb -> body_force)."""
+    p = lbm_params_default()
+    for k, v in d.items():
+        if k == "Fb":
+            p.body_force[0], p.body_force[1] = float(v[0]), float(v[1])
+        elif k == "u_prescribed":
+            p.u_prescribed[0], p.u_prescribed[1] = float(v[0]), float(v[1])
+        elif k in _PARAM_NAMES and k not in ("body_force",):
+            setattr(p, k, v)
+    if d.get("flow", 9) == 0:
+        p.flow = LBM_NONE
+    p.precision = precision
+    return p
+
+
+class Solver:
+    """One solve on the GPU.  ``params`` is an SI dict as produced by
+    ``paper_2302_04120_gb300.workloads``."""
+
+    def __init__(self, params: dict, precision=LBM_FP64, stream=None):
+        self.params = dict(params)
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self.n = self.nx * self.ny
+        self.h = lbm_create(make_params(params, precision), stream)
+        self.precision = precision
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_bc(self, side, kind, uw=None, rho_w=None, tkind=LBM_TBC_NONE, tw=None):
+        rw = self.params.get("rho0", 1000.0) if rho_w is None else rho_w
+        lbm_set_bc(self.h, side, kind, uw, rw, tkind, tw)
+
+    def apply_workload(self, w):
+        for bc in w["bcs"]:
+            self.set_bc(*bc)
+        if w.get("q3") is not None:
+            lbm_set_source(self.h, q3=w["q3"], n=self.n)
+        init = w.get("init") or {}
+        self.init(**init)
+
+    def set_source(self, q3=None, force=None):
+        lbm_set_source(self.h, q3, force, n=self.n)
+
+    def init(self, a=None, ux=None, uy=None, b=None):
+        lbm_init_fields(self.h, a, ux, uy, b, n=self.n)
+
+    def step(self, n):
+        lbm_step(self.h, n)
+
+    @property
+    def steps(self):
+        return lbm_steps_done(self.h)
+
+    def moments(self, mask=63):
+        sel = [name for name, bit in _MOMENT_BITS if mask & bit]
+        out = np.empty((len(sel), self.ny, self.nx))
+        lbm_moments(self.h, mask, out)
+        return {k: out[i] for i, k in enumerate(sel)}
+
+    def integrals(self):
+        return lbm_integrals(self.h)
+
+    def check(self):
+        return lbm_check(self.h)
+
+    def constants(self):
+        return lbm_constants(self.h)
+
+    def get_state(self):
+        return lbm_get_state(self.h)
+
+    def set_state(self, buf):
+        lbm_set_state(self.h, buf)
+
+    def state_arrays(self):
+        """Post-collision populations (q, ny, nx) as float64, deviations added back
+        (f = stored + w_i rho0, g = stored + w_i T0) for single-phase solves."""
+        raw = self.get_state()
+        dt = np.float64 if self.precision == LBM_FP64 else np.float32
+        a = raw.view(dt).astype(np.float64).reshape(-1, self.ny, self.nx)
+        p = self.params
+        if p.get("phase", 0):
+            return dict(z=a[0:9], h=a[9:14], phiu=a[14:16])
+        out = {}
+        k = 0
+        if p.get("flow", 9):
+            w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+            out["f"] = a[0:9] + w9[:, None, None] * p.get("rho0", 1000.0)
+            k = 9
+        if p.get("thermal", 0):
+            w5 = np.array([1 / 3] + [1 / 6] * 4)
+            out["g"] = a[k:k + 5] + w5[:, None, None] * p.get("T0", 300.0)
+        return out

@@ -1,0 +1,203 @@
+"""GPU (CUDA, sm_103a) vs FP64 CPU oracle: single-phase hot path.
+
+Tolerances (stated by the method's contract):
+  FP64 path:        1e-12 relative max-norm on u, T - T_in and on the populations;
+  FP32-deviation:   1e-5 relative L2 on u and T - T_in.
+Populations are compared element by element after the same number of steps
+(GPU post-collision buffer vs the oracle's last post-collision values)."""
+import numpy as np
+import pytest
+
+from _helpers import W5, W9, rel_l2, rel_max, run_gpu, run_oracle
+from paper_2302_04120_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+lbm = pytest.importorskip("paper_2302_04120_gb300.lbm")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_04120_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+FP64, FP32 = 0, 1
+
+
+def _compare_fields(o, s, T_in=None, tol=1e-12, norm=rel_max, prec=FP64):
+    mo = o.moments()
+    mg = s.moments()
+    out = {}
+    out["ux"] = norm(mg["ux"], mo["ux"], np.hypot(mo["ux"], mo["uy"]))
+    out["uy"] = norm(mg["uy"], mo["uy"], np.hypot(mo["ux"], mo["uy"]))
+    if T_in is not None:
+        out["T"] = norm(mg["T"] - T_in, mo["T"] - T_in)
+    for k, v in out.items():
+        assert v < tol, (k, v, out)
+    return out
+
+
+def _compare_populations(o, s, w, tol=1e-12):
+    st = s.state_arrays()
+    p = w["params"]
+    if p.get("flow", 9):
+        fo = o.dist("f", post=True)
+        dev = fo - W9[:, None, None] * p["rho0"]
+        assert rel_max(st["f"] - W9[:, None, None] * p["rho0"], dev) < tol
+    if p.get("thermal", 0):
+        go = o.dist("g", post=True)
+        dev = go - W5[:, None, None] * p["T0"]
+        assert rel_max(st["g"] - W5[:, None, None] * p["T0"], dev) < tol
+
+
+# ---------------------------------------------------------------------------
+def test_poiseuille_workload_full():
+    """64 x 33 D2Q9 BGK channel, 20000 steps, FP64: GPU = oracle to 1e-12 and the
+    steady profile matches the exact discrete half-way bounce-back solution."""
+    w = wl.poiseuille()
+    o = run_oracle(w)
+    s = run_gpu(w, FP64)
+    _compare_fields(o, s)
+    _compare_populations(o, s, w)
+    u = s.moments()["ux"][:, 0]
+    p = w["params"]
+    dx, nu, rho, F = p["dx"], p["nu"], p["rho0"], w["Fb"]
+    y = (np.arange(p["ny"]) + 0.5) * dx
+    H = p["ny"] * dx
+    ex = F / (2 * rho * nu) * y * (H - y) + F * dx * dx / (rho * nu) * (16 * 0.09 - 3) / 24
+    assert np.max(np.abs(u - ex)) / np.max(ex) < 1e-7   # slowest mode decayed to ~1e-8
+
+
+@pytest.mark.parametrize("flow_op,thermal_op", [(0, 0), (1, 1), (1, 0), (0, 1)])
+def test_channel_all_boundaries_fp64(flow_op, thermal_op):
+    """Forced-convection channel (BB-velocity inlet, anti-BB outlet, heat-flux walls,
+    inlet temperature, thermal outflow) on a ragged 100 x 42 grid (several 64 x 4
+    tiles plus partial ones), 300 steps, FP64."""
+    w = wl.channel(nx=100, ny=42, steps=300, Re=100 * 42 / 256, flow_op=flow_op, thermal_op=thermal_op)
+    o = run_oracle(w)
+    s = run_gpu(w, FP64)
+    _compare_fields(o, s, T_in=w["T_in"])
+    _compare_populations(o, s, w)
+
+
+def test_channel_fp32_deviation():
+    """Same channel in FP32-deviation storage: 1e-5 relative L2 on u and T - T_in
+    after 2000 steps."""
+    w = wl.channel(nx=100, ny=42, steps=2000, Re=100 * 42 / 256)
+    o = run_oracle(w)
+    s = run_gpu(w, FP32)
+    _compare_fields(o, s, T_in=w["T_in"], tol=1e-5, norm=rel_l2)
+
+
+@pytest.mark.parametrize("prec,steps,tol", [(FP64, 12, 1e-12), (FP32, 12, 1e-5)])
+def test_channel_full_size(prec, steps, tol):
+    """The 2048 x 256 forced-convection workload in the launch configuration the
+    benchmark times, a few steps (the oracle needs seconds per step at this size)."""
+    w = wl.channel(steps=steps)
+    o = run_oracle(w)
+    s = run_gpu(w, prec)
+    _compare_fields(o, s, T_in=w["T_in"], tol=tol, norm=rel_max if prec == FP64 else rel_l2)
+    if prec == FP64:
+        _compare_populations(o, s, w)
+
+
+def test_sources_and_force_fields():
+    """Per-cell heat source q''' and force field through lbm_set_source."""
+    w = wl.channel(nx=70, ny=36, steps=150, Re=100 * 36 / 256)
+    rng = np.random.default_rng(11)
+    q3 = 1e7 * rng.standard_normal((36, 70))
+    force = 50.0 * rng.standard_normal((2, 36, 70))
+    o = run_oracle(w, q3=q3, force=force)
+    s = run_gpu(w, FP64, q3=q3, force=force)
+    _compare_fields(o, s, T_in=w["T_in"])
+    _compare_populations(o, s, w)
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_thermal_only_gaussian(op):
+    """flow = NONE: D2Q5 advection-diffusion of a Gaussian on a periodic 64 x 48
+    box with a prescribed velocity."""
+    nx, ny, dx = 64, 48, 1e-5
+    alpha = 0.6 / (1000 * 4180)
+    dt = 0.3 * dx * dx / (3 * alpha)
+    u = (2e-4, -1e-4)
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y)
+    T0 = 300 + 10 * np.exp(-((X - 3e-4) ** 2 + (Y - 2.4e-4) ** 2) / (2 * (6e-5) ** 2))
+    params = dict(nx=nx, ny=ny, flow=0, thermal=5, thermal_op=op, dx=dx, dt=dt, rho0=1000.0, cp=4180.0,
+                  k=0.6, T0=300.0, u_prescribed=u)
+    w = dict(params=params, bcs=[], init=dict(a=None, ux=np.full((ny, nx), u[0]), uy=np.full((ny, nx), u[1]), b=T0),
+             steps=200)
+    o = run_oracle(w)
+    s = run_gpu(w, FP64)
+    mo, mg = o.moments(), s.moments()
+    assert rel_max(mg["T"] - 300, mo["T"] - 300) < 1e-12
+    _compare_populations(o, s, w)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 2), (2, 1), (5, 3)])
+def test_tiny_and_degenerate_grids(nx, ny):
+    """Degenerate sizes: a single periodic node, and grids smaller than one tile
+    with walls (every node is a boundary node)."""
+    rng = np.random.default_rng(nx * 10 + ny)
+    dx, nu = 1e-4, 1e-6
+    dt = 0.3 * dx * dx / (3 * nu)
+    p = dict(nx=nx, ny=ny, flow=9, flow_op=1, thermal=5, thermal_op=1, dx=dx, dt=dt, rho0=1000.0, nu=nu,
+             cp=4180.0, k=0.6, T0=300.0, Fb=(3.0, -1.0))
+    bcs = []
+    if ny > 1:
+        bcs = [(2, 1, np.concatenate([np.full(nx, 1e-4), np.zeros(nx)]), 1000.0, 2, np.full(nx, 310.0)),
+               (3, 1, None, 1000.0, 1, np.full(nx, 1e3))]
+    init = dict(a=1000 + rng.standard_normal((ny, nx)), ux=1e-3 * rng.standard_normal((ny, nx)),
+                uy=1e-3 * rng.standard_normal((ny, nx)), b=300 + rng.standard_normal((ny, nx)))
+    w = dict(params=p, bcs=bcs, init=init, steps=40)
+    o = run_oracle(w)
+    s = run_gpu(w, FP64)
+    _compare_fields(o, s, T_in=300.0)
+    _compare_populations(o, s, w)
+
+
+def test_zero_steps_returns_initial_fields():
+    w = wl.channel(nx=40, ny=12, steps=0, Re=100 * 12 / 256)
+    s = run_gpu(w, FP64, steps=0)
+    m = s.moments()
+    np.testing.assert_allclose(m["T"], w["init"]["b"], rtol=0, atol=1e-12)
+    o = run_oracle(w, steps=0)
+    assert rel_max(m["ux"], o.moments()["ux"]) < 1e-12
+
+
+def test_state_roundtrip_device_moments_and_integrals():
+    """Checkpoint/restart through lbm_get_state/lbm_set_state; moments into a
+    device tensor; FP64 mass integral vs the oracle; a planted NaN is flagged."""
+    import torch
+    w = wl.channel(nx=64, ny=24, steps=100, Re=100 * 24 / 256)
+    s = run_gpu(w, FP64)
+    st = s.get_state()
+    s.step(50)
+    a = s.moments()
+    s.set_state(st)
+    s.step(50)
+    b = s.moments()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    dev = torch.empty((2, 24, 64), dtype=torch.float64, device="cuda")
+    lbm.lbm_moments(s.h, lbm.LBM_UX | lbm.LBM_T, dev)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dev[0].cpu().numpy(), b["ux"])
+    np.testing.assert_array_equal(dev[1].cpu().numpy(), b["T"])
+    o = run_oracle(w, steps=150)
+    mass_o = o.moments()["rho"].sum() * w["params"]["dx"] ** 2
+    ints = s.integrals()
+    assert abs(ints[0] - mass_o) / mass_o < 1e-13
+    assert ints[3] == 0 and s.check() == lbm.LBM_OK
+    bad = st.view(np.float64).copy()
+    bad[5 * 64 * 24 + 7] = np.nan
+    s.set_state(bad.view(np.uint8))
+    assert s.check() == lbm.LBM_ERR_DIVERGED
+    assert "non-finite" in lbm.lbm_last_error(s.h)
