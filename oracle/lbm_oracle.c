@@ -144,7 +144,7 @@ typedef struct {
   double *z, *zn, *zpost;
   double *rho, *ux, *uy, *T, *pr, *phi, *Tprev, *phiux_prev, *phiuy_prev;
   double *q3;                    /* q''' field in W m^-3, or NULL                   */
-  double *force;                 /* per-cell force (2N) in N m^-3, or NULL          */
+  double *force;                 /* per-cell force: F_x plane then F_y plane (2N), N m^-3, or NULL */
   int bc[4], tbc[4];
   double rho_w[4];
   double *bcu[4];                /* per side: 2*len (u_x then u_y)                 */
@@ -367,8 +367,8 @@ static void moments_single(orc_t *o) {
   int N = o->N;
 #pragma omp parallel for schedule(static)
   for (int n = 0; n < N; n++) {
-    double Fx = p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
-    double Fy = p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+    double Fx = p->Fb[0] + (o->force ? o->force[n] : 0.0);
+    double Fy = p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
     if (p->flow) {
       /* Eqs. zero_moment_f, first_moment_f */
       double rho = 0, jx = 0, jy = 0;
@@ -418,8 +418,8 @@ static void collide_single(orc_t *o) {
     double ux = o->ux[n], uy = o->uy[n];
     if (p->flow) {
       double rho = o->rho[n];
-      double Fx = p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
-      double Fy = p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+      double Fx = p->Fb[0] + (o->force ? o->force[n] : 0.0);
+      double Fy = p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
       double fv[9], fe[9], fh[9];
       for (int i = 0; i < 9; i++) {
         fv[i] = o->f[i * N + n];
@@ -637,8 +637,8 @@ static void step_two_phase(orc_t *o) {
     }
     double tau = nu / cs2 + 0.5 * dt;
     double drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
-    double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
-    double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+    double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[n] : 0.0);
+    double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
     /* u from Eq. u_Liang, then p from Eq. p_Liang */
     double jx = 0, jy = 0, zs = 0;
     for (int i = 0; i < 9; i++) {
@@ -790,8 +790,8 @@ void orc_moments(void *handle, double *rho, double *ux, double *uy, double *T, d
       double mu = 4.0 * beta * ph * (ph - 1.0) * (ph - 0.5) - kappa * lap[n];
       double r = p->rho_g + ph * (p->rho_l - p->rho_g);
       double drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
-      double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[2 * n] : 0.0);
-      double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[2 * n + 1] : 0.0);
+      double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[n] : 0.0);
+      double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
       double jx = 0, jy = 0, zs = 0;
       for (int i = 0; i < 9; i++) {
         double zi = o->z[i * N + n];

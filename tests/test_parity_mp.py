@@ -1,8 +1,10 @@
 """GPU vs FP64 CPU oracle: two-phase (Allen-Cahn h on D2Q5 + pressure z on D2Q9).
 
 FP64 path: phi, p - mean(p), u to 1e-12 relative max-norm (u relative to the
-largest spurious speed).  FP32 path (FP64 u/p recovery): phi to 1e-5 relative
-max-norm, Laplace pressure jump within 1 % of the oracle's."""
+largest spurious speed) over 20 steps; beyond that the problem itself amplifies
+rounding (measured with the oracle against itself), so longer runs are checked
+against that envelope.  FP32 path (FP64 u/p recovery): Laplace pressure jump
+within 1 % of the oracle's."""
 import numpy as np
 import pytest
 
@@ -28,45 +30,81 @@ def _dp(m):
     return p[phi < 1e-3].mean() - p[phi > 1 - 1e-3].mean()
 
 
+def _envelope(w, eps):
+    """Oracle-vs-oracle spread after the workload's steps when phi0 is perturbed
+    by eps (relative): the problem's own rounding envelope.  The guarded normal
+    grad(phi)/|grad(phi)| is discontinuous where |grad(phi)| is rounding noise, so
+    rounding-level differences grow to ~1e-8 within ~60 steps (measured)."""
+    res = []
+    for pert in (0.0, eps):
+        w2 = dict(w)
+        phi0 = w["init"]["a"] * (1 + pert * np.random.default_rng(0).standard_normal(w["init"]["a"].shape))
+        w2["init"] = dict(w["init"], a=phi0)
+        res.append(run_oracle(w2).moments())
+    m0, m1 = res
+    sp = np.hypot(m0["ux"], m0["uy"])
+    return dict(phi=rel_max(m1["phi"], m0["phi"]), p=rel_max(m1["p"], m0["p"], m0["p"] - m0["p"].mean()),
+                u=rel_max(m1["ux"], m0["ux"], sp))
+
+
 @pytest.mark.parametrize("z_op", [1, 0])
-def test_bubble_fp64(z_op):
+def test_bubble_fp64_short(z_op):
     """70 x 52 periodic box (ragged against the 32 x 8 tile), bubble R = 12, W = 4,
-    saturated water at 25 C, 300 steps, MRT and BGK z."""
-    w = wl.bubble(n=70, ny=52, R_cells=12.0, W_cells=4.0, steps=300, z_op=z_op)
+    saturated water at 25 C, 20 steps, MRT and BGK z: FP64 parity to 1e-12 on phi,
+    p - mean p and u, and on the post-collision h and z."""
+    w = wl.bubble(n=70, ny=52, R_cells=12.0, W_cells=4.0, steps=20, z_op=z_op)
     o = run_oracle(w)
     s = run_gpu(w, 0)
     mo, mg = o.moments(), s.moments()
     assert rel_max(mg["phi"], mo["phi"]) < 1e-12
-    assert rel_max(mg["p"] - mo["p"].mean(), mo["p"] - mo["p"].mean()) < 1e-12
+    assert rel_max(mg["p"], mo["p"], mo["p"] - mo["p"].mean()) < 1e-12
     sp = np.hypot(mo["ux"], mo["uy"])
-    assert rel_max(mg["ux"], mo["ux"], sp) < 1e-10
-    assert rel_max(mg["uy"], mo["uy"], sp) < 1e-10
+    assert rel_max(mg["ux"], mo["ux"], sp) < 1e-12
+    assert rel_max(mg["uy"], mo["uy"], sp) < 1e-12
     st = s.state_arrays()
     assert rel_max(st["h"], o.dist("h", post=True)) < 1e-12
-    assert rel_max(st["z"], o.dist("z", post=True)) < 1e-10
+    assert rel_max(st["z"], o.dist("z", post=True)) < 1e-12
+
+
+def test_bubble_fp64_long_within_envelope():
+    """300 steps: GPU-vs-oracle differences stay within 10x the oracle's own spread
+    under a 1e-15 perturbation of phi0 (and below 1e-6 outright)."""
+    w = wl.bubble(n=70, ny=52, R_cells=12.0, W_cells=4.0, steps=300)
+    env = _envelope(w, 1e-15)
+    o = run_oracle(w)
+    s = run_gpu(w, 0)
+    mo, mg = o.moments(), s.moments()
+    d_phi = rel_max(mg["phi"], mo["phi"])
+    d_p = rel_max(mg["p"], mo["p"], mo["p"] - mo["p"].mean())
+    d_u = rel_max(mg["ux"], mo["ux"], np.hypot(mo["ux"], mo["uy"]))
+    assert d_phi < max(1e-12, 10 * env["phi"]) and d_phi < 1e-6
+    assert d_p < max(1e-12, 10 * env["p"]) and d_p < 1e-6
+    assert d_u < max(1e-12, 10 * env["u"]) and d_u < 1e-6
 
 
 def test_bubble_body_force_and_tiny():
     """Body force (layered-Poiseuille-like drive on a periodic box) and a grid
-    smaller than one tile."""
-    w = wl.bubble(n=20, ny=6, R_cells=3.0, W_cells=3.0, steps=60)
+    smaller than one tile, 20 steps."""
+    w = wl.bubble(n=20, ny=6, R_cells=3.0, W_cells=3.0, steps=20)
     w["params"]["Fb"] = (2e3, 0.0)
     o = run_oracle(w)
     s = run_gpu(w, 0)
     mo, mg = o.moments(), s.moments()
     assert rel_max(mg["phi"], mo["phi"]) < 1e-12
-    assert rel_max(mg["ux"], mo["ux"], np.hypot(mo["ux"], mo["uy"])) < 1e-10
+    assert rel_max(mg["ux"], mo["ux"], np.hypot(mo["ux"], mo["uy"])) < 1e-12
 
 
 def test_bubble_fp32_mixed():
-    """FP32 storage with FP64 density/velocity/pressure recovery: phi within 1e-5,
-    Laplace jump within 1 % of the FP64 oracle's after 2000 steps; phase sum kept."""
+    """FP32 storage with FP64 density/velocity/pressure recovery, 2000 steps:
+    Laplace jump within 1 % of the FP64 oracle's; phi within 10x the oracle's own
+    spread under an FP32-level (1e-7) perturbation of phi0; sum(phi) to 1e-6."""
     w = wl.bubble(n=64, R_cells=16.0, W_cells=4.0, steps=2000)
+    env = _envelope(w, 1e-7)
     o = run_oracle(w)
     s = run_gpu(w, 1)
     mo, mg = o.moments(), s.moments()
-    assert rel_max(mg["phi"], mo["phi"]) < 1e-5
     assert abs(_dp(mg) - _dp(mo)) / abs(_dp(mo)) < 0.01
+    assert rel_max(mg["phi"], mo["phi"]) < 10 * env["phi"]
     ints = s.integrals()
-    assert abs(ints[1] - mo["phi"].sum()) / mo["phi"].sum() < 1e-5
+    assert abs(ints[1] - mo["phi"].sum()) / mo["phi"].sum() < 1e-6
     assert ints[3] == 0
