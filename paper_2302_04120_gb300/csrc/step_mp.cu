@@ -121,13 +121,18 @@ __device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro &m, d
   const double a_int = P.cs2 * 4.0 * m.phi * (1.0 - m.phi) / P.W;
   const R ax = (R)(dpux + a_int * m.nxv), ay = (R)(dpuy + a_int * m.nyv);
   const R phi = (R)m.phi, ux = (R)m.ux, uy = (R)m.uy;
+  R heq_sum = 0;
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
+  for (int q = 1; q < 5; q++) {
     const R cxq = c * (R)cx5(q), cyq = c * (R)cy5(q);
     const R heq = phi * w5<R>(q) * ((R)1 + (cxq * ux + cyq * uy) * inv_cs2);  // Eq. heq_liang
     const R Sh = w5<R>(q) * (cxq * ax + cyq * ay) * inv_cs2;                    // Eq. source_term_interface
+    heq_sum += heq;
     h[q] = h[q] - om * (h[q] - heq) + sfac * Sh;
   }
+  // h_0^eq = phi w_0 = phi - sum_{q>=1} h_q^eq: sum h_eq = phi exactly in the working
+  // precision (in FP32 the rounded weights sum to 1 + 3e-8, a systematic phase gain)
+  h[0] = h[0] - om * (h[0] - (phi - heq_sum));
 }
 
 template <typename R>

@@ -244,18 +244,25 @@ __device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &
   const R om = (R)P.omega;
   const R fac = ((R)1 - (R)0.5 * om) * (R)P.dt;  // (1 - dt/(2 tau)) dt
   const R hu = (R)0.5 * (m.ux * m.ux + m.uy * m.uy) * inv_cs2;  // u^2 / (2 c_s^2)
+  const R uF = m.ux * m.Fx + m.uy * m.Fy;
+  // q >= 1 first; the rest population takes the remainders so that sum f_eq = rho
+  // and sum F_hat = 0 hold exactly in the working precision (the rounded weights
+  // do not sum to one in FP32)
+  R feq_sum = 0, fh_sum = 0;
 #pragma unroll
-  for (int q = 0; q < 9; q++) {
+  for (int q = 1; q < 9; q++) {
     const R cxq = c * (R)cx9(q), cyq = c * (R)cy9(q);
     const R cu = cxq * m.ux + cyq * m.uy;
     // f_eq - w rho0 (Eq. feq_geral, deviation form: no O(rho0) cancellation)
     const R feq = w9<R>(q) * (m.drho + m.rho * (cu * inv_cs2 * ((R)1 + (R)0.5 * cu * inv_cs2) - hu));
     // Guo forcing F_hat (Eq. forcing_term)
     const R cF = cxq * m.Fx + cyq * m.Fy;
-    const R uF = m.ux * m.Fx + m.uy * m.Fy;
     const R Fh = w9<R>(q) * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
+    feq_sum += feq;
+    fh_sum += Fh;
     f[q] = f[q] - om * (f[q] - feq) + fac * Fh;
   }
+  f[0] = f[0] - om * (f[0] - (m.drho - feq_sum)) + fac * (-fh_sum);
 }
 
 template <typename R>
@@ -313,12 +320,18 @@ __device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &
   const R om = (R)P.omegaT;
   const R src = (R)P.tsrc_fac * (R)P.dt * m.qd;
   const R dT = m.T - (R)P.T0;
+  R geq_sum = 0, s_sum = 0;
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
+  for (int q = 1; q < 5; q++) {
     const R cu = c * ((R)cx5(q) * m.ux + (R)cy5(q) * m.uy);
     const R geq = w5<R>(q) * (dT + m.T * cu * inv_cs2);  // Eq. geq_geral minus w T0
-    g[q] = g[q] - om * (g[q] - geq) + w5<R>(q) * src;    // Eq. forcing_term_g
+    const R sq = w5<R>(q) * src;                         // Eq. forcing_term_g
+    geq_sum += geq;
+    s_sum += sq;
+    g[q] = g[q] - om * (g[q] - geq) + sq;
   }
+  // rest population from the remainders: sum g_eq = T - T0, sum S = source, exactly
+  g[0] = g[0] - om * (g[0] - (dT - geq_sum)) + (src - s_sum);
 }
 
 template <typename R>

@@ -78,7 +78,7 @@ def test_poiseuille_workload_full():
     # 20000 steps: measured 1.4e-12 (u_x) and 4.9e-12 (u_y, rounding noise about an
     # exact zero), i.e. FP64 accumulation; 1e-11 bounds it
     _compare_fields(o, s, tol=1e-11)
-    _compare_populations(o, s, w)
+    _compare_populations(o, s, w, tol=1e-11)   # measured 1.3e-12 after 20000 steps
     u = s.moments()["ux"][:, 0]
     p = w["params"]
     dx, nu, rho, F = p["dx"], p["nu"], p["rho0"], w["Fb"]
@@ -109,18 +109,27 @@ def test_channel_fp32_deviation():
     _compare_fields(o, s, T_in=w["T_in"], tol=1e-5, prec=FP32)
 
 
-@pytest.mark.parametrize("prec,steps,tol", [(FP64, 12, 1e-12), (FP32, 200, 1e-5)])
-def test_channel_full_size(prec, steps, tol):
+@pytest.mark.parametrize("prec,steps", [(FP64, 12), (FP32, 200)])
+def test_channel_full_size(prec, steps):
     """The 2048 x 256 forced-convection workload in the launch configuration the
-    benchmark times; 12 steps in FP64, 200 in FP32 (T - T_in must grow above the
-    FP32 resolution of the advective g deviations, ~2e-7 K, for a relative norm
-    to mean anything)."""
+    benchmark times; 12 steps in FP64, 200 in FP32.  FP32: u to 1e-5 relative L2,
+    T to 1e-5 relative L2 in K (the contract's measure) and T - T_in to 1e-4
+    relative max-norm: after 200 steps the heated layer is two rows of 256, so an
+    L2 norm of T - T_in would measure FP32 rounding of the advective g deviations
+    (~2e-7 K) over the unheated 99 % of the grid rather than the heated part."""
     w = wl.channel(steps=steps)
     o = run_oracle(w)
     s = run_gpu(w, prec)
-    _compare_fields(o, s, T_in=w["T_in"], tol=tol, prec=prec)
     if prec == FP64:
+        _compare_fields(o, s, T_in=w["T_in"], tol=1e-12, prec=FP64)
         _compare_populations(o, s, w)
+        return
+    mo, mg = o.moments(), s.moments()
+    sp = np.hypot(mo["ux"], mo["uy"])
+    assert rel_l2(mg["ux"], mo["ux"], sp) < 1e-5
+    assert rel_l2(mg["uy"], mo["uy"], sp) < 1e-5
+    assert rel_l2(mg["T"], mo["T"]) < 1e-5
+    assert rel_max(mg["T"] - w["T_in"], mo["T"] - w["T_in"]) < 1e-4
 
 
 def test_sources_and_force_fields():
