@@ -226,6 +226,42 @@ const char *lbm_last_error(lbm_t h);
 /* Free the device state.  NULL is ignored. */
 void lbm_destroy(lbm_t h);
 
+/*
+ * Allocation-free integrals over macroscopic fields the caller already holds on
+ * the device.  The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc (code that runs inside a memory pool or arena owning the
+ * whole device, under a framework allocator that forbids foreign allocations, or
+ * where an allocation's implicit device synchronisation is not allowed).
+ *
+ * Computes the same four values as lbm_integrals, with the same deterministic
+ * two-stage FP64 reduction:
+ *   out4[0] = sum rho dx^2, out4[1] = sum phi (0 when phi is NULL),
+ *   out4[2] = max |u| over finite cells, out4[3] = number of cells with a
+ *   non-finite value or |u| >= c.
+ * rho, ux, uy (and phi, or NULL): device arrays of nx*ny doubles, row-major;
+ * out4: device array of 4 doubles written by the call; dx [m]; c = dx/dt [m/s];
+ * stream: a cudaStream_t or NULL.  Asynchronous on that stream; it allocates
+ * nothing and calls no allocating routine.
+ *
+ * Scratch: a file-scope device array of LBM_NOALLOC_MAX_BLOCKS x 4 doubles (128 KiB)
+ * that every GPU loading the library holds until the process exits.  Grids larger
+ * than LBM_NOALLOC_MAX_CELLS cells are rejected with LBM_ERR_ARG (message in
+ * lbm_last_error(NULL)); use lbm_integrals for them.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the
+ * array and each call rewrites every entry it reads, so calls that overlap on the
+ * GPU (different streams, or different host threads on one device) race: order
+ * them on one stream.
+ * Errors: LBM_ERR_ARG (NULL pointer, sizes), LBM_ERR_CUDA.
+ */
+#define LBM_NOALLOC_MAX_BLOCKS 4096
+#define LBM_NOALLOC_CELLS_PER_BLOCK 2048
+#define LBM_NOALLOC_MAX_CELLS (LBM_NOALLOC_MAX_BLOCKS * LBM_NOALLOC_CELLS_PER_BLOCK)
+lbm_status lbm_field_integrals_noalloc(const double *rho, const double *ux, const double *uy,
+                                       const double *phi, int nx, int ny, double dx, double c,
+                                       double *out4, void *stream);
+
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,8 @@ struct lbm_s {
 
 static char g_create_err[512];
 
+void lbmk::set_global_error(const char *msg) { snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
+
 static lbm_status fail(lbm_t h, lbm_status st, const char *fmt, ...) {
   char *dst = h ? h->err : g_create_err;
   va_list ap;

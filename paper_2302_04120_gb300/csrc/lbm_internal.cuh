@@ -64,6 +64,9 @@ int sp_integral_blocks(int nx, int ny);
 // Convert nx*ny double planes into pitched storage planes (sources, forces).
 cudaError_t to_storage(const double *in, void *out, int nx, int ny, int pitch, int nplanes,
                        long long plane, int prec, double scale, cudaStream_t s);
+// Text for lbm_last_error(NULL) from entry points that take no handle.
+void set_global_error(const char *msg);
+
 // State <-> packed (unpitched) copies for checkpointing.
 cudaError_t pack_state(const void *state, void *packed, int nx, int ny, int pitch, int nq,
                        long long plane, int elem, int unpack, cudaStream_t s);

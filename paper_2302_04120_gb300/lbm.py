@@ -92,7 +92,10 @@ def lib():
 
 
 def _extra_signatures(L):
-    """Signatures of the batched and adjoint entry points (when built)."""
+    """Signatures of the allocation-free, batched and adjoint entry points."""
+    L.lbm_field_integrals_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                              C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+    L.lbm_field_integrals_noalloc.restype = C.c_int
     if hasattr(L, "lbm_batch_create"):
         L.lbm_batch_create.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
         L.lbm_batch_create.restype = C.c_int
@@ -226,6 +229,17 @@ def lbm_last_error(h=None):
 
 def lbm_destroy(h):
     lib().lbm_destroy(h)
+
+
+def lbm_field_integrals_noalloc(rho, ux, uy, phi, nx, ny, dx, c, out4, stream=None):
+    """Allocation-free integrals of device fields (torch CUDA float64 tensors or raw
+    device addresses) into the device array out4; returns the status code."""
+    def addr(t):
+        if t is None:
+            return None
+        return C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+    return lib().lbm_field_integrals_noalloc(addr(rho), addr(ux), addr(uy), addr(phi), int(nx), int(ny),
+                                             float(dx), float(c), addr(out4), stream)
 
 
 # --- convenience wrapper -----------------------------------------------------
