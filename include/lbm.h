@@ -227,6 +227,35 @@ const char *lbm_last_error(lbm_t h);
 void lbm_destroy(lbm_t h);
 
 /*
+ * Batched solves: many independent single-phase channels of uneven size advanced
+ * together, one kernel launch per time step over a flattened (channel, tile) list,
+ * replayed from a CUDA graph.  Each channel is an ordinary lbm_t owned by the batch:
+ * set its boundaries, sources and initial fields and read its moments with the calls
+ * above (lbm_batch_channel), but advance it only with lbm_batch_step.
+ *  lbm_batch_create  n parameter blocks (same precision, lattices and operators; single
+ *                    phase); stream NULL = a private non-blocking stream (graph capture
+ *                    cannot use the legacy default stream).  Errors as lbm_create.
+ *  lbm_batch_step    advance every channel n steps; all channels must be initialised and
+ *                    in step.  Asynchronous on the batch stream.  Errors: LBM_ERR_STATE,
+ *                    LBM_ERR_CUDA.
+ *  lbm_batch_autotune time candidate tile shapes (32..256 threads) and grid sizes (1..16
+ *                    blocks per SM) on the next step without advancing the solution; keeps
+ *                    the fastest; out_cfg (may be NULL) receives {tile_x, tile_y, grid}.
+ *  lbm_batch_config  set tile shape and grid explicitly (tile_x * tile_y a multiple of 32,
+ *                    at most 256).
+ * Every channel's result equals stepping it alone with lbm_step (same arithmetic).
+ */
+typedef struct lbm_batch_s *lbm_batch_t;
+lbm_status lbm_batch_create(const lbm_params *params, int n, void *stream, lbm_batch_t *out);
+lbm_t lbm_batch_channel(lbm_batch_t b, int k);
+int lbm_batch_size(lbm_batch_t b);
+lbm_status lbm_batch_step(lbm_batch_t b, long n);
+lbm_status lbm_batch_autotune(lbm_batch_t b, int out_cfg[3]);
+lbm_status lbm_batch_config(lbm_batch_t b, int tile_x, int tile_y, int grid);
+const char *lbm_batch_last_error(lbm_batch_t b);
+void lbm_batch_destroy(lbm_batch_t b);
+
+/*
  * Allocation-free integrals over macroscopic fields the caller already holds on
  * the device.  The paper has no counterpart: this is a service for callers that
  * cannot call cudaMalloc (code that runs inside a memory pool or arena owning the
@@ -260,7 +289,6 @@ void lbm_destroy(lbm_t h);
 lbm_status lbm_field_integrals_noalloc(const double *rho, const double *ux, const double *uy,
                                        const double *phi, int nx, int ny, double dx, double c,
                                        double *out4, void *stream);
-
 
 #ifdef __cplusplus
 }

@@ -525,3 +525,303 @@ extern "C" lbm_status lbm_synchronize(lbm_t h) {
   CU(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched solves: many independent single-phase channels, one launch per step
+// ---------------------------------------------------------------------------
+struct lbm_batch_s {
+  int n;
+  lbm_t *ch;              // channel handles (own their buffers and boundaries)
+  cudaStream_t stream;
+  int own_stream;
+  int prec, flow, th;
+  // device tables: parity p, channel k at [p * n + k]; local variant at [2n + k]
+  SpParams *h_tab, *d_tab;
+  int tab_valid;
+  // tile list for the chosen tile shape
+  int4 *d_tiles;
+  int ntiles, tiles_bx, tiles_by;
+  int bx, by, grid;       // launch configuration (autotuned or set)
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;   // two steps: parity 0 then parity 1
+  char err[512];
+};
+
+static lbm_status bfail(lbm_batch_t b, lbm_status st, const char *fmt, ...) {
+  char *dst = b ? b->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define BCU(b, call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" const char *lbm_batch_last_error(lbm_batch_t b) { return b ? b->err : g_create_err; }
+
+static void batch_drop_graph(lbm_batch_t b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = NULL;
+  b->graph = NULL;
+}
+
+extern "C" void lbm_batch_destroy(lbm_batch_t b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (int k = 0; k < b->n; k++) lbm_destroy(b->ch[k]);
+  free(b->ch);
+  free(b->h_tab);
+  cudaFree(b->d_tab);
+  cudaFree(b->d_tiles);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  free(b);
+}
+
+extern "C" lbm_status lbm_batch_create(const lbm_params *params, int n, void *stream, lbm_batch_t *out) {
+  if (!out) return bfail(NULL, LBM_ERR_ARG, "out is NULL");
+  *out = NULL;
+  if (!params || n < 1) return bfail(NULL, LBM_ERR_ARG, "need n >= 1 channel parameter blocks");
+  for (int k = 0; k < n; k++) {
+    const lbm_params &p = params[k];
+    if (p.phase != LBM_NONE) return bfail(NULL, LBM_ERR_ARG, "batched solves are single phase (channel %d)", k);
+    if (p.precision != params[0].precision || p.flow != params[0].flow || p.flow_op != params[0].flow_op ||
+        p.thermal != params[0].thermal || p.thermal_op != params[0].thermal_op)
+      return bfail(NULL, LBM_ERR_ARG, "all channels need the same precision, lattices and operators (channel %d)", k);
+  }
+  lbm_batch_t b = (lbm_batch_t)calloc(1, sizeof(struct lbm_batch_s));
+  if (!b) return bfail(NULL, LBM_ERR_NOMEM, "host allocation failed");
+  b->n = n;
+  b->ch = (lbm_t *)calloc(n, sizeof(lbm_t));
+  b->h_tab = (SpParams *)calloc(3 * (size_t)n, sizeof(SpParams));
+  if (!b->ch || !b->h_tab) { lbm_batch_destroy(b); return bfail(NULL, LBM_ERR_NOMEM, "host allocation failed"); }
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {  // graph capture needs a stream other than the legacy default one
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      lbm_batch_destroy(b);
+      return bfail(NULL, LBM_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    b->own_stream = 1;
+  }
+  for (int k = 0; k < n; k++) {
+    lbm_status st = lbm_create(&params[k], b->stream, &b->ch[k]);
+    if (st != LBM_OK) {
+      char msg[512];
+      snprintf(msg, sizeof(msg), "channel %d: %s", k, g_create_err);
+      lbm_batch_destroy(b);
+      return bfail(NULL, st, "%s", msg);
+    }
+  }
+  b->prec = params[0].precision;
+  sp_kinds(b->ch[0], &b->flow, &b->th);
+  if (cudaMalloc(&b->d_tab, 3 * (size_t)n * sizeof(SpParams)) != cudaSuccess) {
+    lbm_batch_destroy(b);
+    return bfail(NULL, LBM_ERR_NOMEM, "cudaMalloc parameter table");
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->bx = 64;
+  b->by = 4;
+  int occ = lbmk::sp_batch_occupancy(b->prec, b->flow, b->th, 256);
+  b->grid = sms * (occ > 0 ? occ : 4);
+  *out = b;
+  return LBM_OK;
+}
+
+extern "C" lbm_t lbm_batch_channel(lbm_batch_t b, int k) {
+  if (!b || k < 0 || k >= b->n) return NULL;
+  return b->ch[k];
+}
+
+extern "C" int lbm_batch_size(lbm_batch_t b) { return b ? b->n : 0; }
+
+// (Re)build the tile list for a tile shape.
+static lbm_status batch_tiles(lbm_batch_t b, int bx, int by) {
+  if (b->d_tiles && b->tiles_bx == bx && b->tiles_by == by) return LBM_OK;
+  long long total = 0;
+  for (int k = 0; k < b->n; k++)
+    total += (long long)((b->ch[k]->p.nx + bx - 1) / bx) * ((b->ch[k]->p.ny + by - 1) / by);
+  if (total > (1ll << 31) - 1) return bfail(b, LBM_ERR_ARG, "too many tiles");
+  int4 *h = (int4 *)malloc(sizeof(int4) * (size_t)total);
+  if (!h) return bfail(b, LBM_ERR_NOMEM, "host allocation failed");
+  long long t = 0;
+  for (int k = 0; k < b->n; k++) {
+    const int nx = b->ch[k]->p.nx, ny = b->ch[k]->p.ny;
+    for (int y0 = 0; y0 < ny; y0 += by)
+      for (int x0 = 0; x0 < nx; x0 += bx) h[t++] = make_int4(k, x0, y0, 0);
+  }
+  cudaStreamSynchronize(b->stream);
+  cudaFree(b->d_tiles);
+  b->d_tiles = NULL;
+  cudaError_t e = cudaMalloc(&b->d_tiles, sizeof(int4) * (size_t)total);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, h, sizeof(int4) * (size_t)total, cudaMemcpyHostToDevice);
+  free(h);
+  if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "tile list: %s", cudaGetErrorString(e));
+  b->ntiles = (int)total;
+  b->tiles_bx = bx;
+  b->tiles_by = by;
+  batch_drop_graph(b);
+  return LBM_OK;
+}
+
+// Parameter tables for the current state of every channel; upload when changed.
+static lbm_status batch_tables(lbm_batch_t b, int *cur, int *pre) {
+  const int c0 = b->ch[0]->cur, p0 = b->ch[0]->pre;
+  for (int k = 0; k < b->n; k++) {
+    lbm_t h = b->ch[k];
+    if (!h->initialised) return bfail(b, LBM_ERR_STATE, "channel %d is not initialised", k);
+    if (h->cur != c0 || h->pre != p0)
+      return bfail(b, LBM_ERR_STATE, "channel %d is not in step with channel 0 (step it through the batch only)", k);
+  }
+  SpParams *tmp = (SpParams *)malloc(3 * (size_t)b->n * sizeof(SpParams));
+  if (!tmp) return bfail(b, LBM_ERR_NOMEM, "host allocation failed");
+  for (int k = 0; k < b->n; k++) {
+    lbm_t h = b->ch[k];
+    const int save = h->pre;
+    h->pre = 0;
+    tmp[k] = sp_params(h, 0);
+    tmp[b->n + k] = sp_params(h, 1);
+    h->pre = 1;
+    tmp[2 * b->n + k] = sp_params(h, c0);
+    h->pre = save;
+  }
+  if (!b->tab_valid || memcmp(tmp, b->h_tab, 3 * (size_t)b->n * sizeof(SpParams)) != 0) {
+    memcpy(b->h_tab, tmp, 3 * (size_t)b->n * sizeof(SpParams));
+    cudaError_t e = cudaMemcpyAsync(b->d_tab, b->h_tab, 3 * (size_t)b->n * sizeof(SpParams), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // h_tab may change before the copy runs
+    if (e != cudaSuccess) { free(tmp); return bfail(b, LBM_ERR_CUDA, "table upload: %s", cudaGetErrorString(e)); }
+    b->tab_valid = 1;
+  }
+  free(tmp);
+  *cur = c0;
+  *pre = p0;
+  return LBM_OK;
+}
+
+static cudaError_t batch_launch(lbm_batch_t b, const SpParams *table) {
+  return lbmk::sp_batch_step(table, b->d_tiles, b->ntiles, b->prec, b->flow, b->th, dim3(b->bx, b->by), b->grid,
+                             b->stream);
+}
+
+static void batch_advance(lbm_batch_t b, long n) {
+  for (int k = 0; k < b->n; k++) {
+    lbm_t h = b->ch[k];
+    h->cur = (int)((h->cur + n) & 1);
+    h->pre = 0;
+    h->steps += n;
+  }
+}
+
+extern "C" lbm_status lbm_batch_config(lbm_batch_t b, int bx, int by, int grid) {
+  if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
+  if (bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32 || grid < 1)
+    return bfail(b, LBM_ERR_ARG, "tile must be a multiple of 32 threads, at most 256; grid >= 1");
+  lbm_status st = batch_tiles(b, bx, by);
+  if (st != LBM_OK) return st;
+  if (b->bx != bx || b->by != by || b->grid != grid) batch_drop_graph(b);
+  b->bx = bx;
+  b->by = by;
+  b->grid = grid;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_step(lbm_batch_t b, long n) {
+  if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
+  if (n < 0) return bfail(b, LBM_ERR_ARG, "n must be >= 0");
+  if (n == 0) return LBM_OK;
+  lbm_status st = batch_tiles(b, b->bx, b->by);
+  if (st != LBM_OK) return st;
+  int cur, pre;
+  st = batch_tables(b, &cur, &pre);
+  if (st != LBM_OK) return st;
+  if (pre) {  // first step after initialisation: collide the stored f(0) in place
+    BCU(b, batch_launch(b, b->d_tab + 2 * b->n));
+    batch_advance(b, 1);
+    n--;
+    cur = 1 - cur;
+  }
+  if (n > 0 && cur == 1) {  // align to parity 0 for the two-step graph
+    BCU(b, batch_launch(b, b->d_tab + b->n));
+    batch_advance(b, 1);
+    n--;
+  }
+  if (n >= 2) {
+    if (!b->exec) {  // capture: step with parity 0 (buf0 -> buf1), then parity 1
+      BCU(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e1 = batch_launch(b, b->d_tab);
+      cudaError_t e2 = batch_launch(b, b->d_tab + b->n);
+      cudaError_t e3 = cudaStreamEndCapture(b->stream, &b->graph);
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        batch_drop_graph(b);
+        return bfail(b, LBM_ERR_CUDA, "graph capture failed");
+      }
+      BCU(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    for (long k = 0; k < n / 2; k++) BCU(b, cudaGraphLaunch(b->exec, b->stream));
+    batch_advance(b, 2 * (n / 2));
+    n -= 2 * (n / 2);
+  }
+  if (n == 1) {
+    BCU(b, batch_launch(b, b->d_tab));
+    batch_advance(b, 1);
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_autotune(lbm_batch_t b, int out_cfg[3]) {
+  if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
+  int cur, pre;
+  lbm_status st = batch_tables(b, &cur, &pre);
+  if (st != LBM_OK) return st;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static const int shapes[][2] = {{32, 4}, {64, 4}, {128, 2}, {32, 8}, {256, 1}, {64, 2}, {128, 1}};
+  static const int mults[] = {1, 2, 4, 8, 16};
+  // Timing launches re-run the step that the next lbm_batch_step would take (same
+  // source buffer, same destination), so the solution does not advance.
+  const SpParams *table = pre ? b->d_tab + 2 * b->n : b->d_tab + (size_t)cur * b->n;
+  cudaEvent_t e0, e1;
+  BCU(b, cudaEventCreate(&e0));
+  BCU(b, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bb[3] = {b->bx, b->by, b->grid};
+  for (const auto &sh : shapes) {
+    st = batch_tiles(b, sh[0], sh[1]);
+    if (st != LBM_OK) break;
+    const int occ = lbmk::sp_batch_occupancy(b->prec, b->flow, b->th, sh[0] * sh[1]);
+    for (int m : mults) {
+      if (m > (occ > 0 ? occ : 1) * 2) continue;
+      const int grid = sms * m;
+      b->bx = sh[0];
+      b->by = sh[1];
+      b->grid = grid;
+      batch_launch(b, table);  // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 3; r++) batch_launch(b, table);
+      cudaEventRecord(e1, b->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { st = bfail(b, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e)); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bb[0] = sh[0]; bb[1] = sh[1]; bb[2] = grid; }
+    }
+    if (st != LBM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  st = lbm_batch_config(b, bb[0], bb[1], bb[2]);
+  batch_drop_graph(b);
+  if (out_cfg) { out_cfg[0] = b->bx; out_cfg[1] = b->by; out_cfg[2] = b->grid; }
+  return st;
+}

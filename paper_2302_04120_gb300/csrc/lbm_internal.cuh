@@ -49,6 +49,11 @@ enum { TH_NONE = 0, TH_BGK = 1, TH_MRT = 2 };
 
 // Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
+// One step of many solves: table[k] holds the parameters (with this step's src/dst)
+// of channel k; tiles lists (channel, x0, y0) of every blockDim-sized tile.
+cudaError_t sp_batch_step(const SpParams *table, const int4 *tiles, int ntiles, int prec, int flow, int th,
+                          dim3 block, int grid, cudaStream_t s);
+int sp_batch_occupancy(int prec, int flow, int th, int threads);
 // Equilibrium initialisation (pre-collision state of time 0) from double fields (device).
 cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double *a,
                     const double *ux, const double *uy, const double *b, dim3 block,

@@ -31,351 +31,18 @@
 
 #include "lattice.cuh"
 #include "lbm_internal.cuh"
+#include "sp_device.cuh"
 
 namespace lbmk {
-
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3 };
-enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3 };
-
-__device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
-
-// Position of node (i, j) along a side, and the side's length.
-__device__ __forceinline__ int along(int side, int i, int j) { return side < 2 ? j : i; }
-__device__ __forceinline__ int side_len(const SpParams &P, int side) { return side < 2 ? P.ny : P.nx; }
-
-// Which side the link arriving at (i, j) along c = (cx, cy) comes through (source
-// node (i - cx, j - cy) outside the domain), or -1.  y-sides win at corners.
-__device__ __forceinline__ int entry_side(int i, int j, int cx, int cy, int nx, int ny, int xper, int yper) {
-  int si = i - cx, sj = j - cy;
-  if (!yper) {
-    if (sj < 0) return 2;
-    if (sj >= ny) return 3;
-  }
-  if (!xper) {
-    if (si < 0) return 0;
-    if (si >= nx) return 1;
-  }
-  return -1;
-}
-
-// Pre-collision velocity of time t at node n rebuilt from its post-collision
-// populations: rho = sum f*, rho u = sum c f* - dt F / 2 (the collision adds dt F
-// to the momentum, Eqs. first_moment_f and forcing_term).
-template <typename S, typename R>
-__device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, int i, int j, R &ux, R &uy) {
-  long long n = (long long)j * P.pitch + i;
-  R f[9];
-#pragma unroll
-  for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
-  R drho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-  R rho = (R)P.rho0 + drho;
-  R c = (R)P.c;
-  R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
-  R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
-  R Fx = (R)P.Fx, Fy = (R)P.Fy;
-  if (P.force) {
-    const S *fo = (const S *)P.force;
-    Fx += (R)fo[n];
-    Fy += (R)fo[P.plane + n];
-  }
-  ux = (jx - (R)0.5 * (R)P.dt * Fx) / rho;
-  uy = (jy - (R)0.5 * (R)P.dt * Fy) / rho;
-}
-
-// Pull of all momentum populations at node (i, j), with boundary links.
-template <typename S, typename R>
-__device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, int j, bool interior, R f[9]) {
-  const long long n = (long long)j * P.pitch + i;
-  if (interior) {
-#pragma unroll
-    for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n - (long long)cy9(q) * P.pitch - cx9(q)];
-    return;
-  }
-  if (P.local) {  // src holds f(t) itself (first step after initialisation)
-#pragma unroll
-    for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
-    return;
-  }
-  const R c = (R)P.c, inv_cs2 = (R)1 / (R)P.cs2;
-  // outlet velocity extrapolation, Eq. anti_BB_vel and the rule below it (reading:
-  // pre-collision velocities of time t at the boundary node and its inner neighbour)
-  R uwp[4][2];
-#pragma unroll
-  for (int s = 0; s < 4; s++) { uwp[s][0] = 0; uwp[s][1] = 0; }
-#pragma unroll
-  for (int s = 0; s < 4; s++) {
-    bool on = (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
-    if (on && P.side[s].kind == BC_PRESSURE) {
-      int ii = i + (s == 0) - (s == 1), jj = j + (s == 2) - (s == 3);
-      R ub, vb, ui, vi;
-      post_velocity<S, R>(P, src, i, j, ub, vb);
-      post_velocity<S, R>(P, src, ii, jj, ui, vi);
-      uwp[s][0] = ub + (R)0.5 * (ub - ui);
-      uwp[s][1] = vb + (R)0.5 * (vb - vi);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 9; q++) {
-    const int side = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper);
-    if (side < 0) {
-      int si = wrap(i - cx9(q), P.nx), sj = wrap(j - cy9(q), P.ny);
-      f[q] = (R)src[q * P.plane + (long long)sj * P.pitch + si];
-      continue;
-    }
-    // outgoing direction o = opp(q) leaves node (i, j) through `side`
-    const int o = opp9(q);
-    const R fo = (R)src[o * P.plane + n];
-    const DevSide &sd = P.side[side];
-    const int a = along(side, i, j), len = side_len(P, side);
-    const R rw = (R)sd.rho_w;
-    const R cox = c * (R)cx9(o), coy = c * (R)cy9(o);
-    if (sd.kind == BC_PRESSURE) {
-      // Eq. anti_BB_vel in deviation form: f_q - w rho0 = -(f_o* - w rho0) + 2 w [rho_w(...) - rho0]
-      R ux = uwp[side][0], uy = uwp[side][1];
-      R cu = cox * ux + coy * uy;
-      R uu = ux * ux + uy * uy;
-      f[q] = -fo + (R)2 * w9<R>(o) * (rw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - (R)P.rho0);
-    } else {
-      // Eq. BB_vel (walls and velocity inlet): f_q = f_o* - 2 w_o rho_w c_o.u_w / c_s^2
-      R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
-      f[q] = fo - (R)2 * w9<R>(o) * rw * (cox * ux + coy * uy) * inv_cs2;
-    }
-  }
-}
-
-// Pull of the D2Q5 thermal populations at node (i, j) with boundary links.
-template <typename S, typename R>
-__device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, int j, bool interior, R g[5]) {
-  const long long n = (long long)j * P.pitch + i;
-  const S *gsrc = src + (long long)P.gbase * P.plane;
-  if (interior) {
-#pragma unroll
-    for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n - (long long)cy5(q) * P.pitch - cx5(q)];
-    return;
-  }
-  if (P.local) {
-#pragma unroll
-    for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n];
-    return;
-  }
-  const R c = (R)P.c, inv_cs2 = (R)1 / (R)P.cs2;
-#pragma unroll
-  for (int q = 0; q < 5; q++) {
-    const int side = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
-    if (side < 0) {
-      int si = wrap(i - cx5(q), P.nx), sj = wrap(j - cy5(q), P.ny);
-      g[q] = (R)gsrc[q * P.plane + (long long)sj * P.pitch + si];
-      continue;
-    }
-    const int o = opp5(q);
-    const DevSide &sd = P.side[side];
-    const int a = along(side, i, j), len = side_len(P, side);
-    if (sd.tkind == TBC_OUTFLOW) {
-      // g_q(x_b, t+dt) = g_q(x_b-1, t+dt) = g_q*(x_b-1 - c_q dt, t) (Sec. 2.2, outlet)
-      int ii = i + (side == 0) - (side == 1), jj = j + (side == 2) - (side == 3);
-      int si = min(max(ii - cx5(q), 0), P.nx - 1), sj = min(max(jj - cy5(q), 0), P.ny - 1);
-      g[q] = (R)gsrc[q * P.plane + (long long)sj * P.pitch + si];
-    } else if (sd.tkind == TBC_TEMP) {
-      // Eq. anti_BB_T in deviation form
-      const R go = (R)gsrc[o * P.plane + n];
-      R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
-      R cu = c * ((R)cx5(o) * ux + (R)cy5(o) * uy);
-      R uu = ux * ux + uy * uy;
-      R Tw = sd.tw ? (R)sd.tw[a] : (R)0;
-      g[q] = -go + (R)2 * w5<R>(o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - (R)P.T0);
-    } else {
-      // Eq. BB_T with lambda = 1 for the single unknown (FLUX; zero flux = adiabatic)
-      const R go = (R)gsrc[o * P.plane + n];
-      R qf = sd.tw ? (R)sd.tw[a] : (R)0;
-      g[q] = go + (R)P.flux_coef * qf;
-    }
-  }
-}
-
-// ----------------------------------------------------------------------------
-// Moments and collisions (deviation form)
-// ----------------------------------------------------------------------------
-template <typename R>
-struct Macro {
-  R drho, rho, ux, uy, Fx, Fy;  // momentum
-  R sumg, qd, T;                // thermal
-};
-
-template <typename S, typename R>
-__device__ __forceinline__ void load_sources(const SpParams &P, long long n, Macro<R> &m) {
-  m.Fx = (R)P.Fx;
-  m.Fy = (R)P.Fy;
-  if (P.force) {
-    const S *fo = (const S *)P.force;
-    m.Fx += (R)fo[n];
-    m.Fy += (R)fo[P.plane + n];
-  }
-  m.qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
-}
-
-template <typename R, int FLOW, int TH>
-__device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R g[5], Macro<R> &m) {
-  if (FLOW != FLOW_NONE) {
-    // Eqs. zero_moment_f and first_moment_f
-    m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    m.rho = (R)P.rho0 + m.drho;
-    const R c = (R)P.c, hdt = (R)0.5 * (R)P.dt;
-    const R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
-    const R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
-    const R inv = (R)1 / m.rho;
-    m.ux = (jx + hdt * m.Fx) * inv;
-    m.uy = (jy + hdt * m.Fy) * inv;
-  } else {
-    m.drho = 0;
-    m.rho = (R)P.rho0;
-    m.ux = (R)P.ux_pres;
-    m.uy = (R)P.uy_pres;
-  }
-  if (TH != TH_NONE) {
-    // Eq. zero_moment_g
-    m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    m.T = (R)P.T0 + m.sumg + (R)0.5 * (R)P.dt * m.qd;
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &m, R f[9]) {
-  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c), inv_cs4 = inv_cs2 * inv_cs2;
-  const R om = (R)P.omega;
-  const R fac = ((R)1 - (R)0.5 * om) * (R)P.dt;  // (1 - dt/(2 tau)) dt
-  const R hu = (R)0.5 * (m.ux * m.ux + m.uy * m.uy) * inv_cs2;  // u^2 / (2 c_s^2)
-  const R uF = m.ux * m.Fx + m.uy * m.Fy;
-  // q >= 1 first; the rest population takes the remainders so that sum f_eq = rho
-  // and sum F_hat = 0 hold exactly in the working precision (the rounded weights
-  // do not sum to one in FP32)
-  R feq_sum = 0, fh_sum = 0;
-#pragma unroll
-  for (int q = 1; q < 9; q++) {
-    const R cxq = c * (R)cx9(q), cyq = c * (R)cy9(q);
-    const R cu = cxq * m.ux + cyq * m.uy;
-    // f_eq - w rho0 (Eq. feq_geral, deviation form: no O(rho0) cancellation)
-    const R feq = w9<R>(q) * (m.drho + m.rho * (cu * inv_cs2 * ((R)1 + (R)0.5 * cu * inv_cs2) - hu));
-    // Guo forcing F_hat (Eq. forcing_term)
-    const R cF = cxq * m.Fx + cyq * m.Fy;
-    const R Fh = w9<R>(q) * ((cF - uF) * inv_cs2 + cu * cF * inv_cs4);
-    feq_sum += feq;
-    fh_sum += Fh;
-    f[q] = f[q] - om * (f[q] - feq) + fac * Fh;
-  }
-  f[0] = f[0] - om * (f[0] - (m.drho - feq_sum)) + fac * (-fh_sum);
-}
-
-template <typename R>
-__device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &m, R f[9]) {
-  const R c = (R)P.c, ic = (R)1 / c;
-  const R dt = (R)P.dt;
-  // lattice-scaled moments of the deviations (rows of Eq. M_matrix)
-  const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
-  const R s58 = (f[5] + f[6]) + (f[7] + f[8]);
-  const R m_e = -(R)4 * f[0] - s14 + (R)2 * s58;
-  const R m_ep = (R)4 * f[0] - (R)2 * s14 + s58;
-  const R d58 = (f[5] - f[7]), d68 = (f[6] - f[8]);
-  const R m_qx = (R)2 * (f[3] - f[1]) + d58 - d68;
-  const R m_qy = (R)2 * (f[4] - f[2]) + d58 + d68;
-  const R m_xx = (f[1] + f[3]) - (f[2] + f[4]);
-  const R m_xy = (f[5] + f[7]) - (f[6] + f[8]);
-  // equilibrium and forcing moments divided by c^n (Eq. M_matrix_dim row orders)
-  const R ux = m.ux * ic, uy = m.uy * ic, usq = ux * ux + uy * uy;
-  const R Fx = m.Fx * ic, Fy = m.Fy * ic, uF = ux * Fx + uy * Fy;
-  const R eq_e = -(R)2 * m.drho + (R)3 * m.rho * usq;
-  const R eq_ep = m.drho - (R)3 * m.rho * usq;
-  const R eq_qx = -m.rho * ux, eq_qy = -m.rho * uy;
-  const R eq_xx = m.rho * (ux * ux - uy * uy), eq_xy = m.rho * ux * uy;
-  const R s_e = (R)P.s_e, s_ep = (R)P.s_eps, s_q = (R)P.s_q, s_nu = (R)P.s_nu;
-  // Delta m_k = dt Lambda_k (m_k - m_k^eq) - dt (1 - dt Lambda_k / 2) F_k  (Eq. colisao_MRT)
-  const R d_e = s_e * (m_e - eq_e) - ((R)1 - (R)0.5 * s_e) * dt * ((R)6 * uF);
-  const R d_ep = s_ep * (m_ep - eq_ep) + ((R)1 - (R)0.5 * s_ep) * dt * ((R)6 * uF);
-  const R d_jx = -dt * Fx, d_jy = -dt * Fy;
-  const R d_qx = s_q * (m_qx - eq_qx) + ((R)1 - (R)0.5 * s_q) * dt * Fx;
-  const R d_qy = s_q * (m_qy - eq_qy) + ((R)1 - (R)0.5 * s_q) * dt * Fy;
-  const R d_xx = s_nu * (m_xx - eq_xx) - ((R)1 - (R)0.5 * s_nu) * dt * ((R)2 * (ux * Fx - uy * Fy));
-  const R d_xy = s_nu * (m_xy - eq_xy) - ((R)1 - (R)0.5 * s_nu) * dt * (ux * Fy + uy * Fx);
-  // back to populations: M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-  const R a1 = d_e * ((R)1 / (R)36), a2 = d_ep * ((R)1 / (R)36);
-  const R a3 = d_jx * ((R)1 / (R)6), a4 = d_qx * ((R)1 / (R)12);
-  const R a5 = d_jy * ((R)1 / (R)6), a6 = d_qy * ((R)1 / (R)12);
-  const R a7 = d_xx * (R)0.25, a8 = d_xy * (R)0.25;
-  const R ax = -a1 - (R)2 * a2;   // common to i = 1..4
-  const R dg = (R)2 * a1 + a2;    // common to i = 5..8
-  f[0] -= (R)4 * (a2 - a1);
-  f[1] -= ax + a3 - (R)2 * a4 + a7;
-  f[2] -= ax + a5 - (R)2 * a6 - a7;
-  f[3] -= ax - a3 + (R)2 * a4 + a7;
-  f[4] -= ax - a5 + (R)2 * a6 - a7;
-  const R p34 = a3 + a4, p56 = a5 + a6;
-  f[5] -= dg + p34 + p56 + a8;
-  f[6] -= dg - p34 + p56 - a8;
-  f[7] -= dg - p34 - p56 + a8;
-  f[8] -= dg + p34 - p56 - a8;
-}
-
-template <typename R>
-__device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &m, R g[5]) {
-  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c);
-  const R om = (R)P.omegaT;
-  const R src = (R)P.tsrc_fac * (R)P.dt * m.qd;
-  const R dT = m.T - (R)P.T0;
-  R geq_sum = 0, s_sum = 0;
-#pragma unroll
-  for (int q = 1; q < 5; q++) {
-    const R cu = c * ((R)cx5(q) * m.ux + (R)cy5(q) * m.uy);
-    const R geq = w5<R>(q) * (dT + m.T * cu * inv_cs2);  // Eq. geq_geral minus w T0
-    const R sq = w5<R>(q) * src;                         // Eq. forcing_term_g
-    geq_sum += geq;
-    s_sum += sq;
-    g[q] = g[q] - om * (g[q] - geq) + sq;
-  }
-  // rest population from the remainders: sum g_eq = T - T0, sum S = source, exactly
-  g[0] = g[0] - om * (g[0] - (dT - geq_sum)) + (src - s_sum);
-}
-
-template <typename R>
-__device__ __forceinline__ void collide_mrt5(const SpParams &P, const Macro<R> &m, R g[5]) {
-  // D2Q5 moments (1, c_x, c_y, 5|c|^2 - 4c^2, c_x^2 - c_y^2) scaled by c^-n; rates
-  // (0, 1/tau_T, 1/tau_T, 1/dt, 1/dt); source Delta t (I - dt Lambda/2) M (w qdot).
-  const R ic = (R)1 / (R)P.c, dt = (R)P.dt;
-  const R dT = m.T - (R)P.T0;
-  const R m1 = g[1] - g[3], m2 = g[2] - g[4];
-  const R m3 = -(R)4 * g[0] + ((g[1] + g[2]) + (g[3] + g[4]));
-  const R m4 = (g[1] + g[3]) - (g[2] + g[4]);
-  const R sT = (R)P.omegaT;
-  const R d0 = -dt * m.qd;
-  const R d1 = sT * (m1 - m.T * m.ux * ic);
-  const R d2 = sT * (m2 - m.T * m.uy * ic);
-  // e-moment: rate 1/dt, equilibrium -(2/3) dT, source -(2/3) qdot with factor 1/2
-  const R d3 = (m3 + (R)(2.0 / 3.0) * dT) - (R)0.5 * dt * (-(R)(2.0 / 3.0) * m.qd);
-  const R d4 = m4;
-  const R a0 = d0 * (R)0.2, a1 = d1 * (R)0.5, a2 = d2 * (R)0.5, a3 = d3 * (R)0.05, a4 = d4 * (R)0.25;
-  g[0] -= a0 - (R)4 * a3;
-  g[1] -= a0 + a1 + a3 + a4;
-  g[2] -= a0 + a2 + a3 - a4;
-  g[3] -= a0 - a1 + a3 + a4;
-  g[4] -= a0 - a2 + a3 - a4;
-}
-
-template <typename R, int FLOW, int TH>
-__device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R f[9], R g[5]) {
-  if (FLOW == FLOW_BGK) collide_bgk9<R>(P, m, f);
-  if (FLOW == FLOW_MRT) collide_mrt9<R>(P, m, f);
-  if (TH == TH_BGK) collide_bgk5<R>(P, m, g);
-  if (TH == TH_MRT) collide_mrt5<R>(P, m, g);
-}
 
 // ----------------------------------------------------------------------------
 // Kernels
 // ----------------------------------------------------------------------------
+// One node: pull with boundary links, moments, collision, store.
 template <int PREC, int FLOW, int TH>
-__global__ void __launch_bounds__(256) k_step(const SpParams P) {
+__device__ __forceinline__ void step_node(const SpParams &P, int i, int j) {
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= P.nx || j >= P.ny) return;
   const long long n = (long long)j * P.pitch + i;
   const S *src = (const S *)P.src;
   S *dst = (S *)P.dst;
@@ -395,6 +62,29 @@ __global__ void __launch_bounds__(256) k_step(const SpParams P) {
     S *gd = dst + (long long)P.gbase * P.plane;
 #pragma unroll
     for (int q = 0; q < 5; q++) gd[q * P.plane + n] = (S)g[q];
+  }
+}
+
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256) k_step(const SpParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= P.nx || j >= P.ny) return;
+  step_node<PREC, FLOW, TH>(P, i, j);
+}
+
+// Many independent solves in one launch: blocks walk a flattened list of
+// (channel, tile origin) entries with a grid stride; each entry is one
+// blockDim.x x blockDim.y tile of one channel, whose parameters (sizes,
+// boundaries, rates, buffers of this parity) sit in a device table.
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256) k_batch_step(const SpParams *__restrict__ table, const int4 *__restrict__ tiles,
+                                                     int ntiles) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 tl = tiles[t];  // (channel, x0, y0, unused)
+    const SpParams &P = table[tl.x];
+    const int i = tl.y + threadIdx.x, j = tl.z + threadIdx.y;
+    if (i < P.nx && j < P.ny) step_node<PREC, FLOW, TH>(P, i, j);
   }
 }
 
@@ -573,6 +263,42 @@ cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, c
   LBM_SP_DISPATCH(prec, flow, th, CALL_STEP);
 #undef CALL_STEP
   return cudaGetLastError();
+}
+
+cudaError_t sp_batch_step(const SpParams *table, const int4 *tiles, int ntiles, int prec, int flow, int th, dim3 block,
+                          int grid, cudaStream_t s) {
+#define CALL_BATCH(A, B, C) k_batch_step<A, B, C><<<grid, block, 0, s>>>(table, tiles, ntiles)
+  LBM_SP_DISPATCH(prec, flow, th, CALL_BATCH);
+#undef CALL_BATCH
+  return cudaGetLastError();
+}
+
+int sp_batch_occupancy(int prec, int flow, int th, int threads) {
+  int nb = 0;
+#define CALL_OCC(A, B, C) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<A, B, C>, threads, 0)
+  do {
+    if (prec == 0) {
+      if (flow == FLOW_BGK && th == TH_NONE) CALL_OCC(0, FLOW_BGK, TH_NONE);
+      else if (flow == FLOW_BGK && th == TH_BGK) CALL_OCC(0, FLOW_BGK, TH_BGK);
+      else if (flow == FLOW_BGK && th == TH_MRT) CALL_OCC(0, FLOW_BGK, TH_MRT);
+      else if (flow == FLOW_MRT && th == TH_NONE) CALL_OCC(0, FLOW_MRT, TH_NONE);
+      else if (flow == FLOW_MRT && th == TH_BGK) CALL_OCC(0, FLOW_MRT, TH_BGK);
+      else if (flow == FLOW_MRT && th == TH_MRT) CALL_OCC(0, FLOW_MRT, TH_MRT);
+      else if (flow == FLOW_NONE && th == TH_BGK) CALL_OCC(0, FLOW_NONE, TH_BGK);
+      else if (flow == FLOW_NONE && th == TH_MRT) CALL_OCC(0, FLOW_NONE, TH_MRT);
+    } else {
+      if (flow == FLOW_BGK && th == TH_NONE) CALL_OCC(1, FLOW_BGK, TH_NONE);
+      else if (flow == FLOW_BGK && th == TH_BGK) CALL_OCC(1, FLOW_BGK, TH_BGK);
+      else if (flow == FLOW_BGK && th == TH_MRT) CALL_OCC(1, FLOW_BGK, TH_MRT);
+      else if (flow == FLOW_MRT && th == TH_NONE) CALL_OCC(1, FLOW_MRT, TH_NONE);
+      else if (flow == FLOW_MRT && th == TH_BGK) CALL_OCC(1, FLOW_MRT, TH_BGK);
+      else if (flow == FLOW_MRT && th == TH_MRT) CALL_OCC(1, FLOW_MRT, TH_MRT);
+      else if (flow == FLOW_NONE && th == TH_BGK) CALL_OCC(1, FLOW_NONE, TH_BGK);
+      else if (flow == FLOW_NONE && th == TH_MRT) CALL_OCC(1, FLOW_NONE, TH_MRT);
+    }
+  } while (0);
+#undef CALL_OCC
+  return nb;
 }
 
 cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double *a, const double *ux,

@@ -96,9 +96,22 @@ def _extra_signatures(L):
     L.lbm_field_integrals_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                               C.c_double, C.c_double, C.c_void_p, C.c_void_p]
     L.lbm_field_integrals_noalloc.restype = C.c_int
-    if hasattr(L, "lbm_batch_create"):
-        L.lbm_batch_create.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
-        L.lbm_batch_create.restype = C.c_int
+    L.lbm_batch_create.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+    L.lbm_batch_create.restype = C.c_int
+    L.lbm_batch_channel.argtypes = [C.c_void_p, C.c_int]
+    L.lbm_batch_channel.restype = C.c_void_p
+    L.lbm_batch_size.argtypes = [C.c_void_p]
+    L.lbm_batch_size.restype = C.c_int
+    L.lbm_batch_step.argtypes = [C.c_void_p, C.c_long]
+    L.lbm_batch_step.restype = C.c_int
+    L.lbm_batch_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    L.lbm_batch_autotune.restype = C.c_int
+    L.lbm_batch_config.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.lbm_batch_config.restype = C.c_int
+    L.lbm_batch_last_error.argtypes = [C.c_void_p]
+    L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_batch_destroy.argtypes = [C.c_void_p]
+    L.lbm_batch_destroy.restype = None
 
 
 def _check(h, st):
@@ -266,17 +279,18 @@ class Solver:
     """One solve on the GPU.  ``params`` is an SI dict as produced by
     ``paper_2302_04120_gb300.workloads``."""
 
-    def __init__(self, params: dict, precision=LBM_FP64, stream=None):
+    def __init__(self, params: dict, precision=LBM_FP64, stream=None, handle=None):
         self.params = dict(params)
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
         self.n = self.nx * self.ny
-        self.h = lbm_create(make_params(params, precision), stream)
         self.precision = precision
+        self._owned = handle is None
+        self.h = lbm_create(make_params(params, precision), stream) if handle is None else handle
 
     def close(self):
-        if self.h is not None and self.h.value:
+        if self._owned and self.h is not None and self.h.value:
             lbm_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -349,3 +363,47 @@ class Solver:
             w5 = np.array([1 / 3] + [1 / 6] * 4)
             out["g"] = a[k:k + 5] + w5[:, None, None] * p.get("T0", 300.0)
         return out
+
+
+def _bcheck(b, st):
+    if st != LBM_OK:
+        msg = lib().lbm_batch_last_error(b)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many independent single-phase channels advanced by one launch per step.
+    ``channels[k]`` is a Solver view of channel k (boundaries, sources, init,
+    moments); advance only with ``step``."""
+
+    def __init__(self, params_list, precision=LBM_FP64, stream=None):
+        arr = (lbm_params * len(params_list))(*[make_params(p, precision) for p in params_list])
+        h = C.c_void_p()
+        _bcheck(None, lib().lbm_batch_create(arr, len(params_list), stream, C.byref(h)))
+        self.h = h
+        self.channels = [Solver(p, precision, handle=C.c_void_p(lib().lbm_batch_channel(h, k)))
+                         for k, p in enumerate(params_list)]
+
+    def step(self, n):
+        _bcheck(self.h, lib().lbm_batch_step(self.h, int(n)))
+
+    def autotune(self):
+        cfg = (C.c_int * 3)()
+        _bcheck(self.h, lib().lbm_batch_autotune(self.h, cfg))
+        return tuple(cfg)
+
+    def config(self, bx, by, grid):
+        _bcheck(self.h, lib().lbm_batch_config(self.h, bx, by, grid))
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            for c in self.channels:
+                c.h = None
+            lib().lbm_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
