@@ -175,6 +175,15 @@ lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux, const dou
  */
 lbm_status lbm_step(lbm_t h, long n);
 
+/*
+ * Pick the thread-block shape of the single-solve step kernel by timing candidate
+ * shapes (32..256 threads) on the next step, without advancing the solution (the timed
+ * launches repeat that step into the same destination).  out_block (may be NULL)
+ * receives {block_x, block_y}.  Single-phase solves only; the default is 64 x 4.
+ * Errors: LBM_ERR_STATE (not initialised), LBM_ERR_ARG, LBM_ERR_CUDA.
+ */
+lbm_status lbm_autotune(lbm_t h, int out_block[2]);
+
 /* Steps taken since lbm_init_fields (time = steps * dt). */
 long lbm_steps_done(lbm_t h);
 
@@ -254,6 +263,27 @@ lbm_status lbm_batch_autotune(lbm_batch_t b, int out_cfg[3]);
 lbm_status lbm_batch_config(lbm_batch_t b, int tile_x, int tile_y, int grid);
 const char *lbm_batch_last_error(lbm_batch_t b);
 void lbm_batch_destroy(lbm_batch_t b);
+
+/*
+ * Reverse-time discrete adjoint of the fused step for single-phase D2Q9 MRT + D2Q5 MRT
+ * solves in FP64.  Call right after lbm_init_fields (and lbm_set_bc, lbm_set_source):
+ * it runs the forward `steps` steps itself, keeping a checkpoint every ckpt_every
+ * steps, then walks the steps backwards, recomputing each segment's states from its
+ * checkpoint.  Device memory: (steps/ckpt_every + ckpt_every + 3) state buffers.  On
+ * return the handle holds the forward state of time steps * dt.
+ *  loss     L = (1/ny) sum_j (T(nx-1, j; steps) - T_target[j])^2: mean squared error of
+ *           the temperature of the x+ column against T_target (ny host doubles) [K^2]
+ *  g_q3     nx*ny host array (or NULL): dL/dq for the per-cell volumetric heat source
+ *           set by lbm_set_source [K^2 per W m^-3]
+ *  g_qwall  2*nx host array (or NULL): dL/dq_wall per node of the y- wall, then of the
+ *           y+ wall, for sides with LBM_TBC_FLUX [K^2 per W m^-2]
+ *  g_nu     host scalar (or NULL): dL/dnu [K^2 per m^2 s^-1]
+ * The gradient is that of the discrete forward map (exact up to rounding).
+ * Errors: LBM_ERR_ARG (configuration), LBM_ERR_STATE (not freshly initialised),
+ * LBM_ERR_NOMEM, LBM_ERR_CUDA.
+ */
+lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const double *T_target, double *loss, double *g_q3,
+                       double *g_qwall, double *g_nu);
 
 /*
  * Allocation-free integrals over macroscopic fields the caller already holds on

@@ -1,0 +1,326 @@
+// Reverse-time (discrete) adjoint of the single-phase fused step: D2Q9 MRT
+// momentum + D2Q5 MRT thermal, FP64, with the channel boundary rules
+// (BB-velocity inlet and walls, anti-BB pressure outlet with extrapolated
+// velocity, anti-BB temperature inlet, heat-flux walls, thermal outflow).
+//
+// Forward (step_sp.cu): X_t = C(P(X_{t-1})), where P is the pull with boundary
+// links and C the local collision; X_{-1} is the pre-collision initial state.
+// Loss: L = (1/ny) sum_j (T(nx-1, j; N) - T_target(j))^2 with T of P(X_{N-1}).
+// Reverse step t (N-1 >= t >= 0), one launch per node grid:
+//   Lam_X(t)   = P^T Lam_pre(t+1)       gather from the consumers of X_t: the
+//                                        streaming neighbour, the node's own
+//                                        reflected links, the thermal outflow,
+//                                        and the outlet velocity extrapolation;
+//   Lam_pre(t) = C'(pre(t))^T Lam_X(t)   local transposed Jacobian of the MRT
+//                                        collisions (moments, equilibria,
+//                                        forcing, u = j/rho, T = sum g + dt qdot/2),
+// with pre(t) recomputed by pulling X_{t-1}.  Parameter gradients accumulate per
+// node (qdot, wall flux) or per block (the two nu-dependent MRT rates), so the
+// result does not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include "lattice.cuh"
+#include "lbm_internal.cuh"
+#include "sp_device.cuh"
+
+namespace lbmk {
+
+namespace {
+
+typedef double R;
+
+__device__ __forceinline__ long long nidx(const SpParams &P, int i, int j) { return (long long)j * P.pitch + i; }
+
+// The link arriving at node (i, j) along q is an ordinary streaming link (its
+// source is inside the domain or wraps periodically).
+__device__ __forceinline__ bool streams_in(const SpParams &P, int i, int j, int cx, int cy, int xper, int yper) {
+  return entry_side(i, j, cx, cy, P.nx, P.ny, xper, yper) < 0;
+}
+
+// d(pre_p)/d(u_w) of the anti-BB outlet rule for outgoing direction o.
+__device__ __forceinline__ void dpre_duw(const SpParams &P, int o, R rw, R uwx, R uwy, R &gx, R &gy) {
+  const R c = P.c, ics2 = 1.0 / P.cs2;
+  const R cx = c * cx9(o), cy = c * cy9(o);
+  const R cu = cx * uwx + cy * uwy;
+  const R k = 2.0 * w9<R>(o) * rw;
+  gx = k * (cu * cx * ics2 * ics2 - uwx * ics2);
+  gy = k * (cu * cy * ics2 * ics2 - uwy * ics2);
+}
+
+// G = sum over the outlet's unknown populations p of Lam_pre_p * d(pre_p)/d(u_w) at
+// boundary node (bi, bj) of pressure side s; also returns u_w inputs.
+__device__ void outlet_G(const SpParams &P, const R *Xt, const R *LPn, int s, int bi, int bj, R &Gx, R &Gy) {
+  const int ii = bi + (s == 0) - (s == 1), jj = bj + (s == 2) - (s == 3);
+  R ub, vb, ui, vi;
+  post_velocity<R, R>(P, Xt, bi, bj, ub, vb);
+  post_velocity<R, R>(P, Xt, ii, jj, ui, vi);
+  const R uwx = ub + 0.5 * (ub - ui), uwy = vb + 0.5 * (vb - vi);
+  Gx = 0;
+  Gy = 0;
+  const long long nb = nidx(P, bi, bj);
+#pragma unroll
+  for (int p = 0; p < 9; p++) {
+    if (entry_side(bi, bj, cx9(p), cy9(p), P.nx, P.ny, P.xper, P.yper) != s) continue;
+    R gx, gy;
+    dpre_duw(P, opp9(p), (R)P.side[s].rho_w, uwx, uwy, gx, gy);
+    const R lam = LPn[p * P.plane + nb];
+    Gx += lam * gx;
+    Gy += lam * gy;
+  }
+}
+
+// Post-collision density and velocity of X at a node (for d u / d X).
+__device__ __forceinline__ void post_rho_u(const SpParams &P, const R *X, int i, int j, R &rho, R &ux, R &uy) {
+  const long long n = nidx(P, i, j);
+  R s = 0;
+#pragma unroll
+  for (int q = 0; q < 9; q++) s += X[q * P.plane + n];
+  rho = P.rho0 + s;
+  post_velocity<R, R>(P, X, i, j, ux, uy);
+}
+
+}  // namespace
+
+// Loss at the outlet column and the seed Lam_pre(N).  One thread per row j.
+__global__ void k_adj_loss(const SpParams P, const double *Ttarget, double *LP, double *grad_qdot, double *loss_rows) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P.ny) return;
+  const int i = P.nx - 1;
+  const R *src = (const R *)P.src;
+  const bool interior = false;
+  R g[5];
+  pull_g<R, R>(P, src, i, j, interior, g);
+  const long long n = nidx(P, i, j);
+  const R qd = P.qdot ? ((const R *)P.qdot)[n] : 0.0;
+  const R T = P.T0 + ((g[0] + g[1]) + (g[2] + g[3]) + g[4]) + 0.5 * P.dt * qd;
+  const R e = T - Ttarget[j];
+  loss_rows[j] = e * e / P.ny;
+  const R dLdT = 2.0 * e / P.ny;
+  R *LPg = LP + (long long)P.gbase * P.plane;
+#pragma unroll
+  for (int q = 0; q < 5; q++) LPg[q * P.plane + n] = dLdT;
+  grad_qdot[n] += 0.5 * P.dt * dLdT;
+}
+
+// One reverse step.  P.src = X_{t-1} (P.local = 1 when t = 0), Xt = X_t,
+// LPn = Lam_pre(t+1), LP = Lam_pre(t) (output).
+__global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double *__restrict__ Xt,
+                                                  const double *__restrict__ LPn, double *__restrict__ LP,
+                                                  double *grad_qdot, double *grad_flux2, double *grad_flux3,
+                                                  double *nu_partials) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  R dsnu = 0, dsq = 0;
+  if (i < P.nx && j < P.ny) {
+    const long long n = nidx(P, i, j);
+    const R c = P.c, ic = 1.0 / c;
+    // ---- (1) Lam_X(t) = P^T Lam_pre(t+1) at this node --------------------------
+    R lx[9], lg[5];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      R acc = 0;
+      // streaming consumer: node y + c_q pulls population q from here
+      int xi = i + cx9(q), xj = j + cy9(q);
+      if (P.xper) xi = wrap(xi, P.nx);
+      if (P.yper) xj = wrap(xj, P.ny);
+      if (xi >= 0 && xi < P.nx && xj >= 0 && xj < P.ny && streams_in(P, xi, xj, cx9(q), cy9(q), P.xper, P.yper))
+        acc += LPn[q * P.plane + nidx(P, xi, xj)];
+      // reflection consumer: the incoming p = opp(q) at this node built from X_q here
+      const int p = opp9(q);
+      const int side = entry_side(i, j, cx9(p), cy9(p), P.nx, P.ny, P.xper, P.yper);
+      if (side >= 0) acc += (P.side[side].kind == BC_PRESSURE ? -1.0 : 1.0) * LPn[p * P.plane + n];
+      lx[q] = acc;
+    }
+    // outlet velocity extrapolation u_w = 1.5 u(x_b) - 0.5 u(x_b - n)
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+      if (P.side[s].kind != BC_PRESSURE) continue;
+      const bool on = (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
+      const int bi = i - (s == 0) + (s == 1), bj = j - (s == 2) + (s == 3);  // boundary node outward of here
+      const bool inner = !on && ((s == 0 && i == 1) || (s == 1 && i == P.nx - 2) || (s == 2 && j == 1) ||
+                                 (s == 3 && j == P.ny - 2));
+      if (!on && !inner) continue;
+      R Gx, Gy;
+      if (on) outlet_G(P, Xt, LPn, s, i, j, Gx, Gy);
+      else outlet_G(P, Xt, LPn, s, bi, bj, Gx, Gy);
+      R rho, ux, uy;
+      post_rho_u(P, Xt, i, j, rho, ux, uy);
+      const R coef = on ? 1.5 : -0.5;
+#pragma unroll
+      for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * cx9(q) - ux) + Gy * (c * cy9(q) - uy)) / rho;
+    }
+    const R *LPng = LPn + (long long)P.gbase * P.plane;
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      R acc = 0;
+      int xi = i + cx5(q), xj = j + cy5(q);
+      if (P.txper) xi = wrap(xi, P.nx);
+      if (P.typer) xj = wrap(xj, P.ny);
+      if (xi >= 0 && xi < P.nx && xj >= 0 && xj < P.ny && streams_in(P, xi, xj, cx5(q), cy5(q), P.txper, P.typer))
+        acc += LPng[q * P.plane + nidx(P, xi, xj)];
+      const int p = opp5(q);
+      const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
+      if (side >= 0) {
+        const int tk = P.side[side].tkind;
+        if (tk == TBC_FLUX) acc += LPng[p * P.plane + n];
+        else if (tk == TBC_TEMP) acc -= LPng[p * P.plane + n];
+      }
+      // outflow consumer: the unknown q of an outflow side reads X_q of this node
+      const int qside = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
+      if (qside >= 0 && P.side[qside].tkind == TBC_OUTFLOW) acc += LPng[q * P.plane + n];
+      lg[q] = acc;
+    }
+    // wall heat flux gradient: pre_p = X_o + flux_coef q''(a) on flux sides
+#pragma unroll
+    for (int p = 1; p < 5; p++) {
+      const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
+      if (side >= 2 && P.side[side].tkind == TBC_FLUX) {
+        double *gf = side == 2 ? grad_flux2 : grad_flux3;
+        gf[i] += P.flux_coef * LPng[p * P.plane + n];
+      }
+    }
+
+    // ---- (2) pre(t) and the forward intermediates -----------------------------
+    const R *src = (const R *)P.src;
+    const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
+    R f[9], g[5];
+    pull_f<R, R>(P, src, i, j, interior, f);
+    pull_g<R, R>(P, src, i, j, interior, g);
+    Macro<R> m;
+    load_sources<R, R>(P, n, m);
+    moments<R, FLOW_MRT, TH_MRT>(P, f, g, m);
+    const R rho = m.rho, drho = m.drho;
+    const R hx = m.ux * ic, hy = m.uy * ic, usq = hx * hx + hy * hy;
+    const R Fx = m.Fx * ic, Fy = m.Fy * ic;
+    const R dt = P.dt;
+
+    // ---- (3) momentum MRT: transpose ------------------------------------------
+    // moments of Lam_X (same integer rows as the moments of f)
+    const R s14 = (lx[1] + lx[2]) + (lx[3] + lx[4]), s58 = (lx[5] + lx[6]) + (lx[7] + lx[8]);
+    const R d58 = lx[5] - lx[7], d68 = lx[6] - lx[8];
+    const R M_e = -4.0 * lx[0] - s14 + 2.0 * s58;
+    const R M_ep = 4.0 * lx[0] - 2.0 * s14 + s58;
+    const R M_qx = 2.0 * (lx[3] - lx[1]) + d58 - d68;
+    const R M_qy = 2.0 * (lx[4] - lx[2]) + d58 + d68;
+    const R M_xx = (lx[1] + lx[3]) - (lx[2] + lx[4]);
+    const R M_xy = (lx[5] + lx[7]) - (lx[6] + lx[8]);
+    // dL/dd_k = -(M Lam)_k / |row_k|^2
+    const R de = -M_e / 36.0, dep = -M_ep / 36.0, dqx = -M_qx / 12.0, dqy = -M_qy / 12.0;
+    const R dxx = -M_xx / 4.0, dxy = -M_xy / 4.0;
+    const R se = P.s_e, sep = P.s_eps, sq = P.s_q, snu = P.s_nu;
+    // dL/dm_k = s_k dL/dd_k; dL/deq_k = -s_k dL/dd_k
+    const R lme = se * de, lmep = sep * dep, lmqx = sq * dqx, lmqy = sq * dqy, lmxx = snu * dxx, lmxy = snu * dxy;
+    // equilibria of the moments
+    const R m_s14 = (f[1] + f[2]) + (f[3] + f[4]), m_s58 = (f[5] + f[6]) + (f[7] + f[8]);
+    const R mf58 = f[5] - f[7], mf68 = f[6] - f[8];
+    const R m_qx = 2.0 * (f[3] - f[1]) + mf58 - mf68, m_qy = 2.0 * (f[4] - f[2]) + mf58 + mf68;
+    const R m_xx = (f[1] + f[3]) - (f[2] + f[4]), m_xy = (f[5] + f[7]) - (f[6] + f[8]);
+    (void)m_s14;
+    (void)m_s58;
+    const R eq_qx = -rho * hx, eq_qy = -rho * hy, eq_xx = rho * (hx * hx - hy * hy), eq_xy = rho * hx * hy;
+    // nu enters through s_nu (stress moments) and s_q (third-order moments)
+    dsnu = dxx * ((m_xx - eq_xx) + 0.5 * dt * 2.0 * (hx * Fx - hy * Fy)) + dxy * ((m_xy - eq_xy) + 0.5 * dt * (hx * Fy + hy * Fx));
+    dsq = dqx * ((m_qx - eq_qx) - 0.5 * dt * Fx) + dqy * ((m_qy - eq_qy) - 0.5 * dt * Fy);
+    const R le = -se * de, lep = -sep * dep, lqx = -sq * dqx, lqy = -sq * dqy, lxx = -snu * dxx, lxy = -snu * dxy;
+    R l_drho = le * (-2.0 + 3.0 * usq) + lep * (1.0 - 3.0 * usq) + lqx * (-hx) + lqy * (-hy) + lxx * (hx * hx - hy * hy) +
+               lxy * (hx * hy);
+    R l_hx = le * (6.0 * rho * hx) + lep * (-6.0 * rho * hx) + lqx * (-rho) + lxx * (2.0 * rho * hx) + lxy * (rho * hy);
+    R l_hy = le * (6.0 * rho * hy) + lep * (-6.0 * rho * hy) + lqy * (-rho) + lxx * (-2.0 * rho * hy) + lxy * (rho * hx);
+    // forcing moments that depend on u
+    const R l_uF = -6.0 * (1.0 - 0.5 * se) * dt * de + 6.0 * (1.0 - 0.5 * sep) * dt * dep;
+    const R l_Fxx = -(1.0 - 0.5 * snu) * dt * dxx * 2.0, l_Fxy = -(1.0 - 0.5 * snu) * dt * dxy;
+    l_hx += l_uF * Fx + l_Fxx * Fx + l_Fxy * Fy;
+    l_hy += l_uF * Fy - l_Fxx * Fy + l_Fxy * Fx;
+    (void)drho;
+
+    // ---- (4) thermal D2Q5 MRT: transpose --------------------------------------
+    const R B0 = -((lg[0] + lg[1]) + (lg[2] + lg[3]) + lg[4]);
+    const R B1 = -(lg[1] - lg[3]), B2 = -(lg[2] - lg[4]);
+    const R B3 = -(-4.0 * lg[0] + ((lg[1] + lg[2]) + (lg[3] + lg[4])));
+    const R B4 = -((lg[1] + lg[3]) - (lg[2] + lg[4]));
+    const R t0 = B0 / 5.0, t1 = B1 / 2.0, t2 = B2 / 2.0, t3 = B3 / 20.0, t4 = B4 / 4.0;
+    const R sT = P.omegaT;
+    const R lm1 = sT * t1, lm2 = sT * t2, lm3 = t3, lm4 = t4;
+    const R lT = -sT * hx * t1 - sT * hy * t2 + (2.0 / 3.0) * t3;
+    l_hx += -sT * m.T * t1;
+    l_hy += -sT * m.T * t2;
+    grad_qdot[n] += 0.5 * dt * lT - dt * t0 + (dt / 3.0) * t3;
+
+    // ---- (5) back to the pre-collision populations ----------------------------
+    R out[14];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      const int cxq = cx9(q), cyq = cy9(q);
+      // transpose of the moment rows: sum_k M[k][q] lm_k
+      const R e_row = q == 0 ? -4.0 : (q <= 4 ? -1.0 : 2.0);
+      const R ep_row = q == 0 ? 4.0 : (q <= 4 ? -2.0 : 1.0);
+      const R qx_row = q == 0 ? 0.0 : (q <= 4 ? -2.0 * cxq : (R)cxq);
+      const R qy_row = q == 0 ? 0.0 : (q <= 4 ? -2.0 * cyq : (R)cyq);
+      const R xx_row = (q >= 1 && q <= 4) ? (R)(cxq * cxq - cyq * cyq) : 0.0;
+      const R xy_row = q >= 5 ? (R)(cxq * cyq) : 0.0;
+      R v = lx[q] + e_row * lme + ep_row * lmep + qx_row * lmqx + qy_row * lmqy + xx_row * lmxx + xy_row * lmxy;
+      v += l_drho + (l_hx * ((R)cxq - hx) + l_hy * ((R)cyq - hy)) / rho;
+      out[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      const R r1 = (R)cx5(q), r2 = (R)cy5(q);
+      const R r3 = q == 0 ? -4.0 : 1.0;
+      const R r4 = (q == 1 || q == 3) ? 1.0 : (q == 0 ? 0.0 : -1.0);
+      out[9 + q] = lg[q] + r1 * lm1 + r2 * lm2 + r3 * lm3 + r4 * lm4 + lT;
+    }
+#pragma unroll
+    for (int q = 0; q < 14; q++) LP[q * P.plane + n] = out[q];
+  }
+  // per-block, fixed-order sums of the nu-rate sensitivities
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dsnu += __shfl_down_sync(0xffffffffu, dsnu, o);
+    dsq += __shfl_down_sync(0xffffffffu, dsq, o);
+  }
+  __shared__ double sh[8][2];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) { sh[tid >> 5][0] = dsnu; sh[tid >> 5][1] = dsq; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x * blockDim.y) / 32; w++) { a += sh[w][0]; b += sh[w][1]; }
+    double *acc = nu_partials + 2ll * (blockIdx.y * gridDim.x + blockIdx.x);
+    acc[0] += a;
+    acc[1] += b;
+  }
+}
+
+__global__ void k_adj_final(const double *nu_partials, int nb, double *out2) {
+  const int lane = threadIdx.x;
+  double a = 0, b = 0;
+  for (int k = lane; k < nb; k += 32) { a += nu_partials[2 * k]; b += nu_partials[2 * k + 1]; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) { out2[0] = a; out2[1] = b; }
+}
+
+cudaError_t adj_loss(const SpParams &P, const double *Ttarget, double *LP, double *grad_qdot, double *loss_rows,
+                     cudaStream_t s) {
+  k_adj_loss<<<(P.ny + 127) / 128, 128, 0, s>>>(P, Ttarget, LP, grad_qdot, loss_rows);
+  return cudaGetLastError();
+}
+
+dim3 adj_grid(int nx, int ny) { return dim3((nx + 63) / 64, (ny + 3) / 4); }
+
+cudaError_t adj_step(const SpParams &P, const double *Xt, const double *LPn, double *LP, double *grad_qdot,
+                     double *grad_flux2, double *grad_flux3, double *nu_partials, cudaStream_t s) {
+  k_adj_step<<<adj_grid(P.nx, P.ny), dim3(64, 4), 0, s>>>(P, Xt, LPn, LP, grad_qdot, grad_flux2, grad_flux3,
+                                                          nu_partials);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_final(const double *nu_partials, int nb, double *out2, cudaStream_t s) {
+  k_adj_final<<<1, 32, 0, s>>>(nu_partials, nb, out2);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmk

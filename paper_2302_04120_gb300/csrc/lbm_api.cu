@@ -825,3 +825,173 @@ extern "C" lbm_status lbm_batch_autotune(lbm_batch_t b, int out_cfg[3]) {
   if (out_cfg) { out_cfg[0] = b->bx; out_cfg[1] = b->by; out_cfg[2] = b->grid; }
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Reverse-time adjoint of the fused step (D2Q9 MRT + D2Q5 MRT, FP64)
+// ---------------------------------------------------------------------------
+extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const double *T_target, double *loss,
+                                  double *g_q3, double *g_qwall, double *g_nu) {
+  if (!h || !T_target || !loss) return fail(h, LBM_ERR_ARG, "NULL argument");
+  const lbm_params &p = h->p;
+  if (p.phase || p.flow != LBM_D2Q9 || p.flow_op != LBM_MRT || p.thermal != LBM_D2Q5 || p.thermal_op != LBM_MRT)
+    return fail(h, LBM_ERR_ARG, "the adjoint covers single-phase D2Q9 MRT + D2Q5 MRT solves");
+  if (p.precision != LBM_FP64) return fail(h, LBM_ERR_ARG, "the adjoint runs in FP64");
+  if (p.nx < 2) return fail(h, LBM_ERR_ARG, "nx must be >= 2 (loss on the x+ column)");
+  if (steps < 1 || ckpt_every < 1) return fail(h, LBM_ERR_ARG, "steps and ckpt_every must be >= 1");
+  if (!h->initialised || !h->pre)
+    return fail(h, LBM_ERR_STATE, "call lbm_adjoint right after lbm_init_fields (it runs the forward itself)");
+  const int K = ckpt_every;
+  const long M = (steps + K - 1) / K;          // segments
+  const size_t sbytes = (size_t)h->nq * h->plane * sizeof(double);
+  const size_t pbytes = (size_t)h->plane * sizeof(double);
+  const int nx = p.nx, ny = p.ny;
+  dim3 ag = lbmk::adj_grid(nx, ny);
+  const int nblk = (int)(ag.x * ag.y);
+  double *ck = NULL, *seg = NULL, *lp = NULL, *gq = NULL, *gf = NULL, *nup = NULL, *tt = NULL, *lr = NULL, *o2 = NULL;
+  lbm_status st = LBM_OK;
+  cudaError_t e = cudaSuccess;
+#define ACU(call)                                                                       \
+  do {                                                                                  \
+    e = (call);                                                                         \
+    if (e != cudaSuccess) { st = fail(h, LBM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e)); goto done; } \
+  } while (0)
+#define AAL(ptr, bytes)                                                                 \
+  do {                                                                                  \
+    if (cudaMalloc(&(ptr), (bytes)) != cudaSuccess) { st = fail(h, LBM_ERR_NOMEM, "adjoint: cudaMalloc %zu B", (size_t)(bytes)); goto done; } \
+  } while (0)
+  {
+    AAL(ck, sbytes * (size_t)M);
+    AAL(seg, sbytes * (size_t)(K + 1));
+    AAL(lp, sbytes * 2);
+    AAL(gq, pbytes);
+    AAL(gf, sizeof(double) * 2 * nx);
+    AAL(nup, sizeof(double) * 2 * nblk);
+    AAL(tt, sizeof(double) * ny);
+    AAL(lr, sizeof(double) * ny);
+    AAL(o2, sizeof(double) * 2);
+    ACU(cudaMemsetAsync(gq, 0, pbytes, h->stream));
+    ACU(cudaMemsetAsync(gf, 0, sizeof(double) * 2 * nx, h->stream));
+    ACU(cudaMemsetAsync(nup, 0, sizeof(double) * 2 * nblk, h->stream));
+    ACU(cudaMemcpyAsync(tt, T_target, sizeof(double) * ny, cudaMemcpyHostToDevice, h->stream));
+    // forward with checkpoints: ck[m] = X_{mK-1} (ck[0] = pre-collision initial state)
+    ACU(cudaMemcpyAsync(ck, h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice, h->stream));
+    for (long t = 0; t < steps; t++) {
+      st = lbm_step(h, 1);
+      if (st != LBM_OK) goto done;
+      if ((t + 1) % K == 0 && (t + 1) / K < M)
+        ACU(cudaMemcpyAsync((char *)ck + sbytes * (size_t)((t + 1) / K), h->buf[h->cur], sbytes,
+                            cudaMemcpyDeviceToDevice, h->stream));
+    }
+    // loss at time N and the seed Lam_pre(N)
+    int cur = 0;
+    ACU(cudaMemsetAsync(lp, 0, sbytes * 2, h->stream));
+    SpParams P = sp_params(h, h->cur);
+    ACU(lbmk::adj_loss(P, tt, lp, gq, lr, h->stream));
+    for (long m = M - 1; m >= 0; m--) {
+      const long s0 = m * K, s1 = (m + 1) * K < steps ? (m + 1) * K - 1 : steps - 1;
+      // recompute X_{s0-1} .. X_{s1} into seg[0 .. s1-s0+1]
+      ACU(cudaMemcpyAsync(seg, (char *)ck + sbytes * (size_t)m, sbytes, cudaMemcpyDeviceToDevice, h->stream));
+      for (long k = 1; k <= s1 - s0 + 1; k++) {
+        SpParams Q = sp_params(h, 0);
+        Q.local = (m == 0 && k == 1) ? 1 : 0;
+        Q.src = (char *)seg + sbytes * (size_t)(k - 1);
+        Q.dst = (char *)seg + sbytes * (size_t)k;
+        ACU(lbmk::sp_step(Q, 0, lbmk::FLOW_MRT, lbmk::TH_MRT, h->block, h->stream));
+      }
+      for (long t = s1; t >= s0; t--) {
+        const long k = t - s0 + 1;
+        SpParams Q = sp_params(h, 0);
+        Q.local = (t == 0) ? 1 : 0;
+        Q.src = (char *)seg + sbytes * (size_t)(k - 1);
+        Q.dst = NULL;
+        const double *Xt = (const double *)((char *)seg + sbytes * (size_t)k);
+        double *LPn = (double *)((char *)lp + sbytes * (size_t)cur);
+        double *LPo = (double *)((char *)lp + sbytes * (size_t)(1 - cur));
+        ACU(lbmk::adj_step(Q, Xt, LPn, LPo, gq, gf, gf + nx, nup, h->stream));
+        cur = 1 - cur;
+      }
+    }
+    ACU(lbmk::adj_final(nup, nblk, o2, h->stream));
+    // results to the host
+    double *hl = (double *)malloc(sizeof(double) * ny);
+    double ho2[2];
+    if (!hl) { st = fail(h, LBM_ERR_NOMEM, "host allocation"); goto done; }
+    ACU(cudaMemcpyAsync(hl, lr, sizeof(double) * ny, cudaMemcpyDeviceToHost, h->stream));
+    ACU(cudaMemcpyAsync(ho2, o2, sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+    if (g_qwall) ACU(cudaMemcpyAsync(g_qwall, gf, sizeof(double) * 2 * nx, cudaMemcpyDeviceToHost, h->stream));
+    if (g_q3) {
+      // dL/dq''' = dL/dqdot / (rho0 c_p); unpitch on the host
+      double *tmp = (double *)malloc(pbytes);
+      if (!tmp) { free(hl); st = fail(h, LBM_ERR_NOMEM, "host allocation"); goto done; }
+      e = cudaMemcpyAsync(tmp, gq, pbytes, cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e == cudaSuccess)
+        for (int j = 0; j < ny; j++)
+          for (int i = 0; i < nx; i++) g_q3[(size_t)j * nx + i] = tmp[(size_t)j * h->pitch + i] / (p.rho0 * p.cp);
+      free(tmp);
+      if (e != cudaSuccess) { free(hl); st = fail(h, LBM_ERR_CUDA, "gradient copy: %s", cudaGetErrorString(e)); goto done; }
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { free(hl); st = fail(h, LBM_ERR_CUDA, "adjoint: %s", cudaGetErrorString(e)); goto done; }
+    double L = 0;
+    for (int j = 0; j < ny; j++) L += hl[j];
+    free(hl);
+    *loss = L;
+    if (g_nu) {
+      // s_nu = dt/tau, s_q = dt omega_q(1/tau), tau = nu/c_s^2 + dt/2
+      const double dt = p.dt, tau = h->tau, w = 1.0 / tau;
+      const double dw_dnu = -1.0 / (tau * tau * h->cs2);
+      const double dsnu = dt * dw_dnu;
+      const double a = 3.0 / dt - w;
+      const double dwq_dw = -3.0 / (dt * dt * a * a);
+      const double dsq = dt * dwq_dw * dw_dnu;
+      *g_nu = ho2[0] * dsnu + ho2[1] * dsq;
+    }
+  }
+done:
+  cudaStreamSynchronize(h->stream);
+  cudaFree(ck); cudaFree(seg); cudaFree(lp); cudaFree(gq); cudaFree(gf); cudaFree(nup); cudaFree(tt); cudaFree(lr);
+  cudaFree(o2);
+#undef ACU
+#undef AAL
+  return st;
+}
+
+// ---------------------------------------------------------------------------
+// Launch-shape autotuning of the single-solve step kernel
+// ---------------------------------------------------------------------------
+extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  if (!h->initialised) return fail(h, LBM_ERR_STATE, "not initialised");
+  if (two_phase(h)) return fail(h, LBM_ERR_ARG, "two-phase solves use a fixed 32 x 8 tile");
+  int flow, th;
+  sp_kinds(h, &flow, &th);
+  static const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+  // The timed launches repeat the next step (same source, same destination), so the
+  // stored state does not change.
+  SpParams P = sp_params(h, h->cur);
+  cudaEvent_t e0, e1;
+  CU(h, cudaEventCreate(&e0));
+  CU(h, cudaEventCreate(&e1));
+  float best = 1e30f;
+  dim3 bb = h->block;
+  lbm_status st = LBM_OK;
+  for (const auto &sh : shapes) {
+    dim3 b(sh[0], sh[1]);
+    cudaError_t e = lbmk::sp_step(P, h->p.precision, flow, th, b, h->stream);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < 5 && e == cudaSuccess; r++) e = lbmk::sp_step(P, h->p.precision, flow, th, b, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = fail(h, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e)); break; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; bb = b; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  h->block = bb;
+  if (out_block) { out_block[0] = (int)bb.x; out_block[1] = (int)bb.y; }
+  return LBM_OK;
+}

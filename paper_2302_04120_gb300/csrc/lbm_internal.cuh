@@ -69,6 +69,14 @@ int sp_integral_blocks(int nx, int ny);
 // Convert nx*ny double planes into pitched storage planes (sources, forces).
 cudaError_t to_storage(const double *in, void *out, int nx, int ny, int pitch, int nplanes,
                        long long plane, int prec, double scale, cudaStream_t s);
+// Adjoint (adjoint.cu): loss at the outlet column + seed, one reverse step, final sum.
+cudaError_t adj_loss(const SpParams &P, const double *Ttarget, double *LP, double *grad_qdot, double *loss_rows,
+                     cudaStream_t s);
+cudaError_t adj_step(const SpParams &P, const double *Xt, const double *LPn, double *LP, double *grad_qdot,
+                     double *grad_flux2, double *grad_flux3, double *nu_partials, cudaStream_t s);
+cudaError_t adj_final(const double *nu_partials, int nb, double *out2, cudaStream_t s);
+dim3 adj_grid(int nx, int ny);
+
 // Text for lbm_last_error(NULL) from entry points that take no handle.
 void set_global_error(const char *msg);
 

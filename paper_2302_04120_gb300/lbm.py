@@ -112,6 +112,10 @@ def _extra_signatures(L):
     L.lbm_batch_last_error.restype = C.c_char_p
     L.lbm_batch_destroy.argtypes = [C.c_void_p]
     L.lbm_batch_destroy.restype = None
+    L.lbm_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    L.lbm_autotune.restype = C.c_int
+    L.lbm_adjoint.argtypes = [C.c_void_p, C.c_long, C.c_int, C.c_void_p, _dp, C.c_void_p, C.c_void_p, _dp]
+    L.lbm_adjoint.restype = C.c_int
 
 
 def _check(h, st):
@@ -244,6 +248,21 @@ def lbm_destroy(h):
     lib().lbm_destroy(h)
 
 
+def lbm_adjoint(h, steps, ckpt_every, T_target, nx, ny, want_q3=True, want_qwall=True, want_nu=True):
+    """Forward run + reverse-time adjoint: returns (loss, dL/dq3 (ny, nx), dL/dq_wall (2, nx), dL/dnu)."""
+    tt = np.ascontiguousarray(np.asarray(T_target, dtype=np.float64))
+    assert tt.size == ny
+    loss = C.c_double()
+    g3 = np.zeros((ny, nx)) if want_q3 else None
+    gw = np.zeros((2, nx)) if want_qwall else None
+    gn = C.c_double()
+    _check(h, lib().lbm_adjoint(h, int(steps), int(ckpt_every), tt.ctypes.data_as(C.c_void_p), C.byref(loss),
+                                None if g3 is None else g3.ctypes.data_as(C.c_void_p),
+                                None if gw is None else gw.ctypes.data_as(C.c_void_p),
+                                C.byref(gn) if want_nu else None))
+    return loss.value, g3, gw, (gn.value if want_nu else None)
+
+
 def lbm_field_integrals_noalloc(rho, ux, uy, phi, nx, ny, dx, c, out4, stream=None):
     """Allocation-free integrals of device fields (torch CUDA float64 tensors or raw
     device addresses) into the device array out4; returns the status code."""
@@ -331,6 +350,11 @@ class Solver:
 
     def integrals(self):
         return lbm_integrals(self.h)
+
+    def autotune(self):
+        blk = (C.c_int * 2)()
+        _check(self.h, lib().lbm_autotune(self.h, blk))
+        return blk[0], blk[1]
 
     def check(self):
         return lbm_check(self.h)

@@ -227,3 +227,16 @@ def test_state_roundtrip_device_moments_and_integrals():
     s.set_state(bad.view(np.uint8))
     assert s.check() == lbm.LBM_ERR_DIVERGED
     assert "non-finite" in lbm.lbm_last_error(s.h)
+
+
+def test_autotune_keeps_state_and_results():
+    """Autotuning the step's block shape neither advances nor changes the solution."""
+    w = wl.channel(nx=100, ny=42, steps=30, Re=100 * 42 / 256)
+    a = run_gpu(w, FP64, steps=10)
+    blk = a.autotune()
+    assert blk[0] * blk[1] % 32 == 0 and a.steps == 10
+    a.step(20)
+    b = run_gpu(w, FP64, steps=30)
+    ma, mb = a.moments(), b.moments()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
