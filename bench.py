@@ -104,6 +104,8 @@ def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY):
     w = wl.channel(nx=nx, ny=ny, steps=0, Re=100.0 * ny / CELLS_NY)
     s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
     s.apply_workload(w)
+    s.step(1)
+    block = s.autotune()                     # the library's block-shape autotuner
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     flush.fill_(1.0)
     sink = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -122,7 +124,7 @@ def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY):
     chk = s.check()
     s.close()
     del flush
-    return times_ms, chk
+    return times_ms, chk, block
 
 
 def _e2e(prec, steps, warmup, stream, torch):
@@ -153,6 +155,125 @@ def _e2e(prec, steps, warmup, stream, torch):
     return el, 2 * qf.nbytes, 4 * 8
 
 
+def _batch_run(steps, stream, torch):
+    """The batched workload: 256 seeded channels of uneven size (1.5e8 nodes, FP32
+    deviation storage), one launch per step with autotuned tiles, against the same
+    channels stepped one by one (one launch per channel per step).  The state
+    (16.8 GB) is far larger than L2, so no flush is needed."""
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    specs = wl.channel_batch_specs()
+    b = lbm.Batch([wl.channel(nx=sp["nx"], ny=sp["ny"], steps=0, Re=sp["Re"], Pr=sp["Pr"], dx=sp["dx"],
+                              dt=sp["dt"])["params"] for sp in specs], precision=1, stream=stream.cuda_stream)
+    for ch, sp in zip(b.channels, specs):
+        w = wl.channel_from_spec(sp, steps=0)
+        for bc in w["bcs"]:
+            ch.set_bc(*bc)
+        ch.init(**w["init"])
+        del w
+    cells = sum(sp["nx"] * sp["ny"] for sp in specs)
+    b.step(2)
+    cfg = b.autotune()
+    b.step(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    chk = min(c.check() for c in b.channels[:4])
+    e0.record(stream)
+    for _ in range(steps):
+        for c in b.channels:
+            lbm.lbm_step(c.h, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_one = e0.elapsed_time(e1) / 1e3
+    b.close()
+    return dict(workload="channel_batch_256_seed4", channels=len(specs), nodes=cells, steps=steps,
+                value=round(cells * steps / t_batch / 1e6, 1), unit="MLUPS",
+                one_by_one=round(cells * steps / t_one / 1e6, 1), speedup=round(t_one / t_batch, 3),
+                achieved_GBps=round(112 * cells * steps / t_batch / 1e9, 1), tile=list(cfg), status=int(chk),
+                graph="pairs of steps replayed from a CUDA graph")
+
+
+def _adjoint_run(torch):
+    """The gradient workload: 1024 x 128 channel (FP64), 2000 steps, checkpoints every
+    100; wall time of the forward alone against forward + reverse sweep (lbm_adjoint)."""
+    import numpy as np
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    w = wl.adjoint_channel()
+    nx, ny, steps = 1024, 128, 2000
+
+    def fresh():
+        s = lbm.Solver(w["params"], precision=0)
+        for bc in w["bcs"]:
+            s.set_bc(*bc)
+        s.set_source(w["q3"], None)
+        s.init(**w["init"])
+        return s
+
+    s = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(steps)
+    s.moments(lbm.LBM_T)
+    t_fwd = time.perf_counter() - t0
+    s.close()
+    target = np.full(ny, 300.0) + 0.01 * np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
+    s = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_adjoint(s.h, steps, 100, target, nx, ny)
+    t_adj = time.perf_counter() - t0
+    s.close()
+    return dict(workload="channel_adjoint_1024x128_2000steps", forward_s=round(t_fwd, 4),
+                gradient_s=round(t_adj, 4), ratio=round(t_adj / t_fwd, 2), checkpoint_every=100,
+                dtype="f64", gradients="heat source per cell, wall heat flux per node, viscosity",
+                note="gradient_s covers the forward with checkpoints, the segment recomputes and the reverse sweep")
+
+
+def _two_phase_run(steps, stream, torch):
+    """The bubble workload (512 x 512, saturated water 25 C): per-step time of the two
+    launches (phi pass + collide pass) with an L2 flush between steps, FP32 (FP64 u/p
+    recovery) and FP64; plus a 4096 x 4096 roofline-size run of the same kernels."""
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush.fill_(1.0)
+    out = {}
+    for tag, n, R, prec, nst in (("fp32", 512, 64.0, 1, steps), ("fp64", 512, 64.0, 0, max(steps // 4, 20)),
+                                 ("fp32_4096", 4096, 512.0, 1, max(steps // 10, 10))):
+        w = wl.bubble(n=n, R_cells=R, W_cells=5.0, steps=0)
+        s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
+        s.init(**w["init"])
+        with torch.cuda.stream(stream):
+            s.step(5)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+            torch.cuda.synchronize()
+            for k in range(nst):
+                flush.sum()
+                ev[k][0].record(stream)
+                s.step(1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        t = statistics.mean(a.elapsed_time(b) for a, b in ev) / 1e3
+        chk = s.check()
+        s.close()
+        bpc = 128 if prec == 1 else 256
+        out[tag] = dict(nodes=n * n, value=round(n * n / t / 1e6, 1), unit="MLUPS", ms_per_step=round(t * 1e3, 4),
+                        achieved_GBps=round(bpc * n * n / t / 1e9, 1), status=int(chk))
+    del flush
+    peak, _ = _peaks()
+    out["workload"] = "bubble_512x512_R64_sat_water_25C"
+    out["frac_fp32_4096"] = round(out["fp32_4096"]["achieved_GBps"] / peak, 4)
+    out["mixed_over_fp64"] = round(out["fp32"]["value"] / out["fp64"]["value"], 2)
+    out["bytes_per_node"] = {"fp32": 128, "fp64": 256}
+    return out
+
+
 def _cpu_baseline(budget_s=12.0):
     """The FP64 oracle as it stands, on the host cores, on a 256-column slice of the
     same channel (inlet section, all 256 rows), as many steps as fit ~12 s."""
@@ -176,22 +297,24 @@ def _cpu_baseline(budget_s=12.0):
                 sample=f"channel 256x{CELLS_NY} slice of the 2048x{CELLS_NY} workload, {n} steps, FP64, OpenMP")
 
 
-def _traffic_from_profile(kernel_tag):
-    """Per-launch DRAM bytes recorded from an ncu capture, if the kernel source is
-    unchanged since (profiles/dram_traffic.txt: tag bytes source_hash)."""
+def _traffic_from_profile(kernel_tag, block=None):
+    """Per-launch DRAM bytes recorded from an ncu capture, if the kernel source and
+    the launch block are unchanged since (profiles/dram_traffic.txt: tag bytes
+    source_hash block_x block_y)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     h = hashlib.sha1()
-    for f in ("step_sp.cu", "lattice.cuh", "lbm_internal.cuh"):
+    for f in ("step_sp.cu", "sp_device.cuh", "lattice.cuh", "lbm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2302_04120_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     cur = h.hexdigest()[:12]
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == kernel_tag and parts[2] == cur:
-            return float(parts[1])
+        if len(parts) >= 5 and parts[0] == kernel_tag and parts[2] == cur:
+            if block is None or [int(parts[3]), int(parts[4])] == list(block):
+                return float(parts[1])
     return None
 
 
@@ -207,12 +330,12 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     cells = CELLS_NX * CELLS_NY
     # FP64 plain form (same grid), fewer steps: it is ALU-bound on GB300
-    t64, chk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch)
+    t64, chk64, blk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        t32, chk32 = _gpu_run(1, args.steps, args.warmup, stream, torch)
+        t32, chk32, blk32 = _gpu_run(1, args.steps, args.warmup, stream, torch)
     torch.cuda.synchronize()
     total_s = sum(t32) / 1e3
     if ws > 1:
@@ -220,8 +343,11 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_s = float(tt.item())
     # roofline-size variant: 8192 x 4096 nodes, 3.8 GB of state (>> 129 MB L2)
-    tsc, chksc = _gpu_run(1, max(args.steps // 20, 20), args.warmup, stream, torch, nx=8192, ny=4096)
+    tsc, chksc, blksc = _gpu_run(1, max(args.steps // 20, 20), args.warmup, stream, torch, nx=8192, ny=4096)
     e2e_s, h2d, d2h = _e2e(1, min(args.steps, 500), args.warmup, stream, torch)
+    batch = _batch_run(min(args.steps, 100), stream, torch) if not args.no_batch else None
+    adjoint = _adjoint_run(torch) if not args.no_adjoint else None
+    two_phase = _two_phase_run(min(args.steps, 200), stream, torch) if not args.no_two_phase else None
     e2e_steps = min(args.steps, 500)
     if rank != 0:
         if ws > 1:
@@ -253,18 +379,22 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach32 / peak, 4), "peak_source": peak_kind,
-                     "traffic": _traffic_from_profile("k_step_fp32_mrt_mrt_2048x256"),
-                     "kernel": "k_step<1,FLOW_MRT,TH_MRT>", "algorithmic_bytes_per_launch": BYTES_PER_CELL[1] * cells},
+                     "traffic": _traffic_from_profile("k_step_fp32_mrt_mrt_2048x256", blk32),
+                     "kernel": "k_step<1,FLOW_MRT,TH_MRT>", "algorithmic_bytes_per_launch": BYTES_PER_CELL[1] * cells,
+                     "block": list(blk32)},
         "roofline_scaled": {"workload": "channel_d2q9mrt_d2q5mrt_8192x4096", "bound": "hbm",
                             "value": round(8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e6, 1), "unit_value": "MLUPS",
                             "achieved": round(BYTES_PER_CELL[1] * 8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e9, 1),
                             "peak": peak, "unit": "GB/s",
                             "frac": round(BYTES_PER_CELL[1] * 8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e9 / peak, 4),
-                            "steps": len(tsc), "status": int(chksc)},
+                            "steps": len(tsc), "status": int(chksc), "block": list(blksc)},
         "fp64": {"value": round(cells / avg64 / 1e6, 1), "unit": "MLUPS", "steps": len(t64),
                  "achieved_GBps": round(ach64, 1), "frac": round(ach64 / peak, 4), "dtype": "f64",
                  "status": int(chk64)},
         "mixed_over_fp64": round(avg64 / avg32, 2),
+        "batch": batch,
+        "adjoint": adjoint,
+        "two_phase": two_phase,
         "e2e": {"value": round(cells * e2e_steps / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                 "api": "lbm_set_bc x2 (pinned host q'') + lbm_step(1) + lbm_integrals (host)"},
@@ -322,6 +452,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-two-phase", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

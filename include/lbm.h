@@ -105,6 +105,10 @@ enum { LBM_RHO = 1, LBM_UX = 2, LBM_UY = 4, LBM_T = 8, LBM_P = 16, LBM_PHI = 32 
  *  omega_e_dt, omega_eps_dt: free MRT rates times dt (paper: between 1 and 2; default 1).
  *  body_force uniform body force F_b [N m^-3].
  *  u_prescribed velocity used when flow == LBM_NONE [m s^-1].
+ *  gravity, beta_exp, T_ref, rho_ref: Boussinesq two-way coupling of App. D, Eq. buoyancy_force:
+ *             F_b = -rho_ref beta_exp (T - T_ref) g added to the momentum force with the
+ *             node's temperature of the same step (beta_exp = 0 disables it).  Needs
+ *             flow = D2Q9 and thermal = D2Q5.
  */
 typedef struct {
   int flow, flow_op, thermal, thermal_op, phase, z_op, nu_rule, literal, precision;
@@ -115,6 +119,8 @@ typedef struct {
   double omega_e_dt, omega_eps_dt;
   double body_force[2];
   double u_prescribed[2];
+  double gravity[2];
+  double beta_exp, T_ref, rho_ref;
 } lbm_params;
 
 /* Fill *p with defaults: D2Q9 BGK, no thermal, single phase, FP64, water-like

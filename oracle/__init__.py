@@ -39,6 +39,7 @@ class OrcParams(C.Structure):
         ("omega_e_dt", C.c_double), ("omega_eps_dt", C.c_double),
         ("Fb", C.c_double * 2), ("u_prescribed", C.c_double * 2),
         ("conv_coef", C.c_double), ("T_inf", C.c_double),
+        ("gravity", C.c_double * 2), ("beta_exp", C.c_double), ("T_ref", C.c_double), ("rho_ref", C.c_double),
     ]
 
 
@@ -97,7 +98,7 @@ _DEFAULTS = dict(flow=9, flow_op=0, thermal=0, thermal_op=0, phase=0, z_op=1, nu
                  literal=0, rho0=1000.0, nu=1e-6, cp=4180.0, k=0.6, T0=300.0, rho_l=0.0,
                  rho_g=0.0, nu_l=0.0, nu_g=0.0, sigma=0.0, W=1.0, mobility=0.0,
                  omega_e_dt=1.0, omega_eps_dt=1.0, Fb=(0.0, 0.0), u_prescribed=(0.0, 0.0),
-                 conv_coef=0.0, T_inf=0.0)
+                 conv_coef=0.0, T_inf=0.0, gravity=(0.0, 0.0), beta_exp=0.0, T_ref=0.0, rho_ref=0.0)
 
 
 class Oracle:
@@ -114,7 +115,7 @@ class Oracle:
         s = OrcParams()
         for k in _PARAM_KEYS:
             v = full[k]
-            if k in ("Fb", "u_prescribed"):
+            if k in ("Fb", "u_prescribed", "gravity"):
                 getattr(s, k)[0] = float(v[0])
                 getattr(s, k)[1] = float(v[1])
             else:

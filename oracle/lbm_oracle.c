@@ -72,6 +72,8 @@ typedef struct {
   double Fb[2];                     /* uniform body force, N m^-3              */
   double u_prescribed[2];           /* velocity used when flow == 0            */
   double conv_coef, T_inf;          /* lagged sink: qdot -= conv_coef (T_prev - T_inf) */
+  double gravity[2];                /* Boussinesq buoyancy (App. D): F_b = -rho_ref beta_exp (T - T_ref) g */
+  double beta_exp, T_ref, rho_ref;
 } orc_params;
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3 };
@@ -362,15 +364,37 @@ static int along(int side, int x, int y) { return side < 2 ? y : x; }
 /* ------------------------------------------------------------------------- */
 /* Single-phase step                                                         */
 /* ------------------------------------------------------------------------- */
+/* Force on node n: uniform body force + per-cell field + Boussinesq buoyancy of
+   Eq. buoyancy_force, F_b = -rho_ref beta_exp (T - T_ref) g, with T of this step. */
+static void force_at(const orc_t *o, int n, double *Fx, double *Fy) {
+  const orc_params *p = &o->p;
+  int N = o->N;
+  *Fx = p->Fb[0] + (o->force ? o->force[n] : 0.0);
+  *Fy = p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
+  if (p->thermal && p->beta_exp != 0.0) {
+    double b = -p->rho_ref * p->beta_exp * (o->T[n] - p->T_ref);
+    *Fx += b * p->gravity[0];
+    *Fy += b * p->gravity[1];
+  }
+}
+
 static void moments_single(orc_t *o) {
   const orc_params *p = &o->p;
   int N = o->N;
 #pragma omp parallel for schedule(static)
   for (int n = 0; n < N; n++) {
-    double Fx = p->Fb[0] + (o->force ? o->force[n] : 0.0);
-    double Fy = p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
+    if (p->thermal) {
+      double qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;   /* qdot = q'''/(rho c_p) */
+      /* lagged convective sink of the fuse problem: uses T of the previous step (R24) */
+      if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->Tprev[n] - p->T_inf);
+      double s = 0;
+      for (int i = 0; i < 5; i++) s += o->g[i * N + n];
+      o->T[n] = s + 0.5 * p->dt * qd;                          /* Eq. zero_moment_g */
+    }
     if (p->flow) {
-      /* Eqs. zero_moment_f, first_moment_f */
+      /* Eqs. zero_moment_f, first_moment_f (force includes buoyancy of T(t)) */
+      double Fx, Fy;
+      force_at(o, n, &Fx, &Fy);
       double rho = 0, jx = 0, jy = 0;
       for (int i = 0; i < 9; i++) {
         double fi = o->f[i * N + n];
@@ -381,14 +405,6 @@ static void moments_single(orc_t *o) {
       o->rho[n] = rho;
       o->ux[n] = (jx + 0.5 * p->dt * Fx) / rho;
       o->uy[n] = (jy + 0.5 * p->dt * Fy) / rho;
-    }
-    if (p->thermal) {
-      double qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;   /* qdot = q'''/(rho c_p) */
-      /* lagged convective sink of the fuse problem: uses T of the previous step (R24) */
-      if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->Tprev[n] - p->T_inf);
-      double s = 0;
-      for (int i = 0; i < 5; i++) s += o->g[i * N + n];
-      o->T[n] = s + 0.5 * p->dt * qd;                          /* Eq. zero_moment_g */
     }
   }
 }
@@ -418,8 +434,8 @@ static void collide_single(orc_t *o) {
     double ux = o->ux[n], uy = o->uy[n];
     if (p->flow) {
       double rho = o->rho[n];
-      double Fx = p->Fb[0] + (o->force ? o->force[n] : 0.0);
-      double Fy = p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
+      double Fx, Fy;
+      force_at(o, n, &Fx, &Fy);
       double fv[9], fe[9], fh[9];
       for (int i = 0; i < 9; i++) {
         fv[i] = o->f[i * N + n];

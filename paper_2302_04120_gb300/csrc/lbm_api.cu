@@ -123,6 +123,12 @@ static SpParams sp_params(const lbm_t h, int from_buf) {
     const double tau_sg = (p.literal & 1) ? h->tau : h->tauT;  // reading R1
     P.tsrc_fac = 1.0 - p.dt / (2.0 * tau_sg);
     P.flux_coef = p.dt / (p.dx * p.rho0 * p.cp);
+    if (p.flow && p.beta_exp != 0.0) {
+      P.buoy = 1;
+      P.bgx = -p.rho_ref * p.beta_exp * p.gravity[0];
+      P.bgy = -p.rho_ref * p.beta_exp * p.gravity[1];
+      P.T_ref = p.T_ref;
+    }
   }
   P.qdot = h->d_qdot;
   P.force = h->d_force;
@@ -143,6 +149,14 @@ static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {
   P.beta = 12.0 * p.sigma / p.W;   // beta = 12 sigma / W
   P.W = p.W;
   P.tauphi = h->tauphi;
+  P.inv_cs2 = 1.0 / h->cs2;
+  P.g3 = 3.0 / p.dx;
+  P.l6 = 6.0 / (p.dx * p.dx);
+  P.inv_cs2dt = 1.0 / (h->cs2 * p.dt);
+  P.om_h = p.dt / h->tauphi;
+  P.sfac_h = (1.0 - p.dt / (2.0 * h->tauphi)) * p.dt;
+  P.aint_coef = 4.0 * h->cs2 / p.W;
+  P.inv_dt = 1.0 / p.dt;
   P.nu_rule = p.nu_rule;
   P.z_mrt = p.z_op == LBM_MRT;
   P.qy_literal = (p.literal & 2) ? 1 : 0;
@@ -181,6 +195,8 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   } else if (!(p.rho0 > 0)) {
     return fail(NULL, LBM_ERR_ARG, "rho0 must be positive");
   }
+  if (p.beta_exp != 0.0 && (p.flow != LBM_D2Q9 || p.thermal != LBM_D2Q5 || p.phase != LBM_NONE))
+    return fail(NULL, LBM_ERR_ARG, "buoyancy needs a single-phase D2Q9 flow with a D2Q5 thermal LBE");
   if (!(p.omega_e_dt > 0 && p.omega_e_dt < 2) || !(p.omega_eps_dt > 0 && p.omega_eps_dt < 2))
     return fail(NULL, LBM_ERR_ARG, "free MRT rates times dt must lie in (0, 2)");
 
@@ -836,6 +852,7 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
   if (p.phase || p.flow != LBM_D2Q9 || p.flow_op != LBM_MRT || p.thermal != LBM_D2Q5 || p.thermal_op != LBM_MRT)
     return fail(h, LBM_ERR_ARG, "the adjoint covers single-phase D2Q9 MRT + D2Q5 MRT solves");
   if (p.precision != LBM_FP64) return fail(h, LBM_ERR_ARG, "the adjoint runs in FP64");
+  if (p.beta_exp != 0.0) return fail(h, LBM_ERR_ARG, "the adjoint does not cover the buoyancy coupling");
   if (p.nx < 2) return fail(h, LBM_ERR_ARG, "nx must be >= 2 (loss on the x+ column)");
   if (steps < 1 || ckpt_every < 1) return fail(h, LBM_ERR_ARG, "steps and ckpt_every must be >= 1");
   if (!h->initialised || !h->pre)

@@ -35,6 +35,9 @@ struct SpParams {
   double omegaT;          // dt/tau_T
   double tsrc_fac;        // BGK thermal source prefactor (1 - dt/(2 tau_sg))
   double flux_coef;       // dt / (dx rho0 cp): q'' -> K per step (Eq. BB_T, lambda = 1)
+  // Boussinesq buoyancy (App. D): F += (bgx, bgy) (T - T_ref), (bgx, bgy) = -rho_ref beta_exp g
+  int buoy;
+  double bgx, bgy, T_ref;
   // optional per-cell fields (storage precision, pitched planes)
   const void *qdot;       // thermal source qdot [K/s], or null
   const void *force;      // 2 planes F_x, F_y [N m^-3], or null

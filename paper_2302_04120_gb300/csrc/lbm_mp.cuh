@@ -12,6 +12,9 @@ struct MpParams {
   double c, cs2, dt, dx;
   double rho_l, rho_g, nu_l, nu_g;
   double kappa, beta, W, tauphi;
+  // derived constants (host-side): 1/c_s^2, 3/dx, 6/dx^2, 1/(c_s^2 dt), dt/tau_phi,
+  // (1 - dt/(2 tau_phi)) dt, 4 c_s^2 / W, 1/dt
+  double inv_cs2, g3, l6, inv_cs2dt, om_h, sfac_h, aint_coef, inv_dt;
   int nu_rule, z_mrt, qy_literal;
   double Fx, Fy;
   const void *force;  // 2 planes or null

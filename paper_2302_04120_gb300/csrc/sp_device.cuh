@@ -53,6 +53,17 @@ __device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, i
     Fx += (R)fo[n];
     Fy += (R)fo[P.plane + n];
   }
+  if (P.buoy) {
+    // buoyancy of T(t) = T0 + sum g* - dt qdot / 2 at this node
+    const S *gs = src + (long long)P.gbase * P.plane;
+    R sg = (R)0;
+#pragma unroll
+    for (int q = 0; q < 5; q++) sg += (R)gs[q * P.plane + n];
+    const R qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
+    const R dT = ((R)P.T0 - (R)P.T_ref) + sg - (R)0.5 * (R)P.dt * qd;
+    Fx += (R)P.bgx * dT;
+    Fy += (R)P.bgy * dT;
+  }
   ux = (jx - (R)0.5 * (R)P.dt * Fx) / rho;
   uy = (jy - (R)0.5 * (R)P.dt * Fy) / rho;
 }
@@ -190,6 +201,17 @@ __device__ __forceinline__ void load_sources(const SpParams &P, long long n, Mac
 
 template <typename R, int FLOW, int TH>
 __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R g[5], Macro<R> &m) {
+  if (TH != TH_NONE) {
+    // Eq. zero_moment_g
+    m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    m.T = (R)P.T0 + m.sumg + (R)0.5 * (R)P.dt * m.qd;
+    if (FLOW != FLOW_NONE && P.buoy) {
+      // Boussinesq buoyancy with this step's temperature (Eq. buoyancy_force)
+      const R dT = ((R)P.T0 - (R)P.T_ref) + m.sumg + (R)0.5 * (R)P.dt * m.qd;
+      m.Fx += (R)P.bgx * dT;
+      m.Fy += (R)P.bgy * dT;
+    }
+  }
   if (FLOW != FLOW_NONE) {
     // Eqs. zero_moment_f and first_moment_f
     m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
@@ -205,11 +227,6 @@ __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R
     m.rho = (R)P.rho0;
     m.ux = (R)P.ux_pres;
     m.uy = (R)P.uy_pres;
-  }
-  if (TH != TH_NONE) {
-    // Eq. zero_moment_g
-    m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    m.T = (R)P.T0 + m.sumg + (R)0.5 * (R)P.dt * m.qd;
   }
 }
 

@@ -65,62 +65,69 @@ __global__ void __launch_bounds__(256) k_mp_phi(const MpParams P) {
   ((S *)P.phi)[(long long)j * P.pitch + i] = (S)((h[0] + h[1]) + (h[2] + h[3]) + h[4]);
 }
 
-// Macroscopic state of a node (the FP64 recovery of rho, u, p).
+// Macroscopic state of a node.  The order parameter, its stencils, the chemical
+// potential, the forces and the relaxation rates are in the working precision R;
+// rho, u and p -- the recovery that divides by rho_g ~ 0.023 at the interface --
+// are in FP64 in both forms.
+template <typename R>
 struct MpMacro {
-  double phi, rho, ux, uy, p, mu, gx, gy, nxv, nyv, Fx, Fy, drx, dry, tau;
+  R phi, mu, gx, gy, nxv, nyv, Fx, Fy, drx, dry, wb;  // wb = dt / tau
+  double rho, ux, uy, p;
 };
 
 // Gradient/Laplacian from the shared tile, then rho, nu, tau, F, u, p.
 template <typename R>
 __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX + 2], int tx, int ty,
                                          const double zsum_x, const double zsum_y, const double zsum_nz,
-                                         double fext_x, double fext_y, MpMacro &m) {
+                                         R fext_x, R fext_y, MpMacro<R> &m) {
   // D2Q9 neighbours phi(x + c_i dt)
-  const double pc = (double)tile[ty][tx];
-  const double pE = (double)tile[ty][tx + 1], pW = (double)tile[ty][tx - 1];
-  const double pN = (double)tile[ty + 1][tx], pS = (double)tile[ty - 1][tx];
-  const double pNE = (double)tile[ty + 1][tx + 1], pNW = (double)tile[ty + 1][tx - 1];
-  const double pSW = (double)tile[ty - 1][tx - 1], pSE = (double)tile[ty - 1][tx + 1];
+  const R pc = tile[ty][tx];
+  const R pE = tile[ty][tx + 1], pW = tile[ty][tx - 1];
+  const R pN = tile[ty + 1][tx], pS = tile[ty - 1][tx];
+  const R pNE = tile[ty + 1][tx + 1], pNW = tile[ty + 1][tx - 1];
+  const R pSW = tile[ty - 1][tx - 1], pSE = tile[ty - 1][tx + 1];
   // Eq. gradient: sum_i w_i c_i phi_i / (c_s^2 dt) = (3/dx) sum_i w_i e_i phi_i
-  const double g3 = 3.0 / P.dx;
-  m.gx = g3 * ((pE - pW) * (1.0 / 9.0) + ((pNE - pNW) + (pSE - pSW)) * (1.0 / 36.0));
-  m.gy = g3 * ((pN - pS) * (1.0 / 9.0) + ((pNE - pSE) + (pNW - pSW)) * (1.0 / 36.0));
+  const R g3 = (R)P.g3;
+  m.gx = g3 * ((pE - pW) * ((R)1 / (R)9) + ((pNE - pNW) + (pSE - pSW)) * ((R)1 / (R)36));
+  m.gy = g3 * ((pN - pS) * ((R)1 / (R)9) + ((pNE - pSE) + (pNW - pSW)) * ((R)1 / (R)36));
   // Eq. laplacian: sum_i 2 w_i (phi_i - phi) / (c_s^2 dt^2) = (6/dx^2) sum_i w_i (phi_i - phi)
-  const double l6 = 6.0 / (P.dx * P.dx);
-  const double lap = l6 * (((pE + pW) + (pN + pS) - 4.0 * pc) * (1.0 / 9.0) +
-                           ((pNE + pNW) + (pSE + pSW) - 4.0 * pc) * (1.0 / 36.0));
+  const R lap = (R)P.l6 * (((pE + pW) + (pN + pS) - (R)4 * pc) * ((R)1 / (R)9) +
+                           ((pNE + pNW) + (pSE + pSW) - (R)4 * pc) * ((R)1 / (R)36));
   m.phi = pc;
   // Eq. chemical_potential
-  m.mu = 4.0 * P.beta * pc * (pc - 1.0) * (pc - 0.5) - P.kappa * lap;
-  const double gn = sqrt(m.gx * m.gx + m.gy * m.gy);
-  m.nxv = gn != 0.0 ? m.gx / gn : 0.0;  // normal only where |grad phi| != 0
-  m.nyv = gn != 0.0 ? m.gy / gn : 0.0;
-  const double drl = P.rho_l - P.rho_g;
-  m.rho = P.rho_g + pc * drl;
-  double nu;
-  if (P.nu_rule == 0) nu = P.nu_g + pc * (P.nu_l - P.nu_g);
-  else nu = (P.rho_g * P.nu_g + pc * (P.rho_l * P.nu_l - P.rho_g * P.nu_g)) / m.rho;
-  m.tau = nu / P.cs2 + 0.5 * P.dt;
+  m.mu = (R)4 * (R)P.beta * pc * (pc - (R)1) * (pc - (R)0.5) - (R)P.kappa * lap;
+  const R gn = sqrt(m.gx * m.gx + m.gy * m.gy);
+  m.nxv = gn != (R)0 ? m.gx / gn : (R)0;  // normal only where |grad phi| != 0
+  m.nyv = gn != (R)0 ? m.gy / gn : (R)0;
+  const R drl = (R)(P.rho_l - P.rho_g);
+  R nu;
+  if (P.nu_rule == 0) nu = (R)P.nu_g + pc * (R)(P.nu_l - P.nu_g);
+  else nu = ((R)(P.rho_g * P.nu_g) + pc * (R)(P.rho_l * P.nu_l - P.rho_g * P.nu_g)) / ((R)P.rho_g + pc * drl);
+  // tau / dt = nu / (c_s^2 dt) + 1/2 (Eq. eq_kinematic_viscosity)
+  m.wb = (R)1 / (nu * (R)P.inv_cs2dt + (R)0.5);
   m.drx = drl * m.gx;
   m.dry = drl * m.gy;
-  m.Fx = m.mu * m.gx + P.Fx + fext_x;
-  m.Fy = m.mu * m.gy + P.Fy + fext_y;
-  // Eq. u_Liang, then Eq. p_Liang (u first)
-  m.ux = (zsum_x + 0.5 * P.dt * m.Fx) / m.rho;
-  m.uy = (zsum_y + 0.5 * P.dt * m.Fy) / m.rho;
+  m.Fx = m.mu * m.gx + (R)P.Fx + fext_x;
+  m.Fy = m.mu * m.gy + (R)P.Fy + fext_y;
+  // FP64 recovery: rho(phi), Eq. u_Liang, then Eq. p_Liang (u first)
+  const double pcd = (double)pc;
+  m.rho = P.rho_g + pcd * (P.rho_l - P.rho_g);
+  const double inv = 1.0 / m.rho;
+  m.ux = (zsum_x + 0.5 * P.dt * (double)m.Fx) * inv;
+  m.uy = (zsum_y + 0.5 * P.dt * (double)m.Fy) * inv;
   const double usq = m.ux * m.ux + m.uy * m.uy;
-  const double s0 = (4.0 / 9.0) * (-0.5 * usq / P.cs2);  // s_0(u), Eq. s_i_Liang
-  m.p = P.cs2 / (1.0 - 4.0 / 9.0) * (zsum_nz + 0.5 * P.dt * (m.ux * m.drx + m.uy * m.dry) + m.rho * s0);
+  const double s0 = (4.0 / 9.0) * (-0.5 * usq * P.inv_cs2);  // s_0(u), Eq. s_i_Liang
+  m.p = P.cs2 * 1.8 * (zsum_nz + 0.5 * P.dt * (m.ux * (double)m.drx + m.uy * (double)m.dry) + m.rho * s0);
 }
 
 template <typename R>
-__device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro &m, double dpux, double dpuy, R h[5]) {
+__device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro<R> &m, R dpux, R dpuy, R h[5]) {
   const R c = (R)P.c, inv_cs2 = (R)3 / (c * c);
-  const R om = (R)(P.dt / P.tauphi);
-  const R sfac = (R)((1.0 - P.dt / (2.0 * P.tauphi)) * P.dt);
-  const double a_int = P.cs2 * 4.0 * m.phi * (1.0 - m.phi) / P.W;
-  const R ax = (R)(dpux + a_int * m.nxv), ay = (R)(dpuy + a_int * m.nyv);
-  const R phi = (R)m.phi, ux = (R)m.ux, uy = (R)m.uy;
+  const R om = (R)P.om_h;
+  const R sfac = (R)P.sfac_h;
+  const R a_int = (R)P.aint_coef * m.phi * ((R)1 - m.phi);  // c_s^2 4 phi (1 - phi) / W
+  const R ax = dpux + a_int * m.nxv, ay = dpuy + a_int * m.nyv;
+  const R phi = m.phi, ux = (R)m.ux, uy = (R)m.uy;
   R heq_sum = 0;
 #pragma unroll
   for (int q = 1; q < 5; q++) {
@@ -136,16 +143,15 @@ __device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro &m, d
 }
 
 template <typename R>
-__device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro &m, R z[9]) {
-  const double dt = P.dt;
+__device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m, R z[9]) {
   const R c = (R)P.c;
   const R rho = (R)m.rho, ux = (R)m.ux, uy = (R)m.uy;
-  const R Fx = (R)m.Fx, Fy = (R)m.Fy, gx = (R)m.drx, gy = (R)m.dry;
+  const R Fx = m.Fx, Fy = m.Fy, gx = m.drx, gy = m.dry;
   if (!P.z_mrt) {
     // BGK, Eq. eq_lattice_boltzmann_pressure
-    const R inv_cs2 = (R)(1.0 / P.cs2);
-    const R om = (R)(dt / m.tau), sfac = (R)((1.0 - dt / (2.0 * m.tau)) * dt);
-    const R Pp = (R)(m.p / P.cs2);
+    const R inv_cs2 = (R)P.inv_cs2;
+    const R om = m.wb, sfac = ((R)1 - (R)0.5 * m.wb) * (R)P.dt;
+    const R Pp = (R)(m.p * P.inv_cs2);
     const R hu = (R)0.5 * (ux * ux + uy * uy) * inv_cs2;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
@@ -163,7 +169,7 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro &m, R
   // F_hat^z = w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2.
   const R ic = (R)1 / c;
   const R hx = ux * ic, hy = uy * ic, usq = hx * hx + hy * hy;
-  const R Pp = (R)(m.p / P.cs2);
+  const R Pp = (R)(m.p * P.inv_cs2);
   const R s14 = (z[1] + z[2]) + (z[3] + z[4]);
   const R s58 = (z[5] + z[6]) + (z[7] + z[8]);
   const R m0 = z[0] + s14 + s58;
@@ -186,11 +192,11 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro &m, R
   const R Fxx = (R)(2.0 / 3.0) * (ux * gx - uy * gy), Fxy = (R)(1.0 / 3.0) * (ux * gy + uy * gx);
   // multiphase [Lambda]_dim (Sec. 3): 1/dt everywhere except omega_q2 (q_x, and
   // q_y by the isotropic reading) and 1/tau for the stress moments
-  const double wnu = 1.0 / m.tau;
-  const R sq = (R)(dt * (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu));
+  // omega_q2 dt = 3 (2 - omega_nu dt) / (3 - omega_nu dt), omega_nu dt = dt / tau (Sec. 3)
+  const R snu = m.wb;
+  const R sq = (R)3 * ((R)2 - snu) / ((R)3 - snu);
   const R sqy = P.qy_literal ? (R)1 : sq;
-  const R snu = (R)(dt * wnu);
-  const R rdt = (R)dt, one = (R)1, half = (R)0.5;
+  const R rdt = (R)P.dt, one = (R)1, half = (R)0.5;
   const R d0 = m0 - half * rdt * F0;                 // s = 1: (m - 0) - (1 - 1/2) dt F
   const R d_e = (m_e - eq_e);                        // F_e = 0
   const R d_ep = (m_ep - eq_ep) - half * rdt * Fep;
@@ -265,17 +271,17 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
     const long long n = (long long)j * P.pitch + i;
     const S *src = (const S *)P.src;
     R z[9], h[5];
-    double prevx, prevy;
+    R prevx, prevy;
     const double c = P.c;
-    double fex = 0.0, fey = 0.0;
+    R fex = 0, fey = 0;
     if (P.force) {
-      fex = (double)((const S *)P.force)[n];
-      fey = (double)((const S *)P.force)[P.plane + n];
+      fex = (R)((const S *)P.force)[n];
+      fey = (R)((const S *)P.force)[P.plane + n];
     }
     pull_z<S, R>(P, src, i, j, z);
     pull_h<S, R>(P, src, i, j, h);
-    prevx = (double)src[14ll * P.plane + n];
-    prevy = (double)src[15ll * P.plane + n];
+    prevx = (R)src[14ll * P.plane + n];
+    prevy = (R)src[15ll * P.plane + n];
     // FP64 sums for the u and p recovery (Eqs. u_Liang, p_Liang)
     double zd[9];
 #pragma unroll
@@ -283,11 +289,11 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
     const double jx = c * ((zd[1] - zd[3]) + (zd[5] - zd[6]) + (zd[8] - zd[7]));
     const double jy = c * ((zd[2] - zd[4]) + (zd[5] - zd[8]) + (zd[6] - zd[7]));
     const double znz = ((zd[1] + zd[2]) + (zd[3] + zd[4])) + ((zd[5] + zd[6]) + (zd[7] + zd[8]));
-    MpMacro m;
+    MpMacro<R> m;
     mp_macro<R>(P, tile, threadIdx.x + 1, threadIdx.y + 1, jx, jy, znz, fex, fey, m);
     if (MODE == MODE_STEP) {
-      const double pux = m.phi * m.ux, puy = m.phi * m.uy;
-      const double dpux = (pux - prevx) / P.dt, dpuy = (puy - prevy) / P.dt;  // explicit Euler d_t(phi u)
+      const R pux = m.phi * (R)m.ux, puy = m.phi * (R)m.uy;
+      const R dpux = (pux - prevx) * (R)P.inv_dt, dpuy = (puy - prevy) * (R)P.inv_dt;  // explicit Euler d_t(phi u)
       collide_h<R>(P, m, dpux, dpuy, h);
       collide_z<R>(P, m, z);
       S *dst = (S *)P.dst;
@@ -305,12 +311,12 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
       if (mask & 4u) out[(slot++) * N + k] = m.uy;
       if (mask & 8u) out[(slot++) * N + k] = 0.0;
       if (mask & 16u) out[(slot++) * N + k] = m.p;
-      if (mask & 32u) out[(slot++) * N + k] = m.phi;
+      if (mask & 32u) out[(slot++) * N + k] = (double)m.phi;
     } else {
       const double umag = sqrt(m.ux * m.ux + m.uy * m.uy);
       const bool bad = !isfinite(m.rho) || !isfinite(umag) || !isfinite(m.p) || umag >= P.c;
       red[0] = m.rho * P.dx * P.dx;
-      red[1] = m.phi;
+      red[1] = (double)m.phi;
       red[2] = bad ? 0.0 : umag;
       red[3] = bad ? 1.0 : 0.0;
     }

@@ -46,6 +46,7 @@ class lbm_params(C.Structure):
         ("sigma", C.c_double), ("W", C.c_double), ("mobility", C.c_double),
         ("omega_e_dt", C.c_double), ("omega_eps_dt", C.c_double),
         ("body_force", C.c_double * 2), ("u_prescribed", C.c_double * 2),
+        ("gravity", C.c_double * 2), ("beta_exp", C.c_double), ("T_ref", C.c_double), ("rho_ref", C.c_double),
     ]
 
 
@@ -286,6 +287,8 @@ def make_params(d: dict, precision=LBM_FP64) -> lbm_params:
             p.body_force[0], p.body_force[1] = float(v[0]), float(v[1])
         elif k == "u_prescribed":
             p.u_prescribed[0], p.u_prescribed[1] = float(v[0]), float(v[1])
+        elif k == "gravity":
+            p.gravity[0], p.gravity[1] = float(v[0]), float(v[1])
         elif k in _PARAM_NAMES and k not in ("body_force",):
             setattr(p, k, v)
     if d.get("flow", 9) == 0:

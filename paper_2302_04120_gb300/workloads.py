@@ -128,9 +128,10 @@ def bubble(n=512, R_cells=64.0, W_cells=5.0, steps=100000, dx=5e-6, dt=1e-7, mob
 # ---------------------------------------------------------------------------
 # Workload 4: many independent channels of uneven size
 # ---------------------------------------------------------------------------
-def channel_batch(count=256, seed=4, steps=5000, nx_range=(128, 4096), ny_range=(32, 512)):
-    """Independent channels: Nx ~ U{128..4096}, Ny ~ U{32..512}, Re ~ U(10, 200),
-    Pr in {0.7, 7} (numpy PCG64 seed 4, draws in that order per channel).
+def channel_batch_specs(count=256, seed=4, nx_range=(128, 4096), ny_range=(32, 512)):
+    """Per-channel (nx, ny, Re, Pr, dx, dt) of the batched workload: Nx ~ U{128..4096},
+    Ny ~ U{32..512}, Re ~ U(10, 200), Pr in {0.7, 7} (numpy PCG64 seed 4, draws in that
+    order per channel).
 
     dt per channel: the largest dt with a lattice Mach number <= 0.1 based on
     1.5 u_m, clipped so that both relaxation times stay in [0.51, 2.0] dt.
@@ -153,10 +154,20 @@ def channel_batch(count=256, seed=4, steps=5000, nx_range=(128, 4096), ny_range=
         dt_lo = 0.01 * dx * dx / (3.0 * dmin)
         dt_hi = 0.5 * dx * dx / dmax
         dt = max(dt_lo, min(dt_ma, dt_hi))
-        w = channel(nx=nx, ny=ny, steps=steps, Re=Re, Pr=Pr, dx=dx, dt=dt)
-        w["Re"], w["Pr"] = Re, Pr
-        out.append(w)
+        out.append(dict(nx=nx, ny=ny, Re=Re, Pr=Pr, dx=dx, dt=dt))
     return out
+
+
+def channel_from_spec(spec, steps=5000):
+    w = channel(nx=spec["nx"], ny=spec["ny"], steps=steps, Re=spec["Re"], Pr=spec["Pr"], dx=spec["dx"],
+                dt=spec["dt"])
+    w["Re"], w["Pr"] = spec["Re"], spec["Pr"]
+    return w
+
+
+def channel_batch(count=256, seed=4, steps=5000, nx_range=(128, 4096), ny_range=(32, 512)):
+    """The batched workload as full workload dicts (see channel_batch_specs)."""
+    return [channel_from_spec(sp, steps) for sp in channel_batch_specs(count, seed, nx_range, ny_range)]
 
 
 # ---------------------------------------------------------------------------
@@ -193,3 +204,32 @@ def random_state_like(shape, seed, scale=1.0):
     """Seeded perturbation field for parity tests off the equilibrium manifold."""
     rng = np.random.default_rng(seed)
     return scale * rng.standard_normal(shape)
+
+
+# ---------------------------------------------------------------------------
+# Natural convection in a square cavity (two-way coupling through buoyancy)
+# ---------------------------------------------------------------------------
+AIR_333K = dict(rho0=1.059, cp=1008.045, k=0.029, nu=1.90e-5, beta_exp=3.004e-3)
+
+
+def natural_convection(L=0.013, T_h=373.15, T_c=293.85, T_ref=333.5, dx=2e-4, dt=2e-4, steps=40000,
+                       flow_op=0, thermal_op=1, n=None):
+    """Square cavity of side L (air at 333.5 K, App. D): hot left wall T_h, cold right
+    wall T_c, adiabatic top and bottom, no-slip walls, gravity (0, -9.81) m/s^2.
+    L = 13 mm gives Ra ~ 1e4 (App. D).  Start at rest at T_c."""
+    n = int(round(L / dx)) if n is None else n
+    a = AIR_333K
+    params = dict(nx=n, ny=n, flow=9, flow_op=flow_op, thermal=5, thermal_op=thermal_op, phase=0, dx=dx, dt=dt,
+                  rho0=a["rho0"], nu=a["nu"], cp=a["cp"], k=a["k"], T0=T_c, gravity=(0.0, -9.81),
+                  beta_exp=a["beta_exp"], T_ref=T_ref, rho_ref=a["rho0"])
+    bcs = [
+        (0, BC_WALL, None, a["rho0"], TBC_TEMP, np.full(n, T_h)),
+        (1, BC_WALL, None, a["rho0"], TBC_TEMP, np.full(n, T_c)),
+        (2, BC_WALL, None, a["rho0"], TBC_FLUX, np.zeros(n)),
+        (3, BC_WALL, None, a["rho0"], TBC_FLUX, np.zeros(n)),
+    ]
+    init = dict(a=None, ux=np.zeros((n, n)), uy=np.zeros((n, n)), b=np.full((n, n), T_c))
+    alpha = a["k"] / (a["rho0"] * a["cp"])
+    Ra = 9.81 * a["beta_exp"] * (n * dx) ** 3 * (T_h - T_c) / (a["nu"] * alpha)
+    return dict(name=f"cavity_{n}x{n}", params=params, bcs=bcs, init=init, q3=None, steps=steps,
+                alpha=alpha, dT=T_h - T_c, Ra=Ra, L=n * dx)

@@ -505,3 +505,53 @@ def test_two_phase_source_and_equilibria_moments():
     o2.step(200)
     s1 = o2.moments()["phi"].sum()
     assert np.isfinite(s1) and abs(s1 - s0) / s0 < 1e-16 * 200
+
+
+# ---------------------------------------------------------------------------
+# Two-way thermal coupling (Boussinesq buoyancy, App. D)
+# ---------------------------------------------------------------------------
+def cavity_nusselt(m, w):
+    """Mean Nusselt number of the cavity: the heat flux through every interior vertical
+    face (advective u T plus conductive -alpha dT/dx, summed over the rows) over the
+    pure-conduction flux alpha dT; at steady state it is the same through every face."""
+    T, u = m["T"], m["ux"]
+    dx, a = w["params"]["dx"], w["alpha"]
+    Q = (0.5 * (u[:, :-1] * T[:, :-1] + u[:, 1:] * T[:, 1:]) - a * (T[:, 1:] - T[:, :-1]) / dx).sum(0) * dx
+    return Q.mean() / (a * w["dT"]), Q.std() / Q.mean()
+
+
+@pytest.mark.slow
+def test_natural_convection_nusselt_ra1e4():
+    """Square cavity of App. D at Ra ~ 1e4 (L = 13 mm air, dx = dt = 2e-4): steady mean
+    Nusselt number within 1 % of the benchmark 2.243 the paper prints (its dimensional
+    LBM: 2.242), with a uniform heat flux through the cavity (steady state)."""
+    P = _paper()["appD_mean_Nu"]
+    w = wl.natural_convection()
+    o = oracle.Oracle(w["params"])
+    for bc in w["bcs"]:
+        o.set_bc(*bc)
+    o.init(**w["init"])
+    o.step(25000)
+    nu, spread = cavity_nusselt(o.moments(), w)
+    assert abs(nu - P["benchmark"][0]) / P["benchmark"][0] < 0.01
+    assert spread < 1e-4
+
+
+def test_buoyancy_sign_and_scale():
+    """A warm blob in still fluid rises: after a few steps the momentum gained equals
+    -rho_ref beta_exp sum (T - T_ref) g dt per step (Eq. buoyancy_force, first moment)."""
+    w = wl.natural_convection(n=16, steps=0)
+    p = dict(w["params"])
+    o = oracle.Oracle(p)                  # periodic box, no walls
+    x = (np.arange(16) + 0.5) / 16
+    T0 = 333.5 + 5.0 * np.exp(-((x[None, :] - 0.5) ** 2 + (x[:, None] - 0.5) ** 2) / 0.02)
+    o.init(None, None, None, T0)
+    m0 = o.moments()
+    o.step(1)
+    m1 = o.moments()
+    dt = p["dt"]
+    jy0 = (m0["rho"] * m0["uy"]).sum()
+    jy1 = (m1["rho"] * m1["uy"]).sum()
+    F = -p["rho_ref"] * p["beta_exp"] * ((m0["T"] - p["T_ref"]).sum() + (m1["T"] - p["T_ref"]).sum()) / 2 * p["gravity"][1]
+    assert jy1 - jy0 > 0
+    assert abs((jy1 - jy0) / dt - F) / abs(F) < 1e-6

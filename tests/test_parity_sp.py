@@ -240,3 +240,28 @@ def test_autotune_keeps_state_and_results():
     ma, mb = a.moments(), b.moments()
     for k in ma:
         assert np.array_equal(ma[k], mb[k]), k
+
+
+@pytest.mark.parametrize("flow_op,thermal_op", [(0, 1), (1, 1)])
+def test_buoyancy_cavity_parity(flow_op, thermal_op):
+    """Two-way coupling (Boussinesq force of App. D) in the 65 x 65 heated cavity:
+    400 steps FP64 vs the oracle (1e-12), FP32 vs the oracle (1e-5 relative L2)."""
+    w = wl.natural_convection(steps=400, flow_op=flow_op, thermal_op=thermal_op)
+    o = run_oracle(w)
+    s = run_gpu(w, FP64)
+    _compare_fields(o, s, T_in=293.85)
+    _compare_populations(o, s, w)
+    s32 = run_gpu(w, FP32)
+    _compare_fields(o, s32, T_in=293.85, tol=1e-5, prec=FP32)
+
+
+def test_buoyancy_cavity_nusselt_on_gpu():
+    """Steady mean Nusselt number of the Ra ~ 1e4 cavity from the GPU (FP64 and
+    FP32 deviation forms) within 1 % of the benchmark 2.243 printed in App. D."""
+    from test_oracle_pins import cavity_nusselt
+    w = wl.natural_convection(steps=40000)
+    for prec in (FP64, FP32):
+        s = run_gpu(w, prec)
+        nu, spread = cavity_nusselt(s.moments(), w)
+        assert abs(nu - 2.243) / 2.243 < 0.01, (prec, nu)
+        assert spread < 1e-4
