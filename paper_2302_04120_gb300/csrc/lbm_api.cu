@@ -34,8 +34,6 @@ struct lbm_s {
   double *d_uw[4], *d_tw[4];
   // sources (storage precision, pitched)
   void *d_qdot, *d_force;
-  // two-phase work arrays
-  void *d_phi;     // order parameter plane (storage precision)
   // reductions
   double *d_partials;
   int max_blocks;
@@ -165,7 +163,6 @@ static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {
   P.local = h->pre;
   P.src = h->buf[from_buf];
   P.dst = h->buf[1 - from_buf];
-  P.phi = h->d_phi;
   return P;
 }
 
@@ -249,11 +246,6 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
     cudaMemsetAsync(h->d_uw[s], 0, sizeof(double) * 2 * len, h->stream);
     cudaMemsetAsync(h->d_tw[s], 0, sizeof(double) * len, h->stream);
   }
-  if (p.phase) {
-    e = cudaMalloc(&h->d_phi, (size_t)h->plane * h->elem);
-    if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc phi"); }
-    cudaMemsetAsync(h->d_phi, 0, (size_t)h->plane * h->elem, h->stream);
-  }
   h->max_blocks = lbmk::sp_integral_blocks(p.nx, p.ny);
   int mpb = lbmk::mp_integral_blocks(p.nx, p.ny);
   if (mpb > h->max_blocks) h->max_blocks = mpb;
@@ -277,7 +269,6 @@ extern "C" void lbm_destroy(lbm_t h) {
   for (int s = 0; s < 4; s++) { cudaFree(h->d_uw[s]); cudaFree(h->d_tw[s]); }
   cudaFree(h->d_qdot);
   cudaFree(h->d_force);
-  cudaFree(h->d_phi);
   cudaFree(h->d_partials);
   cudaFree(h->d_out4);
   if (h->h_out4) cudaFreeHost(h->h_out4);

@@ -21,7 +21,6 @@ struct MpParams {
   int local;          // 1: src holds the pre-collision state itself (after init)
   const void *src;
   void *dst;
-  void *phi;          // order-parameter plane
 };
 
 cudaError_t mp_step(const MpParams &P, int prec, cudaStream_t s);

@@ -2,23 +2,22 @@
 // pressure-evolution z_i (D2Q9, MRT or BGK) of the model described in Sec. 2.3
 // of Martins, Alvarino & Cabezas-Gomez (arXiv:2302.04120), all in SI units.
 //
-// A step is two launches:
-//   pass 1 (k_mp_phi):     pull h_i from the post-collision buffer and write
-//                          phi = sum h_i (Eq. zero_moment_h);
-//   pass 2 (k_mp_collide): stage a (BX+2) x (BY+2) tile of phi with a one-node
-//                          periodic halo in shared memory, take the isotropic
-//                          gradient and Laplacian (Eqs. gradient, laplacian, D2Q9
-//                          weights), the chemical potential (Eq. chemical_potential),
-//                          the guarded normal, F_s = mu grad phi, grad rho; pull z_i
-//                          and h_i again; recover u (Eq. u_Liang) and p (Eq. p_Liang)
-//                          in FP64; collide h (Eqs. eq_lattice_boltzmann_interface,
-//                          heq_liang, source_term_interface) and z (Eq. colisao_MRT
-//                          with the multiphase [Lambda]_dim of Sec. 3, Eqs. zeq_liang,
-//                          s_i_Liang, forcing_term_pressure_evolution); store h*, z*
-//                          and phi u for the next explicit d_t(phi u).
-// In the FP32 form the populations, phi and (phi u) are stored in FP32 and the
-// collision runs in FP32, while rho(phi), u and p are recovered in FP64: at the
-// ~43000 density ratio of saturated water u = j / rho divides by rho_g = 0.023.
+// A step is ONE launch (k_mp_collide) over 32 x 8 tiles:
+//   * pull h_i for the tile and for a one-node periodic halo ring and stage
+//     phi = sum h_i (Eq. zero_moment_h) in shared memory (the node's own h stay
+//     in registers; halo h re-reads hit L2, so DRAM sees each h once);
+//   * isotropic gradient and Laplacian (Eqs. gradient, laplacian, D2Q9 weights),
+//     chemical potential (Eq. chemical_potential), guarded normal, F_s = mu grad
+//     phi, grad rho; pull z_i; recover u (Eq. u_Liang) and p (Eq. p_Liang);
+//   * collide h (Eqs. eq_lattice_boltzmann_interface, heq_liang,
+//     source_term_interface) and z (Eq. colisao_MRT with the multiphase
+//     [Lambda]_dim of Sec. 3, Eqs. zeq_liang, s_i_Liang,
+//     forcing_term_pressure_evolution); store h*, z* and phi u for the next
+//     explicit d_t(phi u).
+// In the FP32 form the populations and (phi u) are stored in FP32 and the
+// collision runs in FP32, while rho(phi), u and p are recovered in FP64 across the
+// interface and in the gas (phi < 0.999): at the ~43000 density ratio of saturated
+// water u = j / rho divides by rho_g = 0.023.  In the liquid bulk FP32 resolves them.
 #include <cuda_runtime.h>
 
 #include "lattice.cuh"
@@ -52,19 +51,6 @@ __device__ __forceinline__ void pull_z(const MpParams &P, const S *src, int i, i
   }
 }
 
-// pass 1: phi = sum_i h_i (Eq. zero_moment_h)
-template <int PREC>
-__global__ void __launch_bounds__(256) k_mp_phi(const MpParams P) {
-  typedef typename Prec<PREC>::S S;
-  typedef typename Prec<PREC>::R R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= P.nx || j >= P.ny) return;
-  R h[5];
-  pull_h<S, R>(P, (const S *)P.src, i, j, h);
-  ((S *)P.phi)[(long long)j * P.pitch + i] = (S)((h[0] + h[1]) + (h[2] + h[3]) + h[4]);
-}
-
 // Macroscopic state of a node.  The order parameter, its stencils, the chemical
 // potential, the forces and the relaxation rates are in the working precision R;
 // rho, u and p -- the recovery that divides by rho_g ~ 0.023 at the interface --
@@ -76,10 +62,13 @@ struct MpMacro {
 };
 
 // Gradient/Laplacian from the shared tile, then rho, nu, tau, F, u, p.
+// Liquid nodes with phi above this use the working-precision recovery of rho, u, p;
+// all others (the interface, its tanh tails and the gas) recover in FP64.
+constexpr float kPhiFp64Below = 0.999f;
+
 template <typename R>
 __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX + 2], int tx, int ty,
-                                         const double zsum_x, const double zsum_y, const double zsum_nz,
-                                         R fext_x, R fext_y, MpMacro<R> &m) {
+                                         const R z[9], R fext_x, R fext_y, MpMacro<R> &m) {
   // D2Q9 neighbours phi(x + c_i dt)
   const R pc = tile[ty][tx];
   const R pE = tile[ty][tx + 1], pW = tile[ty][tx - 1];
@@ -109,15 +98,39 @@ __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX +
   m.dry = drl * m.gy;
   m.Fx = m.mu * m.gx + (R)P.Fx + fext_x;
   m.Fy = m.mu * m.gy + (R)P.Fy + fext_y;
-  // FP64 recovery: rho(phi), Eq. u_Liang, then Eq. p_Liang (u first)
-  const double pcd = (double)pc;
-  m.rho = P.rho_g + pcd * (P.rho_l - P.rho_g);
-  const double inv = 1.0 / m.rho;
-  m.ux = (zsum_x + 0.5 * P.dt * (double)m.Fx) * inv;
-  m.uy = (zsum_y + 0.5 * P.dt * (double)m.Fy) * inv;
-  const double usq = m.ux * m.ux + m.uy * m.uy;
-  const double s0 = (4.0 / 9.0) * (-0.5 * usq * P.inv_cs2);  // s_0(u), Eq. s_i_Liang
-  m.p = P.cs2 * 1.8 * (zsum_nz + 0.5 * P.dt * (m.ux * (double)m.drx + m.uy * (double)m.dry) + m.rho * s0);
+  // recovery of rho(phi), Eq. u_Liang, then Eq. p_Liang (u first)
+  if (sizeof(R) == 8 || pc < (R)kPhiFp64Below) {
+    // FP64 across the interface and in the gas, where u = j / rho divides by rho_g
+    double zd[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) zd[q] = (double)z[q];
+    const double c = P.c;
+    const double jx = c * ((zd[1] - zd[3]) + (zd[5] - zd[6]) + (zd[8] - zd[7]));
+    const double jy = c * ((zd[2] - zd[4]) + (zd[5] - zd[8]) + (zd[6] - zd[7]));
+    const double znz = ((zd[1] + zd[2]) + (zd[3] + zd[4])) + ((zd[5] + zd[6]) + (zd[7] + zd[8]));
+    m.rho = P.rho_g + (double)pc * (P.rho_l - P.rho_g);
+    const double inv = 1.0 / m.rho;
+    m.ux = (jx + 0.5 * P.dt * (double)m.Fx) * inv;
+    m.uy = (jy + 0.5 * P.dt * (double)m.Fy) * inv;
+    const double usq = m.ux * m.ux + m.uy * m.uy;
+    const double s0 = (4.0 / 9.0) * (-0.5 * usq * P.inv_cs2);  // s_0(u), Eq. s_i_Liang
+    m.p = P.cs2 * 1.8 * (znz + 0.5 * P.dt * (m.ux * (double)m.drx + m.uy * (double)m.dry) + m.rho * s0);
+  } else {
+    // liquid (rho within 0.1 % of rho_l): the working precision resolves u and p
+    const R c = (R)P.c;
+    const R jx = c * ((z[1] - z[3]) + (z[5] - z[6]) + (z[8] - z[7]));
+    const R jy = c * ((z[2] - z[4]) + (z[5] - z[8]) + (z[6] - z[7]));
+    const R znz = ((z[1] + z[2]) + (z[3] + z[4])) + ((z[5] + z[6]) + (z[7] + z[8]));
+    const R rho = (R)P.rho_g + pc * (R)(P.rho_l - P.rho_g);
+    const R inv = (R)1 / rho;
+    const R hdt = (R)(0.5 * P.dt);
+    const R ux = (jx + hdt * m.Fx) * inv, uy = (jy + hdt * m.Fy) * inv;
+    const R s0 = (R)(4.0 / 9.0) * ((R)-0.5 * (ux * ux + uy * uy) * (R)P.inv_cs2);
+    m.rho = (double)rho;
+    m.ux = (double)ux;
+    m.uy = (double)uy;
+    m.p = (double)((R)(P.cs2 * 1.8) * (znz + hdt * (ux * m.drx + uy * m.dry) + rho * s0));
+  }
 }
 
 template <typename R>
@@ -256,41 +269,45 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
   __shared__ R tile[BY + 2][BX + 2];
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
   const int tid = threadIdx.y * BX + threadIdx.x;
-  const S *phi = (const S *)P.phi;
-  // stage phi with a one-node periodic halo
-  for (int t = tid; t < (BX + 2) * (BY + 2); t += BX * BY) {
-    const int ty = t / (BX + 2), tx = t - ty * (BX + 2);
-    const int gi = modi(i0 + tx - 1, P.nx), gj = modi(j0 + ty - 1, P.ny);
-    tile[ty][tx] = (R)phi[(long long)gj * P.pitch + gi];
-  }
-  __syncthreads();
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   const bool live = (i < P.nx) && (j < P.ny);
+  const S *src = (const S *)P.src;
+  // phi = sum_i h_i (Eq. zero_moment_h) of the tile and of a one-node periodic halo,
+  // from pulled h: this node's h stays in registers for its collision
+  R h[5];
+  {
+    const int gi = i < P.nx ? i : modi(i, P.nx), gj = j < P.ny ? j : modi(j, P.ny);
+    pull_h<S, R>(P, src, gi, gj, h);
+    tile[threadIdx.y + 1][threadIdx.x + 1] = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
+  }
+  constexpr int kHalo = 2 * (BX + 2) + 2 * BY;
+  for (int t = tid; t < kHalo; t += BX * BY) {
+    int tx, ty;
+    if (t < BX + 2) { tx = t; ty = 0; }                            // row below the tile
+    else if (t < 2 * (BX + 2)) { tx = t - (BX + 2); ty = BY + 1; }  // row above
+    else if (t < 2 * (BX + 2) + BY) { tx = 0; ty = t - 2 * (BX + 2) + 1; }  // left column
+    else { tx = BX + 1; ty = t - 2 * (BX + 2) - BY + 1; }           // right column
+    const int gi = modi(i0 + tx - 1, P.nx), gj = modi(j0 + ty - 1, P.ny);
+    R hh[5];
+    pull_h<S, R>(P, src, gi, gj, hh);
+    tile[ty][tx] = (hh[0] + hh[1]) + (hh[2] + hh[3]) + hh[4];
+  }
+  __syncthreads();
   double red[4] = {0.0, 0.0, 0.0, 0.0};
   if (live) {
     const long long n = (long long)j * P.pitch + i;
-    const S *src = (const S *)P.src;
-    R z[9], h[5];
+    R z[9];
     R prevx, prevy;
-    const double c = P.c;
     R fex = 0, fey = 0;
     if (P.force) {
       fex = (R)((const S *)P.force)[n];
       fey = (R)((const S *)P.force)[P.plane + n];
     }
     pull_z<S, R>(P, src, i, j, z);
-    pull_h<S, R>(P, src, i, j, h);
     prevx = (R)src[14ll * P.plane + n];
     prevy = (R)src[15ll * P.plane + n];
-    // FP64 sums for the u and p recovery (Eqs. u_Liang, p_Liang)
-    double zd[9];
-#pragma unroll
-    for (int q = 0; q < 9; q++) zd[q] = (double)z[q];
-    const double jx = c * ((zd[1] - zd[3]) + (zd[5] - zd[6]) + (zd[8] - zd[7]));
-    const double jy = c * ((zd[2] - zd[4]) + (zd[5] - zd[8]) + (zd[6] - zd[7]));
-    const double znz = ((zd[1] + zd[2]) + (zd[3] + zd[4])) + ((zd[5] + zd[6]) + (zd[7] + zd[8]));
     MpMacro<R> m;
-    mp_macro<R>(P, tile, threadIdx.x + 1, threadIdx.y + 1, jx, jy, znz, fex, fey, m);
+    mp_macro<R>(P, tile, threadIdx.x + 1, threadIdx.y + 1, z, fex, fey, m);
     if (MODE == MODE_STEP) {
       const R pux = m.phi * (R)m.ux, puy = m.phi * (R)m.uy;
       const R dpux = (pux - prevx) * (R)P.inv_dt, dpuy = (puy - prevy) * (R)P.inv_dt;  // explicit Euler d_t(phi u)
@@ -382,10 +399,8 @@ int mp_integral_blocks(int nx, int ny) {
 cudaError_t mp_step(const MpParams &P, int prec, cudaStream_t s) {
   dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
   if (prec == 0) {
-    k_mp_phi<0><<<g, b, 0, s>>>(P);
     k_mp_collide<0, MODE_STEP><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
   } else {
-    k_mp_phi<1><<<g, b, 0, s>>>(P);
     k_mp_collide<1, MODE_STEP><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
   }
   return cudaGetLastError();
@@ -402,10 +417,8 @@ cudaError_t mp_init(const MpParams &P, int prec, const double *phi0, const doubl
 cudaError_t mp_moments(const MpParams &P, int prec, unsigned mask, double *out, cudaStream_t s) {
   dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
   if (prec == 0) {
-    k_mp_phi<0><<<g, b, 0, s>>>(P);
     k_mp_collide<0, MODE_MOMENTS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
   } else {
-    k_mp_phi<1><<<g, b, 0, s>>>(P);
     k_mp_collide<1, MODE_MOMENTS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
   }
   return cudaGetLastError();
@@ -415,10 +428,8 @@ cudaError_t mp_integrals(const MpParams &P, int prec, double *partials, int max_
   dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
   if ((int)(g.x * g.y) > max_blocks) return cudaErrorInvalidValue;
   if (prec == 0) {
-    k_mp_phi<0><<<g, b, 0, s>>>(P);
     k_mp_collide<0, MODE_INTEGRALS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, partials);
   } else {
-    k_mp_phi<1><<<g, b, 0, s>>>(P);
     k_mp_collide<1, MODE_INTEGRALS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, partials);
   }
   k_mp_final<<<1, 32, 0, s>>>(partials, (int)(g.x * g.y), out4);
