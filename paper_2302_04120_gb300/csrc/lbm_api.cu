@@ -92,6 +92,16 @@ static int axis_periodic(const lbm_t h, int axis, int thermal) {
   return h->bc[a] == LBM_BC_PERIODIC && h->bc[b] == LBM_BC_PERIODIC;
 }
 
+template <typename R>
+static void fill_const(const SpParams &P, lbmk::SpConst<R> &k) {
+  k.c = (R)P.c; k.cs2 = (R)P.cs2; k.dt = (R)P.dt; k.rho0 = (R)P.rho0; k.T0 = (R)P.T0;
+  k.Fx = (R)P.Fx; k.Fy = (R)P.Fy; k.ux_pres = (R)P.ux_pres; k.uy_pres = (R)P.uy_pres;
+  k.omega = (R)P.omega; k.s_e = (R)P.s_e; k.s_eps = (R)P.s_eps; k.s_q = (R)P.s_q; k.s_nu = (R)P.s_nu;
+  k.omegaT = (R)P.omegaT; k.tsrc_fac = (R)P.tsrc_fac; k.flux_coef = (R)P.flux_coef;
+  k.bgx = (R)P.bgx; k.bgy = (R)P.bgy; k.T_ref = (R)P.T_ref;
+  for (int s = 0; s < 4; s++) k.rho_w[s] = (R)P.side[s].rho_w;
+}
+
 static SpParams sp_params(const lbm_t h, int from_buf) {
   SpParams P;
   memset(&P, 0, sizeof(P));
@@ -130,10 +140,22 @@ static SpParams sp_params(const lbm_t h, int from_buf) {
   }
   P.qdot = h->d_qdot;
   P.force = h->d_force;
+  fill_const(P, P.kd);
+  fill_const(P, P.kf);
   P.local = h->pre;
   P.src = h->buf[from_buf];
   P.dst = h->buf[1 - from_buf];
   return P;
+}
+
+template <typename R>
+static void fill_mp_const(const lbmk::MpParams &P, lbmk::MpConst<R> &k) {
+  k.c = (R)P.c; k.dt = (R)P.dt; k.inv_cs2 = (R)P.inv_cs2; k.g3 = (R)P.g3; k.l6 = (R)P.l6;
+  k.beta = (R)P.beta; k.kappa = (R)P.kappa; k.rho_g = (R)P.rho_g; k.drl = (R)(P.rho_l - P.rho_g);
+  k.nu_g = (R)P.nu_g; k.dnu = (R)(P.nu_l - P.nu_g); k.zg = (R)(P.rho_g * P.nu_g);
+  k.dzeta = (R)(P.rho_l * P.nu_l - P.rho_g * P.nu_g); k.inv_cs2dt = (R)P.inv_cs2dt;
+  k.Fx = (R)P.Fx; k.Fy = (R)P.Fy; k.hdt = (R)(0.5 * P.dt); k.pcoef = (R)(P.cs2 * 1.8);
+  k.om_h = (R)P.om_h; k.sfac_h = (R)P.sfac_h; k.aint_coef = (R)P.aint_coef; k.inv_dt = (R)P.inv_dt;
 }
 
 static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {
@@ -163,6 +185,8 @@ static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {
   P.local = h->pre;
   P.src = h->buf[from_buf];
   P.dst = h->buf[1 - from_buf];
+  fill_mp_const(P, P.kd);  // after every field it reads is set
+  fill_mp_const(P, P.kf);
   return P;
 }
 

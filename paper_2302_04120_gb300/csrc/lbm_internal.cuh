@@ -15,6 +15,16 @@ struct DevSide {
   const double *tw;  // len: q'' (FLUX) or T_w (TEMP)
 };
 
+// Constants of a single-phase solve in the working precision R, filled on the host:
+// the FP32 kernels must not convert double parameters per thread (on GB300 each
+// conversion is an instruction of the slow FP64 pipe).
+template <typename R>
+struct SpConst {
+  R c, cs2, dt, rho0, T0, Fx, Fy, ux_pres, uy_pres;
+  R omega, s_e, s_eps, s_q, s_nu, omegaT, tsrc_fac, flux_coef, bgx, bgy, T_ref;
+  R rho_w[4];
+};
+
 // Everything a single-phase kernel needs; passed by value.
 struct SpParams {
   int nx, ny, pitch;
@@ -41,11 +51,20 @@ struct SpParams {
   // optional per-cell fields (storage precision, pitched planes)
   const void *qdot;       // thermal source qdot [K/s], or null
   const void *force;      // 2 planes F_x, F_y [N m^-3], or null
+  SpConst<double> kd;     // the constants above, in FP64 ...
+  SpConst<float> kf;      // ... and in FP32
   // state
   int local;              // 1: src holds pre-collision f(t) itself (right after init)
   const void *src;        // post-collision populations of the previous step
   void *dst;              // post-collision populations written by this step
 };
+
+template <typename R>
+__device__ __forceinline__ const SpConst<R> &K(const SpParams &P);
+template <>
+__device__ __forceinline__ const SpConst<double> &K<double>(const SpParams &P) { return P.kd; }
+template <>
+__device__ __forceinline__ const SpConst<float> &K<float>(const SpParams &P) { return P.kf; }
 
 enum { FLOW_NONE = 0, FLOW_BGK = 1, FLOW_MRT = 2 };
 enum { TH_NONE = 0, TH_BGK = 1, TH_MRT = 2 };

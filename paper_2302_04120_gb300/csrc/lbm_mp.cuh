@@ -4,6 +4,14 @@
 
 namespace lbmk {
 
+// Constants of a two-phase solve in the working precision R (host-filled, so the
+// FP32 kernels convert nothing per thread on GB300's slow FP64 pipe).
+template <typename R>
+struct MpConst {
+  R c, dt, inv_cs2, g3, l6, beta, kappa, rho_g, drl, nu_g, dnu, zg, dzeta, inv_cs2dt;
+  R Fx, Fy, hdt, pcoef, om_h, sfac_h, aint_coef, inv_dt;
+};
+
 // Two-phase solve on a fully periodic grid.  State planes: z_0..8, h_0..4,
 // (phi u)_x, (phi u)_y of the previous step.
 struct MpParams {
@@ -17,11 +25,20 @@ struct MpParams {
   double inv_cs2, g3, l6, inv_cs2dt, om_h, sfac_h, aint_coef, inv_dt;
   int nu_rule, z_mrt, qy_literal;
   double Fx, Fy;
+  MpConst<double> kd;
+  MpConst<float> kf;
   const void *force;  // 2 planes or null
   int local;          // 1: src holds the pre-collision state itself (after init)
   const void *src;
   void *dst;
 };
+
+template <typename R>
+__device__ __forceinline__ const MpConst<R> &KM(const MpParams &P);
+template <>
+__device__ __forceinline__ const MpConst<double> &KM<double>(const MpParams &P) { return P.kd; }
+template <>
+__device__ __forceinline__ const MpConst<float> &KM<float>(const MpParams &P) { return P.kf; }
 
 cudaError_t mp_step(const MpParams &P, int prec, cudaStream_t s);
 // Equilibria of the given fields (pre-collision state of time 0) into P.dst.

@@ -43,11 +43,11 @@ __device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, i
 #pragma unroll
   for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
   R drho = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-  R rho = (R)P.rho0 + drho;
-  R c = (R)P.c;
+  R rho = K<R>(P).rho0 + drho;
+  R c = K<R>(P).c;
   R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
   R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
-  R Fx = (R)P.Fx, Fy = (R)P.Fy;
+  R Fx = K<R>(P).Fx, Fy = K<R>(P).Fy;
   if (P.force) {
     const S *fo = (const S *)P.force;
     Fx += (R)fo[n];
@@ -60,12 +60,12 @@ __device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, i
 #pragma unroll
     for (int q = 0; q < 5; q++) sg += (R)gs[q * P.plane + n];
     const R qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
-    const R dT = ((R)P.T0 - (R)P.T_ref) + sg - (R)0.5 * (R)P.dt * qd;
-    Fx += (R)P.bgx * dT;
-    Fy += (R)P.bgy * dT;
+    const R dT = (K<R>(P).T0 - K<R>(P).T_ref) + sg - (R)0.5 * K<R>(P).dt * qd;
+    Fx += K<R>(P).bgx * dT;
+    Fy += K<R>(P).bgy * dT;
   }
-  ux = (jx - (R)0.5 * (R)P.dt * Fx) / rho;
-  uy = (jy - (R)0.5 * (R)P.dt * Fy) / rho;
+  ux = (jx - (R)0.5 * K<R>(P).dt * Fx) / rho;
+  uy = (jy - (R)0.5 * K<R>(P).dt * Fy) / rho;
 }
 
 // Pull of all momentum populations at node (i, j), with boundary links.
@@ -82,7 +82,7 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
     for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
     return;
   }
-  const R c = (R)P.c, inv_cs2 = (R)1 / (R)P.cs2;
+  const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
   // outlet velocity extrapolation, Eq. anti_BB_vel and the rule below it (reading:
   // pre-collision velocities of time t at the boundary node and its inner neighbour)
   R uwp[4][2];
@@ -113,14 +113,14 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
     const R fo = (R)src[o * P.plane + n];
     const DevSide &sd = P.side[side];
     const int a = along(side, i, j), len = side_len(P, side);
-    const R rw = (R)sd.rho_w;
+    const R rw = K<R>(P).rho_w[side];
     const R cox = c * (R)cx9(o), coy = c * (R)cy9(o);
     if (sd.kind == BC_PRESSURE) {
       // Eq. anti_BB_vel in deviation form: f_q - w rho0 = -(f_o* - w rho0) + 2 w [rho_w(...) - rho0]
       R ux = uwp[side][0], uy = uwp[side][1];
       R cu = cox * ux + coy * uy;
       R uu = ux * ux + uy * uy;
-      f[q] = -fo + (R)2 * w9<R>(o) * (rw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - (R)P.rho0);
+      f[q] = -fo + (R)2 * w9<R>(o) * (rw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - K<R>(P).rho0);
     } else {
       // Eq. BB_vel (walls and velocity inlet): f_q = f_o* - 2 w_o rho_w c_o.u_w / c_s^2
       R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
@@ -144,7 +144,7 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
     for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n];
     return;
   }
-  const R c = (R)P.c, inv_cs2 = (R)1 / (R)P.cs2;
+  const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
 #pragma unroll
   for (int q = 0; q < 5; q++) {
     const int side = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
@@ -168,12 +168,12 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
       R cu = c * ((R)cx5(o) * ux + (R)cy5(o) * uy);
       R uu = ux * ux + uy * uy;
       R Tw = sd.tw ? (R)sd.tw[a] : (R)0;
-      g[q] = -go + (R)2 * w5<R>(o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - (R)P.T0);
+      g[q] = -go + (R)2 * w5<R>(o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - K<R>(P).T0);
     } else {
       // Eq. BB_T with lambda = 1 for the single unknown (FLUX; zero flux = adiabatic)
       const R go = (R)gsrc[o * P.plane + n];
       R qf = sd.tw ? (R)sd.tw[a] : (R)0;
-      g[q] = go + (R)P.flux_coef * qf;
+      g[q] = go + K<R>(P).flux_coef * qf;
     }
   }
 }
@@ -189,8 +189,8 @@ struct Macro {
 
 template <typename S, typename R>
 __device__ __forceinline__ void load_sources(const SpParams &P, long long n, Macro<R> &m) {
-  m.Fx = (R)P.Fx;
-  m.Fy = (R)P.Fy;
+  m.Fx = K<R>(P).Fx;
+  m.Fy = K<R>(P).Fy;
   if (P.force) {
     const S *fo = (const S *)P.force;
     m.Fx += (R)fo[n];
@@ -204,19 +204,19 @@ __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R
   if (TH != TH_NONE) {
     // Eq. zero_moment_g
     m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    m.T = (R)P.T0 + m.sumg + (R)0.5 * (R)P.dt * m.qd;
+    m.T = K<R>(P).T0 + m.sumg + (R)0.5 * K<R>(P).dt * m.qd;
     if (FLOW != FLOW_NONE && P.buoy) {
       // Boussinesq buoyancy with this step's temperature (Eq. buoyancy_force)
-      const R dT = ((R)P.T0 - (R)P.T_ref) + m.sumg + (R)0.5 * (R)P.dt * m.qd;
-      m.Fx += (R)P.bgx * dT;
-      m.Fy += (R)P.bgy * dT;
+      const R dT = (K<R>(P).T0 - K<R>(P).T_ref) + m.sumg + (R)0.5 * K<R>(P).dt * m.qd;
+      m.Fx += K<R>(P).bgx * dT;
+      m.Fy += K<R>(P).bgy * dT;
     }
   }
   if (FLOW != FLOW_NONE) {
     // Eqs. zero_moment_f and first_moment_f
     m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    m.rho = (R)P.rho0 + m.drho;
-    const R c = (R)P.c, hdt = (R)0.5 * (R)P.dt;
+    m.rho = K<R>(P).rho0 + m.drho;
+    const R c = K<R>(P).c, hdt = (R)0.5 * K<R>(P).dt;
     const R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
     const R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
     const R inv = (R)1 / m.rho;
@@ -224,17 +224,17 @@ __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R
     m.uy = (jy + hdt * m.Fy) * inv;
   } else {
     m.drho = 0;
-    m.rho = (R)P.rho0;
-    m.ux = (R)P.ux_pres;
-    m.uy = (R)P.uy_pres;
+    m.rho = K<R>(P).rho0;
+    m.ux = K<R>(P).ux_pres;
+    m.uy = K<R>(P).uy_pres;
   }
 }
 
 template <typename R>
 __device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &m, R f[9]) {
-  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c), inv_cs4 = inv_cs2 * inv_cs2;
-  const R om = (R)P.omega;
-  const R fac = ((R)1 - (R)0.5 * om) * (R)P.dt;  // (1 - dt/(2 tau)) dt
+  const R c = K<R>(P).c, inv_cs2 = (R)3 / (c * c), inv_cs4 = inv_cs2 * inv_cs2;
+  const R om = K<R>(P).omega;
+  const R fac = ((R)1 - (R)0.5 * om) * K<R>(P).dt;  // (1 - dt/(2 tau)) dt
   const R hu = (R)0.5 * (m.ux * m.ux + m.uy * m.uy) * inv_cs2;  // u^2 / (2 c_s^2)
   const R uF = m.ux * m.Fx + m.uy * m.Fy;
   // q >= 1 first; the rest population takes the remainders so that sum f_eq = rho
@@ -259,8 +259,8 @@ __device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &
 
 template <typename R>
 __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &m, R f[9]) {
-  const R c = (R)P.c, ic = (R)1 / c;
-  const R dt = (R)P.dt;
+  const R c = K<R>(P).c, ic = (R)1 / c;
+  const R dt = K<R>(P).dt;
   // lattice-scaled moments of the deviations (rows of Eq. M_matrix)
   const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
   const R s58 = (f[5] + f[6]) + (f[7] + f[8]);
@@ -278,7 +278,7 @@ __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &
   const R eq_ep = m.drho - (R)3 * m.rho * usq;
   const R eq_qx = -m.rho * ux, eq_qy = -m.rho * uy;
   const R eq_xx = m.rho * (ux * ux - uy * uy), eq_xy = m.rho * ux * uy;
-  const R s_e = (R)P.s_e, s_ep = (R)P.s_eps, s_q = (R)P.s_q, s_nu = (R)P.s_nu;
+  const R s_e = K<R>(P).s_e, s_ep = K<R>(P).s_eps, s_q = K<R>(P).s_q, s_nu = K<R>(P).s_nu;
   // Delta m_k = dt Lambda_k (m_k - m_k^eq) - dt (1 - dt Lambda_k / 2) F_k  (Eq. colisao_MRT)
   const R d_e = s_e * (m_e - eq_e) - ((R)1 - (R)0.5 * s_e) * dt * ((R)6 * uF);
   const R d_ep = s_ep * (m_ep - eq_ep) + ((R)1 - (R)0.5 * s_ep) * dt * ((R)6 * uF);
@@ -308,10 +308,10 @@ __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &
 
 template <typename R>
 __device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &m, R g[5]) {
-  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c);
-  const R om = (R)P.omegaT;
-  const R src = (R)P.tsrc_fac * (R)P.dt * m.qd;
-  const R dT = m.T - (R)P.T0;
+  const R c = K<R>(P).c, inv_cs2 = (R)3 / (c * c);
+  const R om = K<R>(P).omegaT;
+  const R src = K<R>(P).tsrc_fac * K<R>(P).dt * m.qd;
+  const R dT = m.T - K<R>(P).T0;
   R geq_sum = 0, s_sum = 0;
 #pragma unroll
   for (int q = 1; q < 5; q++) {
@@ -330,12 +330,12 @@ template <typename R>
 __device__ __forceinline__ void collide_mrt5(const SpParams &P, const Macro<R> &m, R g[5]) {
   // D2Q5 moments (1, c_x, c_y, 5|c|^2 - 4c^2, c_x^2 - c_y^2) scaled by c^-n; rates
   // (0, 1/tau_T, 1/tau_T, 1/dt, 1/dt); source Delta t (I - dt Lambda/2) M (w qdot).
-  const R ic = (R)1 / (R)P.c, dt = (R)P.dt;
-  const R dT = m.T - (R)P.T0;
+  const R ic = (R)1 / K<R>(P).c, dt = K<R>(P).dt;
+  const R dT = m.T - K<R>(P).T0;
   const R m1 = g[1] - g[3], m2 = g[2] - g[4];
   const R m3 = -(R)4 * g[0] + ((g[1] + g[2]) + (g[3] + g[4]));
   const R m4 = (g[1] + g[3]) - (g[2] + g[4]);
-  const R sT = (R)P.omegaT;
+  const R sT = K<R>(P).omegaT;
   const R d0 = -dt * m.qd;
   const R d1 = sT * (m1 - m.T * m.ux * ic);
   const R d2 = sT * (m2 - m.T * m.uy * ic);

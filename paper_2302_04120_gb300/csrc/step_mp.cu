@@ -58,7 +58,7 @@ __device__ __forceinline__ void pull_z(const MpParams &P, const S *src, int i, i
 template <typename R>
 struct MpMacro {
   R phi, mu, gx, gy, nxv, nyv, Fx, Fy, drx, dry, wb;  // wb = dt / tau
-  double rho, ux, uy, p;
+  R rho, ux, uy, p;
 };
 
 // Gradient/Laplacian from the shared tile, then rho, nu, tau, F, u, p.
@@ -76,28 +76,29 @@ __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX +
   const R pNE = tile[ty + 1][tx + 1], pNW = tile[ty + 1][tx - 1];
   const R pSW = tile[ty - 1][tx - 1], pSE = tile[ty - 1][tx + 1];
   // Eq. gradient: sum_i w_i c_i phi_i / (c_s^2 dt) = (3/dx) sum_i w_i e_i phi_i
-  const R g3 = (R)P.g3;
+  const MpConst<R> &K = KM<R>(P);
+  const R g3 = K.g3;
   m.gx = g3 * ((pE - pW) * ((R)1 / (R)9) + ((pNE - pNW) + (pSE - pSW)) * ((R)1 / (R)36));
   m.gy = g3 * ((pN - pS) * ((R)1 / (R)9) + ((pNE - pSE) + (pNW - pSW)) * ((R)1 / (R)36));
   // Eq. laplacian: sum_i 2 w_i (phi_i - phi) / (c_s^2 dt^2) = (6/dx^2) sum_i w_i (phi_i - phi)
-  const R lap = (R)P.l6 * (((pE + pW) + (pN + pS) - (R)4 * pc) * ((R)1 / (R)9) +
+  const R lap = K.l6 * (((pE + pW) + (pN + pS) - (R)4 * pc) * ((R)1 / (R)9) +
                            ((pNE + pNW) + (pSE + pSW) - (R)4 * pc) * ((R)1 / (R)36));
   m.phi = pc;
   // Eq. chemical_potential
-  m.mu = (R)4 * (R)P.beta * pc * (pc - (R)1) * (pc - (R)0.5) - (R)P.kappa * lap;
+  m.mu = (R)4 * K.beta * pc * (pc - (R)1) * (pc - (R)0.5) - K.kappa * lap;
   const R gn = sqrt(m.gx * m.gx + m.gy * m.gy);
   m.nxv = gn != (R)0 ? m.gx / gn : (R)0;  // normal only where |grad phi| != 0
   m.nyv = gn != (R)0 ? m.gy / gn : (R)0;
-  const R drl = (R)(P.rho_l - P.rho_g);
+  const R drl = K.drl;
   R nu;
-  if (P.nu_rule == 0) nu = (R)P.nu_g + pc * (R)(P.nu_l - P.nu_g);
-  else nu = ((R)(P.rho_g * P.nu_g) + pc * (R)(P.rho_l * P.nu_l - P.rho_g * P.nu_g)) / ((R)P.rho_g + pc * drl);
+  if (P.nu_rule == 0) nu = K.nu_g + pc * K.dnu;
+  else nu = (K.zg + pc * K.dzeta) / (K.rho_g + pc * drl);
   // tau / dt = nu / (c_s^2 dt) + 1/2 (Eq. eq_kinematic_viscosity)
-  m.wb = (R)1 / (nu * (R)P.inv_cs2dt + (R)0.5);
+  m.wb = (R)1 / (nu * K.inv_cs2dt + (R)0.5);
   m.drx = drl * m.gx;
   m.dry = drl * m.gy;
-  m.Fx = m.mu * m.gx + (R)P.Fx + fext_x;
-  m.Fy = m.mu * m.gy + (R)P.Fy + fext_y;
+  m.Fx = m.mu * m.gx + K.Fx + fext_x;
+  m.Fy = m.mu * m.gy + K.Fy + fext_y;
   // recovery of rho(phi), Eq. u_Liang, then Eq. p_Liang (u first)
   if (sizeof(R) == 8 || pc < (R)kPhiFp64Below) {
     // FP64 across the interface and in the gas, where u = j / rho divides by rho_g
@@ -108,39 +109,43 @@ __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX +
     const double jx = c * ((zd[1] - zd[3]) + (zd[5] - zd[6]) + (zd[8] - zd[7]));
     const double jy = c * ((zd[2] - zd[4]) + (zd[5] - zd[8]) + (zd[6] - zd[7]));
     const double znz = ((zd[1] + zd[2]) + (zd[3] + zd[4])) + ((zd[5] + zd[6]) + (zd[7] + zd[8]));
-    m.rho = P.rho_g + (double)pc * (P.rho_l - P.rho_g);
-    const double inv = 1.0 / m.rho;
-    m.ux = (jx + 0.5 * P.dt * (double)m.Fx) * inv;
-    m.uy = (jy + 0.5 * P.dt * (double)m.Fy) * inv;
-    const double usq = m.ux * m.ux + m.uy * m.uy;
+    const double rho = P.rho_g + (double)pc * (P.rho_l - P.rho_g);
+    const double inv = 1.0 / rho;
+    const double ux = (jx + 0.5 * P.dt * (double)m.Fx) * inv;
+    const double uy = (jy + 0.5 * P.dt * (double)m.Fy) * inv;
+    const double usq = ux * ux + uy * uy;
     const double s0 = (4.0 / 9.0) * (-0.5 * usq * P.inv_cs2);  // s_0(u), Eq. s_i_Liang
-    m.p = P.cs2 * 1.8 * (znz + 0.5 * P.dt * (m.ux * (double)m.drx + m.uy * (double)m.dry) + m.rho * s0);
+    m.rho = (R)rho;
+    m.ux = (R)ux;
+    m.uy = (R)uy;
+    m.p = (R)(P.cs2 * 1.8 * (znz + 0.5 * P.dt * (ux * (double)m.drx + uy * (double)m.dry) + rho * s0));
   } else {
     // liquid (rho within 0.1 % of rho_l): the working precision resolves u and p
-    const R c = (R)P.c;
+    const R c = K.c;
     const R jx = c * ((z[1] - z[3]) + (z[5] - z[6]) + (z[8] - z[7]));
     const R jy = c * ((z[2] - z[4]) + (z[5] - z[8]) + (z[6] - z[7]));
     const R znz = ((z[1] + z[2]) + (z[3] + z[4])) + ((z[5] + z[6]) + (z[7] + z[8]));
-    const R rho = (R)P.rho_g + pc * (R)(P.rho_l - P.rho_g);
+    const R rho = K.rho_g + pc * K.drl;
     const R inv = (R)1 / rho;
-    const R hdt = (R)(0.5 * P.dt);
+    const R hdt = K.hdt;
     const R ux = (jx + hdt * m.Fx) * inv, uy = (jy + hdt * m.Fy) * inv;
-    const R s0 = (R)(4.0 / 9.0) * ((R)-0.5 * (ux * ux + uy * uy) * (R)P.inv_cs2);
-    m.rho = (double)rho;
-    m.ux = (double)ux;
-    m.uy = (double)uy;
-    m.p = (double)((R)(P.cs2 * 1.8) * (znz + hdt * (ux * m.drx + uy * m.dry) + rho * s0));
+    const R s0 = (R)(4.0 / 9.0) * ((R)-0.5 * (ux * ux + uy * uy) * K.inv_cs2);
+    m.rho = rho;
+    m.ux = ux;
+    m.uy = uy;
+    m.p = K.pcoef * (znz + hdt * (ux * m.drx + uy * m.dry) + rho * s0);
   }
 }
 
 template <typename R>
 __device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro<R> &m, R dpux, R dpuy, R h[5]) {
-  const R c = (R)P.c, inv_cs2 = (R)3 / (c * c);
-  const R om = (R)P.om_h;
-  const R sfac = (R)P.sfac_h;
-  const R a_int = (R)P.aint_coef * m.phi * ((R)1 - m.phi);  // c_s^2 4 phi (1 - phi) / W
+  const MpConst<R> &K = KM<R>(P);
+  const R c = K.c, inv_cs2 = K.inv_cs2;
+  const R om = K.om_h;
+  const R sfac = K.sfac_h;
+  const R a_int = K.aint_coef * m.phi * ((R)1 - m.phi);  // c_s^2 4 phi (1 - phi) / W
   const R ax = dpux + a_int * m.nxv, ay = dpuy + a_int * m.nyv;
-  const R phi = m.phi, ux = (R)m.ux, uy = (R)m.uy;
+  const R phi = m.phi, ux = m.ux, uy = m.uy;
   R heq_sum = 0;
 #pragma unroll
   for (int q = 1; q < 5; q++) {
@@ -157,14 +162,15 @@ __device__ __forceinline__ void collide_h(const MpParams &P, const MpMacro<R> &m
 
 template <typename R>
 __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m, R z[9]) {
-  const R c = (R)P.c;
-  const R rho = (R)m.rho, ux = (R)m.ux, uy = (R)m.uy;
+  const MpConst<R> &K = KM<R>(P);
+  const R c = K.c;
+  const R rho = m.rho, ux = m.ux, uy = m.uy;
   const R Fx = m.Fx, Fy = m.Fy, gx = m.drx, gy = m.dry;
   if (!P.z_mrt) {
     // BGK, Eq. eq_lattice_boltzmann_pressure
-    const R inv_cs2 = (R)P.inv_cs2;
-    const R om = m.wb, sfac = ((R)1 - (R)0.5 * m.wb) * (R)P.dt;
-    const R Pp = (R)(m.p * P.inv_cs2);
+    const R inv_cs2 = K.inv_cs2;
+    const R om = m.wb, sfac = ((R)1 - (R)0.5 * m.wb) * K.dt;
+    const R Pp = m.p * K.inv_cs2;
     const R hu = (R)0.5 * (ux * ux + uy * uy) * inv_cs2;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
@@ -182,7 +188,7 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m
   // F_hat^z = w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2.
   const R ic = (R)1 / c;
   const R hx = ux * ic, hy = uy * ic, usq = hx * hx + hy * hy;
-  const R Pp = (R)(m.p * P.inv_cs2);
+  const R Pp = m.p * K.inv_cs2;
   const R s14 = (z[1] + z[2]) + (z[3] + z[4]);
   const R s58 = (z[5] + z[6]) + (z[7] + z[8]);
   const R m0 = z[0] + s14 + s58;
@@ -209,7 +215,7 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m
   const R snu = m.wb;
   const R sq = (R)3 * ((R)2 - snu) / ((R)3 - snu);
   const R sqy = P.qy_literal ? (R)1 : sq;
-  const R rdt = (R)P.dt, one = (R)1, half = (R)0.5;
+  const R rdt = K.dt, one = (R)1, half = (R)0.5;
   const R d0 = m0 - half * rdt * F0;                 // s = 1: (m - 0) - (1 - 1/2) dt F
   const R d_e = (m_e - eq_e);                        // F_e = 0
   const R d_ep = (m_ep - eq_ep) - half * rdt * Fep;
@@ -309,8 +315,8 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
     MpMacro<R> m;
     mp_macro<R>(P, tile, threadIdx.x + 1, threadIdx.y + 1, z, fex, fey, m);
     if (MODE == MODE_STEP) {
-      const R pux = m.phi * (R)m.ux, puy = m.phi * (R)m.uy;
-      const R dpux = (pux - prevx) * (R)P.inv_dt, dpuy = (puy - prevy) * (R)P.inv_dt;  // explicit Euler d_t(phi u)
+      const R pux = m.phi * m.ux, puy = m.phi * m.uy;
+      const R dpux = (pux - prevx) * KM<R>(P).inv_dt, dpuy = (puy - prevy) * KM<R>(P).inv_dt;  // explicit Euler d_t(phi u)
       collide_h<R>(P, m, dpux, dpuy, h);
       collide_z<R>(P, m, z);
       S *dst = (S *)P.dst;
@@ -323,16 +329,17 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
     } else if (MODE == MODE_MOMENTS) {
       const long long N = (long long)P.nx * P.ny, k = (long long)j * P.nx + i;
       int slot = 0;
-      if (mask & 1u) out[(slot++) * N + k] = m.rho;
-      if (mask & 2u) out[(slot++) * N + k] = m.ux;
-      if (mask & 4u) out[(slot++) * N + k] = m.uy;
+      if (mask & 1u) out[(slot++) * N + k] = (double)m.rho;
+      if (mask & 2u) out[(slot++) * N + k] = (double)m.ux;
+      if (mask & 4u) out[(slot++) * N + k] = (double)m.uy;
       if (mask & 8u) out[(slot++) * N + k] = 0.0;
-      if (mask & 16u) out[(slot++) * N + k] = m.p;
+      if (mask & 16u) out[(slot++) * N + k] = (double)m.p;
       if (mask & 32u) out[(slot++) * N + k] = (double)m.phi;
     } else {
-      const double umag = sqrt(m.ux * m.ux + m.uy * m.uy);
-      const bool bad = !isfinite(m.rho) || !isfinite(umag) || !isfinite(m.p) || umag >= P.c;
-      red[0] = m.rho * P.dx * P.dx;
+      const double ux = (double)m.ux, uy = (double)m.uy, rho = (double)m.rho, p = (double)m.p;
+      const double umag = sqrt(ux * ux + uy * uy);
+      const bool bad = !isfinite(rho) || !isfinite(umag) || !isfinite(p) || umag >= P.c;
+      red[0] = rho * P.dx * P.dx;
       red[1] = (double)m.phi;
       red[2] = bad ? 0.0 : umag;
       red[3] = bad ? 1.0 : 0.0;
