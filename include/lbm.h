@@ -146,7 +146,9 @@ lbm_status lbm_create(const lbm_params *p, void *stream, lbm_t *out);
  *  tkind thermal rule (LBM_TBC_*); tw host array of len doubles: q'' [W m^-2, positive
  *        into the fluid] for FLUX, T_w [K] for TEMP, ignored otherwise; NULL = zero.
  * Both sides of an axis must be periodic together, for each lattice.  A link that
- * leaves through a corner takes the y-side rule.
+ * leaves through a corner takes the y-side rule.  The arrays are copied before the
+ * call returns (through pinned staging, without synchronising the stream); the new
+ * values apply to steps enqueued after the call.
  * Errors: LBM_ERR_ARG (side, kind, pairing), LBM_ERR_CUDA.
  */
 lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, double rho_w, int tkind,

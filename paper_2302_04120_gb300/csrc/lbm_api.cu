@@ -32,6 +32,8 @@ struct lbm_s {
   int bc[4], tbc[4];
   double rho_w[4];
   double *d_uw[4], *d_tw[4];
+  double *h_stage[4];        // pinned staging of the boundary arrays, one slot per side
+  cudaEvent_t stage_done[4];  // the slot's last upload has been consumed
   // sources (storage precision, pitched)
   void *d_qdot, *d_force;
   // reductions
@@ -266,6 +268,8 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
     int len = s < 2 ? p.ny : p.nx;
     e = cudaMalloc(&h->d_uw[s], sizeof(double) * 2 * len);
     if (e == cudaSuccess) e = cudaMalloc(&h->d_tw[s], sizeof(double) * len);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage[s], sizeof(double) * 3 * len);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done[s], cudaEventDisableTiming);
     if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc boundary arrays"); }
     cudaMemsetAsync(h->d_uw[s], 0, sizeof(double) * 2 * len, h->stream);
     cudaMemsetAsync(h->d_tw[s], 0, sizeof(double) * len, h->stream);
@@ -290,7 +294,12 @@ extern "C" void lbm_destroy(lbm_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   for (int b = 0; b < 2; b++) cudaFree(h->buf[b]);
-  for (int s = 0; s < 4; s++) { cudaFree(h->d_uw[s]); cudaFree(h->d_tw[s]); }
+  for (int s = 0; s < 4; s++) {
+    cudaFree(h->d_uw[s]);
+    cudaFree(h->d_tw[s]);
+    if (h->h_stage[s]) cudaFreeHost(h->h_stage[s]);
+    if (h->stage_done[s]) cudaEventDestroy(h->stage_done[s]);
+  }
   cudaFree(h->d_qdot);
   cudaFree(h->d_force);
   cudaFree(h->d_partials);
@@ -321,12 +330,24 @@ extern "C" lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, 
   h->bc[side] = kind;
   h->tbc[side] = tkind;
   h->rho_w[side] = rho_w > 0 ? rho_w : h->p.rho0;
-  if (uw) CU(h, cudaMemcpyAsync(h->d_uw[side], uw, sizeof(double) * 2 * len, cudaMemcpyHostToDevice, h->stream));
-  else CU(h, cudaMemsetAsync(h->d_uw[side], 0, sizeof(double) * 2 * len, h->stream));
-  if (tw) CU(h, cudaMemcpyAsync(h->d_tw[side], tw, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
-  else CU(h, cudaMemsetAsync(h->d_tw[side], 0, sizeof(double) * len, h->stream));
-  // host arrays may be reused by the caller after return
-  CU(h, cudaStreamSynchronize(h->stream));
+  // Copy through this side's pinned staging slot so the call returns without a stream
+  // synchronisation (the caller may reuse its arrays at once); wait only until the
+  // slot's previous upload has been consumed.
+  CU(h, cudaEventSynchronize(h->stage_done[side]));
+  double *st = h->h_stage[side];
+  if (uw) {
+    memcpy(st, uw, sizeof(double) * 2 * len);
+    CU(h, cudaMemcpyAsync(h->d_uw[side], st, sizeof(double) * 2 * len, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CU(h, cudaMemsetAsync(h->d_uw[side], 0, sizeof(double) * 2 * len, h->stream));
+  }
+  if (tw) {
+    memcpy(st + 2 * len, tw, sizeof(double) * len);
+    CU(h, cudaMemcpyAsync(h->d_tw[side], st + 2 * len, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CU(h, cudaMemsetAsync(h->d_tw[side], 0, sizeof(double) * len, h->stream));
+  }
+  CU(h, cudaEventRecord(h->stage_done[side], h->stream));
   return LBM_OK;
 }
 

@@ -152,28 +152,28 @@ __global__ void __launch_bounds__(256) k_moments(const SpParams P, unsigned mask
   if (mask & 32u) out[(slot++) * N + k] = 0.0;
 }
 
-// Deterministic integrals: per-block FP64 partials in a fixed shuffle-tree order.
-__device__ __forceinline__ void block_reduce4(double v[4], double *out) {
-  // v[0], v[1], v[3] summed; v[2] max
+// Deterministic integrals.  Per node: the density deviation rho - rho0 and |u|^2 in
+// FP64 from the working-precision moments (no square root per node), and a health
+// flag; warp sums in a fixed shuffle tree; per-block FP64 partials (sum of
+// rho - rho0, 0, max |u|^2, bad-node count); a one-block final pass in a fixed order
+// adds N rho0 and takes the one square root.
+__device__ __forceinline__ void block_partials(double drho, double u2, int bad, double *out) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
-    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
-    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
-    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+    drho += __shfl_down_sync(0xffffffffu, drho, o);
+    u2 = fmax(u2, __shfl_down_sync(0xffffffffu, u2, o));
   }
-  __shared__ double sh[8][4];
+  const int nbad = __popc(__ballot_sync(0xffffffffu, bad));
+  __shared__ double sh[8][3];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-  if (lane == 0) {
-    sh[warp][0] = v[0]; sh[warp][1] = v[1]; sh[warp][2] = v[2]; sh[warp][3] = v[3];
-  }
+  if (lane == 0) { sh[warp][0] = drho; sh[warp][1] = u2; sh[warp][2] = (double)nbad; }
   __syncthreads();
   if (tid == 0) {
-    double a = 0, b = 0, mx = 0, cnt = 0;
-    for (int w = 0; w < nw; w++) { a += sh[w][0]; b += sh[w][1]; mx = fmax(mx, sh[w][2]); cnt += sh[w][3]; }
-    out[0] = a; out[1] = b; out[2] = mx; out[3] = cnt;
+    double a = 0, mx = 0, cnt = 0;
+    for (int w = 0; w < nw; w++) { a += sh[w][0]; mx = fmax(mx, sh[w][1]); cnt += sh[w][2]; }
+    out[0] = a; out[1] = 0.0; out[2] = mx; out[3] = cnt;
   }
 }
 
@@ -183,7 +183,8 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
   typedef typename Prec<PREC>::R R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  double drho = 0.0, u2 = 0.0;
+  int bad = 0;
   if (i < P.nx && j < P.ny) {
     const long long n = (long long)j * P.pitch + i;
     const S *src = (const S *)P.src;
@@ -194,37 +195,46 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
     Macro<R> m;
     load_sources<S, R>(P, n, m);
     moments<R, FLOW, TH>(P, f, g, m);
-    const double rho = P.rho0 + (double)m.drho;
     const double ux = (double)m.ux, uy = (double)m.uy;
-    const double umag = sqrt(ux * ux + uy * uy);
-    const double T = (TH != TH_NONE) ? (double)m.T : 0.0;
-    v[0] = rho * P.dx * P.dx;
-    v[2] = umag;
-    const bool bad = !isfinite(rho) || !isfinite(umag) || !isfinite(T) || umag >= P.c;
-    v[3] = bad ? 1.0 : 0.0;
-    if (bad) v[2] = 0.0;
+    drho = (double)m.drho;
+    u2 = ux * ux + uy * uy;
+    const R Tchk = (TH != TH_NONE) ? m.T : (R)0;
+    bad = !isfinite(drho) || !isfinite(u2) || !isfinite(Tchk) || u2 >= P.c * P.c;
+    if (bad) { drho = 0.0; u2 = 0.0; }
   }
-  block_reduce4(v, partials + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
+  block_partials(drho, u2, bad, partials + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 
-__global__ void k_final_reduce(const double *partials, int nb, double *out4) {
-  // one warp; lane l sums blocks l, l+32, ... then a fixed shuffle tree
-  const int lane = threadIdx.x;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int b = lane; b < nb; b += 32) {
-    v[0] += partials[4 * b + 0];
-    v[1] += partials[4 * b + 1];
-    v[2] = fmax(v[2], partials[4 * b + 2]);
-    v[3] += partials[4 * b + 3];
+// One block of 256 threads: thread t sums partials t, t + 256, ... in order, then a
+// fixed tree.  mass = (N rho0 + sum (rho - rho0)) dx^2, max |u| = sqrt(max |u|^2).
+__global__ void __launch_bounds__(256) k_final_reduce(const double *partials, int nb, double n_rho0, double area,
+                                                      double *out4) {
+  const int t = threadIdx.x;
+  double a = 0, b = 0, mx = 0, cnt = 0;
+  for (int k = t; k < nb; k += 256) {
+    a += partials[4 * k + 0];
+    b += partials[4 * k + 1];
+    mx = fmax(mx, partials[4 * k + 2]);
+    cnt += partials[4 * k + 3];
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
-    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
-    v[2] = fmax(v[2], __shfl_down_sync(0xffffffffu, v[2], o));
-    v[3] += __shfl_down_sync(0xffffffffu, v[3], o);
+  __shared__ double sh[4][256];
+  sh[0][t] = a; sh[1][t] = b; sh[2][t] = mx; sh[3][t] = cnt;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) {
+      sh[0][t] += sh[0][t + w];
+      sh[1][t] += sh[1][t + w];
+      sh[2][t] = fmax(sh[2][t], sh[2][t + w]);
+      sh[3][t] += sh[3][t + w];
+    }
+    __syncthreads();
   }
-  if (lane == 0) { out4[0] = v[0]; out4[1] = v[1]; out4[2] = v[2]; out4[3] = v[3]; }
+  if (t == 0) {
+    out4[0] = (n_rho0 + sh[0][0]) * area;
+    out4[1] = sh[1][0];
+    out4[2] = sqrt(sh[2][0]);
+    out4[3] = sh[3][0];
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -334,7 +344,8 @@ cudaError_t sp_integrals(const SpParams &P, int prec, int flow, int th, double *
 #define CALL_INT(A, B, C) k_integrals<A, B, C><<<grid, kRedBlock, 0, s>>>(P, partials)
   LBM_SP_DISPATCH(prec, flow, th, CALL_INT);
 #undef CALL_INT
-  k_final_reduce<<<1, 32, 0, s>>>(partials, (int)(grid.x * grid.y), out4);
+  k_final_reduce<<<1, 256, 0, s>>>(partials, (int)(grid.x * grid.y), (double)P.nx * P.ny * P.rho0, P.dx * P.dx,
+                                   out4);
   return cudaGetLastError();
 }
 
