@@ -105,7 +105,8 @@ def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY):
     s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
     s.apply_workload(w)
     s.step(1)
-    block = s.autotune()                     # the library's block-shape autotuner
+    s.autotune()                             # the library's launch autotuner (grid or TMA-staged)
+    launch = s.launch_config()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     flush.fill_(1.0)
     sink = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -124,7 +125,7 @@ def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY):
     chk = s.check()
     s.close()
     del flush
-    return times_ms, chk, block
+    return times_ms, chk, launch
 
 
 def _e2e(prec, steps, warmup, stream, torch):
@@ -139,6 +140,8 @@ def _e2e(prec, steps, warmup, stream, torch):
     s.apply_workload(w)
     qf = torch.empty(CELLS_NX, dtype=torch.float64, pin_memory=True).numpy()
     qf[:] = w["qflux"]
+    s.step(1)
+    s.autotune()
     for k in range(warmup):
         lbm.lbm_set_bc(s.h, 2, lbm.LBM_BC_WALL, None, 1000.0, lbm.LBM_TBC_FLUX, qf)
         s.step(1)
@@ -297,7 +300,23 @@ def _cpu_baseline(budget_s=12.0):
                 sample=f"channel 256x{CELLS_NY} slice of the 2048x{CELLS_NY} workload, {n} steps, FP64, OpenMP")
 
 
-def _traffic_from_profile(kernel_tag, block=None):
+def _kernel_tag(launch):
+    return "k_step_tma" if launch[0] == 1 else "k_step"
+
+
+def _kernel_name(launch):
+    if launch[0] == 1:
+        return f"k_step_tma<1,FLOW_MRT,TH_MRT,{launch[1]}>"
+    return "k_step<1,FLOW_MRT,TH_MRT>"
+
+
+def _launch_desc(launch):
+    if launch[0] == 1:
+        return {"kind": "tma", "tile": [32, launch[1]], "stages": launch[2], "ctas_per_sm": launch[3]}
+    return {"kind": "grid", "block": [launch[1], launch[2]]}
+
+
+def _traffic_from_profile(kernel_tag):
     """Per-launch DRAM bytes recorded from an ncu capture, if the kernel source is
     unchanged since (profiles/dram_traffic.txt: tag bytes source_hash block)."""
     import hashlib
@@ -305,7 +324,7 @@ def _traffic_from_profile(kernel_tag, block=None):
     if not os.path.exists(path):
         return None
     h = hashlib.sha1()
-    for f in ("step_sp.cu", "sp_device.cuh", "lattice.cuh", "lbm_internal.cuh"):
+    for f in ("step_sp.cu", "step_tma.cu", "sp_device.cuh", "lattice.cuh", "lbm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2302_04120_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     cur = h.hexdigest()[:12]
@@ -378,18 +397,19 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(ach32 / peak, 4), "peak_source": peak_kind,
-                     "traffic": _traffic_from_profile("k_step_fp32_mrt_mrt_2048x256", blk32),
-                     "kernel": "k_step<1,FLOW_MRT,TH_MRT>", "algorithmic_bytes_per_launch": BYTES_PER_CELL[1] * cells,
-                     "block": list(blk32)},
+                     "traffic": _traffic_from_profile(_kernel_tag(blk32) + "_fp32_mrt_mrt_2048x256"),
+                     "kernel": _kernel_name(blk32), "algorithmic_bytes_per_launch": BYTES_PER_CELL[1] * cells,
+                     "launch": _launch_desc(blk32)},
         "roofline_scaled": {"workload": "channel_d2q9mrt_d2q5mrt_8192x4096", "bound": "hbm",
                             "value": round(8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e6, 1), "unit_value": "MLUPS",
                             "achieved": round(BYTES_PER_CELL[1] * 8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e9, 1),
                             "peak": peak, "unit": "GB/s",
                             "frac": round(BYTES_PER_CELL[1] * 8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e9 / peak, 4),
-                            "steps": len(tsc), "status": int(chksc), "block": list(blksc)},
+                            "steps": len(tsc), "status": int(chksc), "kernel": _kernel_name(blksc),
+                            "launch": _launch_desc(blksc)},
         "fp64": {"value": round(cells / avg64 / 1e6, 1), "unit": "MLUPS", "steps": len(t64),
                  "achieved_GBps": round(ach64, 1), "frac": round(ach64 / peak, 4), "dtype": "f64",
-                 "status": int(chk64)},
+                 "status": int(chk64), "launch": _launch_desc(blk64)},
         "mixed_over_fp64": round(avg64 / avg32, 2),
         "batch": batch,
         "adjoint": adjoint,

@@ -184,13 +184,35 @@ lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux, const dou
 lbm_status lbm_step(lbm_t h, long n);
 
 /*
- * Pick the thread-block shape of the single-solve step kernel by timing candidate
- * shapes (32..256 threads) on the next step, without advancing the solution (the timed
- * launches repeat that step into the same destination).  out_block (may be NULL)
- * receives {block_x, block_y}.  Single-phase solves only; the default is 64 x 4.
+ * Pick the launch of the single-solve step kernel by timing candidates (grid launches
+ * of 32..256 threads and TMA-staged persistent launches, see lbm_set_launch) on the
+ * next step, without advancing the solution (the timed launches repeat that step into
+ * the same destination).  out_block (may be NULL) receives the chosen thread-block
+ * shape {block_x, block_y}.  Single-phase solves only; the default is a 64 x 4 grid
+ * launch.
  * Errors: LBM_ERR_STATE (not initialised), LBM_ERR_ARG, LBM_ERR_CUDA.
  */
 lbm_status lbm_autotune(lbm_t h, int out_block[2]);
+
+/*
+ * Launch configuration of the single-phase step (no counterpart in the paper: a
+ * choice of memory pipeline for the same arithmetic).  cfg[4]:
+ *  {LBM_LAUNCH_GRID, block_x, block_y, 0}: one thread per node, block_x a multiple
+ *     of 32, block_x * block_y <= 256 (the default, 64 x 4);
+ *  {LBM_LAUNCH_TMA, tile_height (4 or 8), stages (1..4), CTAs per SM}: persistent
+ *     CTAs of 32 x tile_height threads; per tile, the pulled values of every
+ *     population plane arrive as tensor-memory-accelerator boxes in shared memory,
+ *     `stages` tiles ahead (the first step after lbm_init_fields always uses the
+ *     grid launch).  A wait for a box that runs out (about 1 s) marks the handle;
+ *     the next lbm_integrals / lbm_check then fails with LBM_ERR_TIMEOUT.
+ * lbm_autotune chooses among both kinds; lbm_launch_config reads the current one.
+ * Errors: LBM_ERR_ARG (two-phase handle, out-of-range value, more CTAs per SM than
+ * fit), LBM_ERR_CUDA (the driver refused the tensor maps).
+ */
+#define LBM_LAUNCH_GRID 0
+#define LBM_LAUNCH_TMA 1
+lbm_status lbm_set_launch(lbm_t h, const int cfg[4]);
+lbm_status lbm_launch_config(lbm_t h, int cfg[4]);
 
 /* Steps taken since lbm_init_fields (time = steps * dt). */
 long lbm_steps_done(lbm_t h);

@@ -39,9 +39,16 @@ struct lbm_s {
   // reductions
   double *d_partials;
   int max_blocks;
-  double *d_out4;
-  double *h_out4;  // pinned
+  double *d_out4;  // 4 integrals, then the step kernels' error flag (an int in slot 4)
+  double *h_out4;  // pinned, 5 doubles
   dim3 block;
+  // single-phase step launch: LBM_LAUNCH_GRID (one node per thread, `block`) or
+  // LBM_LAUNCH_TMA (persistent CTAs of 32 x tma_ty threads, boxes staged by TMA)
+  int launch_kind;
+  int tma_ty, tma_stages, tma_ctas;  // tma_ctas: CTAs per SM
+  int nsm;
+  CUtensorMap tmap[2];  // one per state buffer, boxes 36 x tmap_ty
+  int tmap_ty;          // 0 until encoded
   char err[512];
 };
 
@@ -278,9 +285,26 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   int mpb = lbmk::mp_integral_blocks(p.nx, p.ny);
   if (mpb > h->max_blocks) h->max_blocks = mpb;
   e = cudaMalloc(&h->d_partials, sizeof(double) * 4 * h->max_blocks);
-  if (e == cudaSuccess) e = cudaMalloc(&h->d_out4, sizeof(double) * 4);
-  if (e == cudaSuccess) e = cudaMallocHost(&h->h_out4, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_out4, sizeof(double) * 6);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_out4, 0, sizeof(double) * 6, h->stream);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_out4, sizeof(double) * 6);
   if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc reduction scratch"); }
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) h->nsm = 1;
+  }
+  h->launch_kind = LBM_LAUNCH_GRID;
+  h->tma_ty = 8;
+  h->tma_stages = 3;
+  h->tma_ctas = 2;
+  h->tmap_ty = 0;
+  if (!p.phase && (p.flow || p.thermal)) {
+    int fk = p.flow ? (p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
+    int tk = p.thermal ? (p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
+    lbmk::sp_tma_prepare(p.precision, fk, tk);  // failure leaves only the grid launch usable
+    cudaGetLastError();
+  }
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_CUDA, "create: %s", cudaGetErrorString(e)); }
   *out = h;
@@ -454,6 +478,8 @@ static void sp_kinds(const lbm_t h, int *flow, int *th) {
   *th = h->p.thermal ? (h->p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
 }
 
+static int *step_flag(lbm_t h) { return (int *)(h->d_out4 + 4); }
+
 extern "C" lbm_status lbm_step(lbm_t h, long n) {
   if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
   if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
@@ -465,6 +491,10 @@ extern "C" lbm_status lbm_step(lbm_t h, long n) {
     if (two_phase(h)) {
       lbmk::MpParams P = mp_params(h, h->cur);
       e = lbmk::mp_step(P, h->p.precision, h->stream);
+    } else if (h->launch_kind == LBM_LAUNCH_TMA && !h->pre) {
+      SpParams P = sp_params(h, h->cur);
+      e = lbmk::sp_step_tma(P, h->tmap[h->cur], h->p.precision, flow, th, h->tma_ty, h->tma_stages,
+                            h->nsm * h->tma_ctas, step_flag(h), h->stream);
     } else {
       SpParams P = sp_params(h, h->cur);
       e = lbmk::sp_step(P, h->p.precision, flow, th, h->block, h->stream);
@@ -526,9 +556,12 @@ extern "C" lbm_status lbm_integrals(lbm_t h, double out[4]) {
     e = lbmk::sp_integrals(P, h->p.precision, flow, th, h->d_partials, h->max_blocks, h->d_out4, h->stream);
   }
   if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "integrals launch: %s", cudaGetErrorString(e));
-  CU(h, cudaMemcpyAsync(h->h_out4, h->d_out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(h->h_out4, h->d_out4, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   memcpy(out, h->h_out4, 4 * sizeof(double));
+  int flag;
+  memcpy(&flag, h->h_out4 + 4, sizeof(int));
+  if (flag) return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged copies (flag %d)", flag);
   return LBM_OK;
 }
 
@@ -1013,38 +1046,136 @@ done:
 // ---------------------------------------------------------------------------
 // Launch-shape autotuning of the single-solve step kernel
 // ---------------------------------------------------------------------------
+// Encode the tensor maps of both state buffers for boxes of height ty.
+static lbm_status ensure_tmaps(lbm_t h, int ty) {
+  if (h->tmap_ty == ty) return LBM_OK;
+  for (int b = 0; b < 2; b++) {
+    int r = lbmk::sp_tma_encode(h->buf[b], h->pitch, h->p.ny, h->nq, (int)h->elem, ty, &h->tmap[b]);
+    if (r != 0) {
+      h->tmap_ty = 0;
+      return fail(h, LBM_ERR_CUDA, "tensor map encoding failed (%d)", r);
+    }
+  }
+  h->tmap_ty = ty;
+  return LBM_OK;
+}
+
+static lbm_status check_launch(lbm_t h, const int cfg[4]) {
+  if (two_phase(h)) return fail(h, LBM_ERR_ARG, "two-phase solves use a fixed 32 x 8 tile");
+  if (cfg[0] == LBM_LAUNCH_GRID) {
+    if (cfg[1] < 32 || cfg[1] % 32 != 0 || cfg[2] < 1 || cfg[1] * cfg[2] > 256)
+      return fail(h, LBM_ERR_ARG, "grid launch: block_x a multiple of 32, block_x * block_y <= 256");
+    return LBM_OK;
+  }
+  if (cfg[0] == LBM_LAUNCH_TMA) {
+    int flow, th;
+    sp_kinds(h, &flow, &th);
+    if (cfg[1] != 4 && cfg[1] != 8) return fail(h, LBM_ERR_ARG, "TMA launch: tile height 4 or 8");
+    if (cfg[2] < 1 || cfg[2] > 4) return fail(h, LBM_ERR_ARG, "TMA launch: 1..4 stages");
+    int occ = lbmk::sp_tma_occupancy(h->p.precision, flow, th, cfg[1], cfg[2]);
+    if (cfg[3] < 1 || cfg[3] > occ)
+      return fail(h, LBM_ERR_ARG, "TMA launch: 1..%d CTAs per SM fit for this tile and stage count", occ);
+    return ensure_tmaps(h, cfg[1]);
+  }
+  return fail(h, LBM_ERR_ARG, "launch kind must be LBM_LAUNCH_GRID or LBM_LAUNCH_TMA");
+}
+
+static void apply_launch(lbm_t h, const int cfg[4]) {
+  h->launch_kind = cfg[0];
+  if (cfg[0] == LBM_LAUNCH_GRID) {
+    h->block = dim3(cfg[1], cfg[2]);
+  } else {
+    h->tma_ty = cfg[1];
+    h->tma_stages = cfg[2];
+    h->tma_ctas = cfg[3];
+  }
+}
+
+extern "C" lbm_status lbm_set_launch(lbm_t h, const int cfg[4]) {
+  if (!h || !cfg) return fail(h, LBM_ERR_ARG, "NULL argument");
+  lbm_status st = check_launch(h, cfg);
+  if (st != LBM_OK) return st;
+  apply_launch(h, cfg);
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_launch_config(lbm_t h, int cfg[4]) {
+  if (!h || !cfg) return fail(h, LBM_ERR_ARG, "NULL argument");
+  cfg[0] = h->launch_kind;
+  if (h->launch_kind == LBM_LAUNCH_GRID) {
+    cfg[1] = (int)h->block.x;
+    cfg[2] = (int)h->block.y;
+    cfg[3] = 0;
+  } else {
+    cfg[1] = h->tma_ty;
+    cfg[2] = h->tma_stages;
+    cfg[3] = h->tma_ctas;
+  }
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
   if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
   if (!h->initialised) return fail(h, LBM_ERR_STATE, "not initialised");
   if (two_phase(h)) return fail(h, LBM_ERR_ARG, "two-phase solves use a fixed 32 x 8 tile");
   int flow, th;
   sp_kinds(h, &flow, &th);
+  // candidates: grid launches of 32..256 threads, then TMA launches
+  int cands[64][4];
+  int nc = 0;
   static const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
-  // The timed launches repeat the next step (same source, same destination), so the
-  // stored state does not change.
+  for (const auto &sh : shapes) {
+    cands[nc][0] = LBM_LAUNCH_GRID; cands[nc][1] = sh[0]; cands[nc][2] = sh[1]; cands[nc][3] = 0;
+    nc++;
+  }
+  for (int ty = 4; ty <= 8; ty += 4)
+    for (int stages = 2; stages <= 4; stages++) {
+      int occ = lbmk::sp_tma_occupancy(h->p.precision, flow, th, ty, stages);
+      for (int ctas = 1; ctas <= occ && ctas <= 4; ctas++) {
+        cands[nc][0] = LBM_LAUNCH_TMA; cands[nc][1] = ty; cands[nc][2] = stages; cands[nc][3] = ctas;
+        nc++;
+      }
+    }
+  // The timed launches repeat the next step (same source, same destination) with
+  // the non-local pull; the destination is rewritten in full by the next real
+  // step, so the stored state does not change.
   SpParams P = sp_params(h, h->cur);
+  P.local = 0;
   cudaEvent_t e0, e1;
   CU(h, cudaEventCreate(&e0));
   CU(h, cudaEventCreate(&e1));
   float best = 1e30f;
-  dim3 bb = h->block;
+  int bestc = -1;
   lbm_status st = LBM_OK;
-  for (const auto &sh : shapes) {
-    dim3 b(sh[0], sh[1]);
-    cudaError_t e = lbmk::sp_step(P, h->p.precision, flow, th, b, h->stream);  // warm-up
+  for (int c = 0; c < nc; c++) {
+    const int *cf = cands[c];
+    if (cf[0] == LBM_LAUNCH_TMA && ensure_tmaps(h, cf[1]) != LBM_OK) continue;  // TMA unavailable: grid only
+    auto launch = [&]() -> cudaError_t {
+      if (cf[0] == LBM_LAUNCH_GRID) return lbmk::sp_step(P, h->p.precision, flow, th, dim3(cf[1], cf[2]), h->stream);
+      return lbmk::sp_step_tma(P, h->tmap[h->cur], h->p.precision, flow, th, cf[1], cf[2], h->nsm * cf[3],
+                               step_flag(h), h->stream);
+    };
+    cudaError_t e = launch();  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-    for (int r = 0; r < 5 && e == cudaSuccess; r++) e = lbmk::sp_step(P, h->p.precision, flow, th, b, h->stream);
+    for (int r = 0; r < 5 && e == cudaSuccess; r++) e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) { st = fail(h, LBM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e)); break; }
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; bb = b; }
+    if (ms < best) { best = ms; bestc = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != LBM_OK) return st;
-  h->block = bb;
-  if (out_block) { out_block[0] = (int)bb.x; out_block[1] = (int)bb.y; }
+  h->err[0] = 0;
+  if (bestc >= 0) {
+    if (cands[bestc][0] == LBM_LAUNCH_TMA) ensure_tmaps(h, cands[bestc][1]);
+    apply_launch(h, cands[bestc]);
+  }
+  if (out_block) {
+    out_block[0] = h->launch_kind == LBM_LAUNCH_GRID ? (int)h->block.x : 32;
+    out_block[1] = h->launch_kind == LBM_LAUNCH_GRID ? (int)h->block.y : h->tma_ty;
+  }
   return LBM_OK;
 }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host C-ABI (lbm_api.cu) and the kernels.
 // Not part of the public interface (include/lbm.h is).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,6 +77,18 @@ cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, c
 cudaError_t sp_batch_step(const SpParams *table, const int4 *tiles, int ntiles, int prec, int flow, int th,
                           dim3 block, int grid, cudaStream_t s);
 int sp_batch_occupancy(int prec, int flow, int th, int threads);
+// TMA-staged persistent step (step_tma.cu).  sp_tma_encode fills the tensor map of
+// one state buffer (3-D: pitch x ny x nq planes, 36 x ty boxes; ty 4 or 8) and
+// returns 0, or nonzero when the driver refuses it.  sp_tma_prepare raises the
+// dynamic shared-memory limit of the kernels of one (prec, flow, th).  The step
+// runs `grid` CTAs of 32 x ty threads with `stages` (1..4) slots of boxes in
+// flight; flag (device int) receives 1 if a copy wait ran out.  P.local must be 0.
+int sp_tma_encode(void *base, int pitch, int ny, int nq, int elem, int ty, CUtensorMap *out);
+cudaError_t sp_tma_prepare(int prec, int flow, int th);
+int sp_tma_occupancy(int prec, int flow, int th, int ty, int stages);
+size_t sp_tma_smem(int prec, int flow, int th, int ty, int stages);
+cudaError_t sp_step_tma(const SpParams &P, const CUtensorMap &map, int prec, int flow, int th, int ty, int stages,
+                        int grid, int *flag, cudaStream_t s);
 // Equilibrium initialisation (pre-collision state of time 0) from double fields (device).
 cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double *a,
                     const double *ux, const double *uy, const double *b, dim3 block,

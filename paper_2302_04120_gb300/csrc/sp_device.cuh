@@ -358,4 +358,31 @@ __device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R 
   if (TH == TH_MRT) collide_mrt5<R>(P, m, g);
 }
 
+// Dispatch of a launcher body over the supported (precision, momentum operator,
+// thermal operator) combinations; CALL(PREC, FLOW, TH) names one instantiation.
+#define LBM_SP_DISPATCH(PREC_, FLOW_, TH_, CALL)                                      \
+  do {                                                                                \
+    if (PREC_ == 0) {                                                                 \
+      if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(0, FLOW_BGK, TH_NONE); }        \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK) { CALL(0, FLOW_BGK, TH_BGK); }     \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT) { CALL(0, FLOW_BGK, TH_MRT); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_NONE) { CALL(0, FLOW_MRT, TH_NONE); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK) { CALL(0, FLOW_MRT, TH_BGK); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(0, FLOW_MRT, TH_MRT); }     \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(0, FLOW_NONE, TH_BGK); }   \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(0, FLOW_NONE, TH_MRT); }   \
+      else return cudaErrorInvalidValue;                                              \
+    } else {                                                                          \
+      if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(1, FLOW_BGK, TH_NONE); }        \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK) { CALL(1, FLOW_BGK, TH_BGK); }     \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT) { CALL(1, FLOW_BGK, TH_MRT); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_NONE) { CALL(1, FLOW_MRT, TH_NONE); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK) { CALL(1, FLOW_MRT, TH_BGK); }     \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(1, FLOW_MRT, TH_MRT); }     \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(1, FLOW_NONE, TH_BGK); }   \
+      else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(1, FLOW_NONE, TH_MRT); }   \
+      else return cudaErrorInvalidValue;                                              \
+    }                                                                                 \
+  } while (0)
+
 }  // namespace lbmk

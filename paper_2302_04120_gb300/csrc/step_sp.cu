@@ -242,30 +242,6 @@ __global__ void __launch_bounds__(256) k_final_reduce(const double *partials, in
 // ----------------------------------------------------------------------------
 static dim3 grid_for(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
 
-#define LBM_SP_DISPATCH(PREC_, FLOW_, TH_, CALL)                                      \
-  do {                                                                                \
-    if (PREC_ == 0) {                                                                 \
-      if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(0, FLOW_BGK, TH_NONE); }        \
-      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK) { CALL(0, FLOW_BGK, TH_BGK); }     \
-      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT) { CALL(0, FLOW_BGK, TH_MRT); }     \
-      else if (FLOW_ == FLOW_MRT && TH_ == TH_NONE) { CALL(0, FLOW_MRT, TH_NONE); }   \
-      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK) { CALL(0, FLOW_MRT, TH_BGK); }     \
-      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(0, FLOW_MRT, TH_MRT); }     \
-      else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(0, FLOW_NONE, TH_BGK); }   \
-      else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(0, FLOW_NONE, TH_MRT); }   \
-      else return cudaErrorInvalidValue;                                              \
-    } else {                                                                          \
-      if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(1, FLOW_BGK, TH_NONE); }        \
-      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK) { CALL(1, FLOW_BGK, TH_BGK); }     \
-      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT) { CALL(1, FLOW_BGK, TH_MRT); }     \
-      else if (FLOW_ == FLOW_MRT && TH_ == TH_NONE) { CALL(1, FLOW_MRT, TH_NONE); }   \
-      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK) { CALL(1, FLOW_MRT, TH_BGK); }     \
-      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(1, FLOW_MRT, TH_MRT); }     \
-      else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(1, FLOW_NONE, TH_BGK); }   \
-      else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(1, FLOW_NONE, TH_MRT); }   \
-      else return cudaErrorInvalidValue;                                              \
-    }                                                                                 \
-  } while (0)
 
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
   dim3 grid = grid_for(P.nx, P.ny, block);

@@ -25,6 +25,7 @@ LBM_FP64, LBM_FP32DEV = 0, 1
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE = 0, 1, 2, 3
 LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW = 0, 1, 2, 3
 LBM_RHO, LBM_UX, LBM_UY, LBM_T, LBM_P, LBM_PHI = 1, 2, 4, 8, 16, 32
+LBM_LAUNCH_GRID, LBM_LAUNCH_TMA = 0, 1
 _MOMENT_BITS = [("rho", 1), ("ux", 2), ("uy", 4), ("T", 8), ("p", 16), ("phi", 32)]
 
 
@@ -115,6 +116,10 @@ def _extra_signatures(L):
     L.lbm_batch_destroy.restype = None
     L.lbm_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
     L.lbm_autotune.restype = C.c_int
+    L.lbm_set_launch.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    L.lbm_set_launch.restype = C.c_int
+    L.lbm_launch_config.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    L.lbm_launch_config.restype = C.c_int
     L.lbm_adjoint.argtypes = [C.c_void_p, C.c_long, C.c_int, C.c_void_p, _dp, C.c_void_p, C.c_void_p, _dp]
     L.lbm_adjoint.restype = C.c_int
 
@@ -249,6 +254,18 @@ def lbm_destroy(h):
     lib().lbm_destroy(h)
 
 
+def lbm_set_launch(h, cfg):
+    """Single-phase step launch: cfg = (kind, a, b, c), see include/lbm.h."""
+    arr = (C.c_int * 4)(*[int(v) for v in cfg])
+    _check(h, lib().lbm_set_launch(h, arr))
+
+
+def lbm_launch_config(h):
+    arr = (C.c_int * 4)()
+    _check(h, lib().lbm_launch_config(h, arr))
+    return tuple(arr)
+
+
 def lbm_adjoint(h, steps, ckpt_every, T_target, nx, ny, want_q3=True, want_qwall=True, want_nu=True):
     """Forward run + reverse-time adjoint: returns (loss, dL/dq3 (ny, nx), dL/dq_wall (2, nx), dL/dnu)."""
     tt = np.ascontiguousarray(np.asarray(T_target, dtype=np.float64))
@@ -358,6 +375,13 @@ class Solver:
         blk = (C.c_int * 2)()
         _check(self.h, lib().lbm_autotune(self.h, blk))
         return blk[0], blk[1]
+
+    def set_launch(self, kind, a, b, c=0):
+        """(LBM_LAUNCH_GRID, block_x, block_y) or (LBM_LAUNCH_TMA, tile_height, stages, ctas_per_sm)."""
+        lbm_set_launch(self.h, (kind, a, b, c))
+
+    def launch_config(self):
+        return lbm_launch_config(self.h)
 
     def check(self):
         return lbm_check(self.h)
