@@ -18,6 +18,11 @@ __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >=
 __device__ __forceinline__ int along(int side, int i, int j) { return side < 2 ? j : i; }
 __device__ __forceinline__ int side_len(const SpParams &P, int side) { return side < 2 ? P.ny : P.nx; }
 
+// Node (i, j) lies on side s (0: x = 0, 1: x = nx - 1, 2: y = 0, 3: y = ny - 1).
+__device__ __forceinline__ bool on_side(const SpParams &P, int s, int i, int j) {
+  return (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
+}
+
 // Which side the link arriving at (i, j) along c = (cx, cy) comes through (source
 // node (i - cx, j - cy) outside the domain), or -1.  y-sides win at corners.
 __device__ __forceinline__ int entry_side(int i, int j, int cx, int cy, int nx, int ny, int xper, int yper) {
@@ -83,15 +88,37 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
     return;
   }
   const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
-  // outlet velocity extrapolation, Eq. anti_BB_vel and the rule below it (reading:
-  // pre-collision velocities of time t at the boundary node and its inner neighbour)
+  // 1. gather, branch-free so that all nine loads are in flight together: the
+  //    streaming source (periodic wrap included), or for a link entering through a
+  //    side the outgoing population o = opp(q) of this node
+  int side[9];
+  R raw[9];
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    side[q] = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper);
+    const long long at = side[q] < 0
+                             ? q * P.plane + (long long)wrap(j - cy9(q), P.ny) * P.pitch + wrap(i - cx9(q), P.nx)
+                             : opp9(q) * P.plane + n;
+    raw[q] = (R)src[at];
+  }
+  // 2. wall / inlet velocities of the sides this node lies on, loaded up front
+  R uws[4][2];
+#pragma unroll
+  for (int s = 0; s < 4; s++) {
+    const double *uw = P.side[s].uw;
+    const bool ld = on_side(P, s, i, j) && uw != nullptr;
+    const int a = along(s, i, j), len = side_len(P, s);
+    uws[s][0] = ld ? (R)uw[a] : (R)0;
+    uws[s][1] = ld ? (R)uw[len + a] : (R)0;
+  }
+  // 3. outlet velocity extrapolation, Eq. anti_BB_vel and the rule below it (reading:
+  //    pre-collision velocities of time t at the boundary node and its inner neighbour)
   R uwp[4][2];
 #pragma unroll
   for (int s = 0; s < 4; s++) { uwp[s][0] = 0; uwp[s][1] = 0; }
 #pragma unroll
   for (int s = 0; s < 4; s++) {
-    bool on = (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
-    if (on && P.side[s].kind == BC_PRESSURE) {
+    if (on_side(P, s, i, j) && P.side[s].kind == BC_PRESSURE) {
       int ii = i + (s == 0) - (s == 1), jj = j + (s == 2) - (s == 3);
       R ub, vb, ui, vi;
       post_velocity<S, R>(P, src, i, j, ub, vb);
@@ -100,30 +127,34 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
       uwp[s][1] = vb + (R)0.5 * (vb - vi);
     }
   }
+  // 4. boundary links (side values picked with compile-time side indices)
 #pragma unroll
   for (int q = 0; q < 9; q++) {
-    const int side = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper);
-    if (side < 0) {
-      int si = wrap(i - cx9(q), P.nx), sj = wrap(j - cy9(q), P.ny);
-      f[q] = (R)src[q * P.plane + (long long)sj * P.pitch + si];
+    if (side[q] < 0) {
+      f[q] = raw[q];
       continue;
     }
-    // outgoing direction o = opp(q) leaves node (i, j) through `side`
     const int o = opp9(q);
-    const R fo = (R)src[o * P.plane + n];
-    const DevSide &sd = P.side[side];
-    const int a = along(side, i, j), len = side_len(P, side);
-    const R rw = K<R>(P).rho_w[side];
+    const R fo = raw[q];
+    int kind = BC_WALL;
+    R rw = 0, ux = 0, uy = 0;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+      if (side[q] == s) {
+        kind = P.side[s].kind;
+        rw = K<R>(P).rho_w[s];
+        ux = kind == BC_PRESSURE ? uwp[s][0] : uws[s][0];
+        uy = kind == BC_PRESSURE ? uwp[s][1] : uws[s][1];
+      }
+    }
     const R cox = c * (R)cx9(o), coy = c * (R)cy9(o);
-    if (sd.kind == BC_PRESSURE) {
+    if (kind == BC_PRESSURE) {
       // Eq. anti_BB_vel in deviation form: f_q - w rho0 = -(f_o* - w rho0) + 2 w [rho_w(...) - rho0]
-      R ux = uwp[side][0], uy = uwp[side][1];
       R cu = cox * ux + coy * uy;
       R uu = ux * ux + uy * uy;
       f[q] = -fo + (R)2 * w9<R>(o) * (rw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - K<R>(P).rho0);
     } else {
       // Eq. BB_vel (walls and velocity inlet): f_q = f_o* - 2 w_o rho_w c_o.u_w / c_s^2
-      R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
       f[q] = fo - (R)2 * w9<R>(o) * rw * (cox * ux + coy * uy) * inv_cs2;
     }
   }
@@ -145,35 +176,66 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
     return;
   }
   const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
+  // 1. gather (branch-free, all five loads in flight together)
+  int side[5], tk[5];
+  R raw[5];
 #pragma unroll
   for (int q = 0; q < 5; q++) {
-    const int side = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
-    if (side < 0) {
-      int si = wrap(i - cx5(q), P.nx), sj = wrap(j - cy5(q), P.ny);
-      g[q] = (R)gsrc[q * P.plane + (long long)sj * P.pitch + si];
+    side[q] = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
+    tk[q] = TBC_NONE;
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+      if (side[q] == s) tk[q] = P.side[s].tkind;
+    long long at;
+    if (side[q] < 0) {
+      at = q * P.plane + (long long)wrap(j - cy5(q), P.ny) * P.pitch + wrap(i - cx5(q), P.nx);
+    } else if (tk[q] == TBC_OUTFLOW) {
+      // g_q(x_b, t+dt) = g_q(x_b-1, t+dt) = g_q*(x_b-1 - c_q dt, t) (Sec. 2.2, outlet)
+      const int ii = i + (side[q] == 0) - (side[q] == 1), jj = j + (side[q] == 2) - (side[q] == 3);
+      const int si = min(max(ii - cx5(q), 0), P.nx - 1), sj = min(max(jj - cy5(q), 0), P.ny - 1);
+      at = q * P.plane + (long long)sj * P.pitch + si;
+    } else {
+      at = opp5(q) * P.plane + n;
+    }
+    raw[q] = (R)gsrc[at];
+  }
+  // 2. wall temperatures / fluxes and velocities of the sides this node lies on
+  R tws[4], uws[4][2];
+#pragma unroll
+  for (int s = 0; s < 4; s++) {
+    const bool on = on_side(P, s, i, j);
+    const double *tw = P.side[s].tw, *uw = P.side[s].uw;
+    const int a = along(s, i, j), len = side_len(P, s);
+    tws[s] = (on && tw) ? (R)tw[a] : (R)0;
+    uws[s][0] = (on && uw) ? (R)uw[a] : (R)0;
+    uws[s][1] = (on && uw) ? (R)uw[len + a] : (R)0;
+  }
+  // 3. boundary links
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    if (side[q] < 0 || tk[q] == TBC_OUTFLOW) {
+      g[q] = raw[q];
       continue;
     }
     const int o = opp5(q);
-    const DevSide &sd = P.side[side];
-    const int a = along(side, i, j), len = side_len(P, side);
-    if (sd.tkind == TBC_OUTFLOW) {
-      // g_q(x_b, t+dt) = g_q(x_b-1, t+dt) = g_q*(x_b-1 - c_q dt, t) (Sec. 2.2, outlet)
-      int ii = i + (side == 0) - (side == 1), jj = j + (side == 2) - (side == 3);
-      int si = min(max(ii - cx5(q), 0), P.nx - 1), sj = min(max(jj - cy5(q), 0), P.ny - 1);
-      g[q] = (R)gsrc[q * P.plane + (long long)sj * P.pitch + si];
-    } else if (sd.tkind == TBC_TEMP) {
+    const R go = raw[q];
+    R Tw = 0, ux = 0, uy = 0;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+      if (side[q] == s) {
+        Tw = tws[s];
+        ux = uws[s][0];
+        uy = uws[s][1];
+      }
+    }
+    if (tk[q] == TBC_TEMP) {
       // Eq. anti_BB_T in deviation form
-      const R go = (R)gsrc[o * P.plane + n];
-      R ux = sd.uw ? (R)sd.uw[a] : (R)0, uy = sd.uw ? (R)sd.uw[len + a] : (R)0;
       R cu = c * ((R)cx5(o) * ux + (R)cy5(o) * uy);
       R uu = ux * ux + uy * uy;
-      R Tw = sd.tw ? (R)sd.tw[a] : (R)0;
       g[q] = -go + (R)2 * w5<R>(o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - K<R>(P).T0);
     } else {
       // Eq. BB_T with lambda = 1 for the single unknown (FLUX; zero flux = adiabatic)
-      const R go = (R)gsrc[o * P.plane + n];
-      R qf = sd.tw ? (R)sd.tw[a] : (R)0;
-      g[q] = go + K<R>(P).flux_coef * qf;
+      g[q] = go + K<R>(P).flux_coef * Tw;
     }
   }
 }

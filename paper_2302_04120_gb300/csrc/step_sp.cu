@@ -38,15 +38,16 @@ namespace lbmk {
 // ----------------------------------------------------------------------------
 // Kernels
 // ----------------------------------------------------------------------------
-// One node: pull with boundary links, moments, collision, store.
-template <int PREC, int FLOW, int TH>
+// One node: pull with boundary links, moments, collision, store.  INNER: the
+// caller guarantees an interior node of a non-local step (no boundary code).
+template <int PREC, int FLOW, int TH, bool INNER = false>
 __device__ __forceinline__ void step_node(const SpParams &P, int i, int j) {
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
   const long long n = (long long)j * P.pitch + i;
   const S *src = (const S *)P.src;
   S *dst = (S *)P.dst;
-  const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
+  const bool interior = INNER || (!P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1));
   R f[9], g[5];
   if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
   if (TH != TH_NONE) pull_g<S, R>(P, src, i, j, interior, g);
@@ -65,6 +66,49 @@ __device__ __forceinline__ void step_node(const SpParams &P, int i, int j) {
   }
 }
 
+// Boundary frame of the grid: rows j = 0 and j = ny - 1, then the columns i = 0
+// and i = nx - 1 between them (each node once, also for nx or ny < 3).  Gives the
+// node of frame index f, or false past the last one.
+__device__ __forceinline__ bool frame_node(int nx, int ny, int f, int &i, int &j) {
+  const int rows = ny >= 2 ? 2 : 1, cols = nx >= 2 ? 2 : 1;
+  if (f < rows * nx) {
+    i = f % nx;
+    j = (f / nx) ? ny - 1 : 0;
+    return true;
+  }
+  f -= rows * nx;
+  const int inner = ny - 2;
+  if (inner <= 0 || f >= cols * inner) return false;
+  i = (f / inner) ? nx - 1 : 0;
+  j = 1 + f % inner;
+  return true;
+}
+
+__host__ __device__ inline int frame_nodes(int nx, int ny) {
+  return (ny >= 2 ? 2 : 1) * nx + (nx >= 2 ? 2 : 1) * (ny > 2 ? ny - 2 : 0);
+}
+
+// A step after the first: the first nfb blocks take the boundary frame (the
+// boundary rules, whose gathers and velocity reconstructions make these nodes the
+// longest-running; they start first), the other blocks the interior tiles of a
+// grid of ntx tiles per row, with the boundary code compiled out.  Keeping the
+// frame in warps of its own spares the interior warps that touch the inlet or
+// outlet column from running both paths one after the other.
+template <int PREC, int FLOW, int TH>
+__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_step_split(const SpParams P, int nfb, int ntx) {
+  const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((int)blockIdx.x < nfb) {
+    int i, j;
+    if (frame_node(P.nx, P.ny, blockIdx.x * nt + tid, i, j)) step_node<PREC, FLOW, TH>(P, i, j);
+    return;
+  }
+  const int t = blockIdx.x - nfb;
+  const int i = (t % ntx) * blockDim.x + threadIdx.x, j = (t / ntx) * blockDim.y + threadIdx.y;
+  if (i <= 0 || j <= 0 || i >= P.nx - 1 || j >= P.ny - 1) return;
+  step_node<PREC, FLOW, TH, true>(P, i, j);
+}
+
+// Every node in one pass (the first step after initialisation, whose pull is local).
 template <int PREC, int FLOW, int TH>
 __global__ void __launch_bounds__(256) k_step(const SpParams P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,6 +289,15 @@ static dim3 grid_for(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x,
 
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
   dim3 grid = grid_for(P.nx, P.ny, block);
+  if (!P.local) {
+    const int nt = block.x * block.y;
+    const int nfb = (frame_nodes(P.nx, P.ny) + nt - 1) / nt;
+    const int nblk = nfb + (int)(grid.x * grid.y);
+#define CALL_SPLIT(A, B, C) k_step_split<A, B, C><<<nblk, block, 0, s>>>(P, nfb, (int)grid.x)
+    LBM_SP_DISPATCH(prec, flow, th, CALL_SPLIT);
+#undef CALL_SPLIT
+    return cudaGetLastError();
+  }
 #define CALL_STEP(A, B, C) k_step<A, B, C><<<grid, block, 0, s>>>(P)
   LBM_SP_DISPATCH(prec, flow, th, CALL_STEP);
 #undef CALL_STEP
