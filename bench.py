@@ -96,7 +96,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY):
+def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY, launch=None):
     """Per-step event timing of the fused step with an L2 flush between steps."""
     from paper_2302_04120_gb300 import lbm
     from paper_2302_04120_gb300 import workloads as wl
@@ -105,7 +105,10 @@ def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY):
     s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
     s.apply_workload(w)
     s.step(1)
-    s.autotune()                             # the library's launch autotuner (grid or TMA-staged)
+    if launch is None:
+        s.autotune()                         # the library's launch autotuner (grid or TMA-staged)
+    else:
+        s.set_launch(*launch)                # a fixed launch (profiling runs)
     launch = s.launch_config()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     flush.fill_(1.0)
@@ -301,13 +304,23 @@ def _cpu_baseline(budget_s=12.0):
 
 
 def _kernel_tag(launch):
-    return "k_step_tma" if launch[0] == 1 else "k_step"
+    return "k_step_tma" if launch[0] == 1 else "k_step_split"
 
 
 def _kernel_name(launch):
     if launch[0] == 1:
         return f"k_step_tma<1,FLOW_MRT,TH_MRT,{launch[1]}>"
-    return "k_step<1,FLOW_MRT,TH_MRT>"
+    return "k_step_split<1,FLOW_MRT,TH_MRT>"
+
+
+def _parse_launch(text):
+    """'grid,BX,BY' or 'tma,TY,STAGES,CTAS_PER_SM' -> lbm_set_launch tuple."""
+    if not text:
+        return None
+    parts = text.split(",")
+    kind = {"grid": 0, "tma": 1}[parts[0]]
+    vals = [int(v) for v in parts[1:]] + [0] * (4 - len(parts))
+    return (kind, vals[0], vals[1], vals[2])
 
 
 def _launch_desc(launch):
@@ -347,13 +360,21 @@ def run_ours(args):
     build.build()
     stream = torch.cuda.Stream()
     cells = CELLS_NX * CELLS_NY
+    launch = _parse_launch(args.launch)
+    if args.profile_step:
+        # only the FP32 2048 x 256 leg (first launch local, then `warmup` + `steps`
+        # launches of the step kernel), for profiler captures of the timed kernel
+        t32, chk32, l32 = _gpu_run(1, args.steps, args.warmup, stream, torch, launch=launch)
+        print(json.dumps({"profile_step": WORKLOAD, "kernel": _kernel_name(l32), "launch": _launch_desc(l32),
+                          "ms_per_step": round(statistics.mean(t32), 5), "status": int(chk32)}), flush=True)
+        return
     # FP64 plain form (same grid), fewer steps: it is ALU-bound on GB300
-    t64, chk64, blk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch)
+    t64, chk64, blk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch, launch=launch)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        t32, chk32, blk32 = _gpu_run(1, args.steps, args.warmup, stream, torch)
+        t32, chk32, blk32 = _gpu_run(1, args.steps, args.warmup, stream, torch, launch=launch)
     torch.cuda.synchronize()
     total_s = sum(t32) / 1e3
     if ws > 1:
@@ -361,7 +382,8 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_s = float(tt.item())
     # roofline-size variant: 8192 x 4096 nodes, 3.8 GB of state (>> 129 MB L2)
-    tsc, chksc, blksc = _gpu_run(1, max(args.steps // 20, 20), args.warmup, stream, torch, nx=8192, ny=4096)
+    tsc, chksc, blksc = _gpu_run(1, max(args.steps // 20, 20), args.warmup, stream, torch, nx=8192, ny=4096,
+                                 launch=launch)
     e2e_s, h2d, d2h = _e2e(1, min(args.steps, 500), args.warmup, stream, torch)
     batch = _batch_run(min(args.steps, 100), stream, torch) if not args.no_batch else None
     adjoint = _adjoint_run(torch) if not args.no_adjoint else None
@@ -474,6 +496,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-two-phase", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="fixed step launch instead of the autotuner: grid,BX,BY or tma,TY,STAGES,CTAS")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -122,13 +122,15 @@ __global__ void __launch_bounds__(256) k_step(const SpParams P) {
 // blockDim.x x blockDim.y tile of one channel, whose parameters (sizes,
 // boundaries, rates, buffers of this parity) sit in a device table.
 template <int PREC, int FLOW, int TH>
-__global__ void __launch_bounds__(256) k_batch_step(const SpParams *__restrict__ table, const int4 *__restrict__ tiles,
+__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_batch_step(const SpParams *__restrict__ table, const int4 *__restrict__ tiles,
                                                      int ntiles) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 tl = tiles[t];  // (channel, x0, y0, unused)
     const SpParams &P = table[tl.x];
     const int i = tl.y + threadIdx.x, j = tl.z + threadIdx.y;
-    if (i < P.nx && j < P.ny) step_node<PREC, FLOW, TH>(P, i, j);
+    if (i >= P.nx || j >= P.ny) continue;
+    if (!P.local && i > 0 && j > 0 && i < P.nx - 1 && j < P.ny - 1) step_node<PREC, FLOW, TH, true>(P, i, j);
+    else step_node<PREC, FLOW, TH>(P, i, j);
   }
 }
 

@@ -35,7 +35,10 @@ def _setup(solver, w):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_batch_equals_one_by_one(prec):
     """57 steps (pre-collision first step, parity alignment, graph pairs and a
-    trailing single step): every channel equals the same channel stepped alone."""
+    trailing single step): every channel equals the same channel stepped alone to
+    rounding -- 1e-13 (FP64) or 1e-6 (FP32) of each field's magnitude.  The batched
+    and the single-solve kernels inline the same arithmetic in different contexts,
+    and the compiler may contract a different pair of operations into an FMA."""
     ws = _small_batch()
     b = lbm.Batch([w["params"] for w in ws], precision=prec)
     for ch, w in zip(b.channels, ws):
@@ -47,7 +50,11 @@ def test_batch_equals_one_by_one(prec):
         s.step(57)
         a, r = b.channels[k].moments(), s.moments()
         for key in ("ux", "uy", "T", "rho"):
-            assert np.array_equal(a[key], r[key]), (k, key, np.max(np.abs(a[key] - r[key])))
+            # T and rho relative to their absolute values (FP32 holds T ~ 300 K to
+            # ~2e-5 K), velocities relative to the largest speed
+            scale = np.max(np.hypot(r["ux"], r["uy"])) if key in ("ux", "uy") else np.max(np.abs(r[key]))
+            tol = 1e-13 if prec == 0 else 1e-6
+            assert np.max(np.abs(a[key] - r[key])) <= tol * scale, (k, key, np.max(np.abs(a[key] - r[key])))
         assert b.channels[k].steps == 57
 
 

@@ -230,16 +230,22 @@ def test_state_roundtrip_device_moments_and_integrals():
 
 
 def test_autotune_keeps_state_and_results():
-    """Autotuning the step's block shape neither advances nor changes the solution."""
+    """Autotuning the step's launch neither advances nor changes the solution: bit
+    for bit when it keeps the grid launch (the block shape does not enter the
+    arithmetic), to FP64 rounding (1e-13) when it picks the TMA-staged kernel."""
     w = wl.channel(nx=100, ny=42, steps=30, Re=100 * 42 / 256)
     a = run_gpu(w, FP64, steps=10)
     blk = a.autotune()
     assert blk[0] * blk[1] % 32 == 0 and a.steps == 10
+    kind = a.launch_config()[0]
     a.step(20)
     b = run_gpu(w, FP64, steps=30)
     ma, mb = a.moments(), b.moments()
     for k in ma:
-        assert np.array_equal(ma[k], mb[k]), k
+        if kind == lbm.LBM_LAUNCH_GRID:
+            assert np.array_equal(ma[k], mb[k]), k
+        else:
+            assert np.max(np.abs(ma[k] - mb[k])) <= 1e-13 * max(np.max(np.abs(mb[k])), 1e-300), k
 
 
 @pytest.mark.parametrize("flow_op,thermal_op", [(0, 1), (1, 1)])
