@@ -53,6 +53,18 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(x, device):
+    """Largest value of x over all ranks of the initialised process group (x itself
+    with one process).  Replicas do independent work; this is the only collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -376,11 +388,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         t32, chk32, blk32 = _gpu_run(1, args.steps, args.warmup, stream, torch, launch=launch)
     torch.cuda.synchronize()
-    total_s = sum(t32) / 1e3
-    if ws > 1:
-        tt = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
+    total_s = _max_over_ranks(sum(t32) / 1e3, "cuda")
     # roofline-size variant: 8192 x 4096 nodes, 3.8 GB of state (>> 129 MB L2)
     tsc, chksc, blksc = _gpu_run(1, max(args.steps // 20, 20), args.warmup, stream, torch, nx=8192, ny=4096,
                                  launch=launch)

@@ -34,12 +34,14 @@ struct lbm_s {
   double *d_uw[4], *d_tw[4];
   double *h_stage[4];        // pinned staging of the boundary arrays, one slot per side
   cudaEvent_t stage_done[4];  // the slot's last upload has been consumed
+  int uw_zero[4], tw_zero[4];  // the device array holds zeros (no upload since the last fill)
   // sources (storage precision, pitched)
   void *d_qdot, *d_force;
   // reductions
   double *d_partials;
   int max_blocks;
-  double *d_out4;  // 4 integrals, then the step kernels' error flag (an int in slot 4)
+  double *d_out4;  // 4 integrals, the step kernels' error flag (an int in slot 4) and the
+                   // integrals' block counter (an unsigned in slot 5, zero between calls)
   double *h_out4;  // pinned, 5 doubles
   dim3 block;
   // single-phase step launch: LBM_LAUNCH_GRID (one node per thread, `block`) or
@@ -280,6 +282,7 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
     if (e != cudaSuccess) { lbm_destroy(h); return fail(NULL, LBM_ERR_NOMEM, "cudaMalloc boundary arrays"); }
     cudaMemsetAsync(h->d_uw[s], 0, sizeof(double) * 2 * len, h->stream);
     cudaMemsetAsync(h->d_tw[s], 0, sizeof(double) * len, h->stream);
+    h->uw_zero[s] = h->tw_zero[s] = 1;
   }
   h->max_blocks = lbmk::sp_integral_blocks(p.nx, p.ny);
   int mpb = lbmk::mp_integral_blocks(p.nx, p.ny);
@@ -356,22 +359,27 @@ extern "C" lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, 
   h->rho_w[side] = rho_w > 0 ? rho_w : h->p.rho0;
   // Copy through this side's pinned staging slot so the call returns without a stream
   // synchronisation (the caller may reuse its arrays at once); wait only until the
-  // slot's previous upload has been consumed.
-  CU(h, cudaEventSynchronize(h->stage_done[side]));
+  // slot's previous upload has been consumed.  A missing array zero-fills the device
+  // copy, unless it already holds zeros.
   double *st = h->h_stage[side];
+  if (uw || tw) CU(h, cudaEventSynchronize(h->stage_done[side]));
   if (uw) {
     memcpy(st, uw, sizeof(double) * 2 * len);
     CU(h, cudaMemcpyAsync(h->d_uw[side], st, sizeof(double) * 2 * len, cudaMemcpyHostToDevice, h->stream));
-  } else {
+    h->uw_zero[side] = 0;
+  } else if (!h->uw_zero[side]) {
     CU(h, cudaMemsetAsync(h->d_uw[side], 0, sizeof(double) * 2 * len, h->stream));
+    h->uw_zero[side] = 1;
   }
   if (tw) {
     memcpy(st + 2 * len, tw, sizeof(double) * len);
     CU(h, cudaMemcpyAsync(h->d_tw[side], st + 2 * len, sizeof(double) * len, cudaMemcpyHostToDevice, h->stream));
-  } else {
+    h->tw_zero[side] = 0;
+  } else if (!h->tw_zero[side]) {
     CU(h, cudaMemsetAsync(h->d_tw[side], 0, sizeof(double) * len, h->stream));
+    h->tw_zero[side] = 1;
   }
-  CU(h, cudaEventRecord(h->stage_done[side], h->stream));
+  if (uw || tw) CU(h, cudaEventRecord(h->stage_done[side], h->stream));
   return LBM_OK;
 }
 
@@ -553,7 +561,8 @@ extern "C" lbm_status lbm_integrals(lbm_t h, double out[4]) {
     int flow, th;
     sp_kinds(h, &flow, &th);
     SpParams P = sp_params(h, h->cur);
-    e = lbmk::sp_integrals(P, h->p.precision, flow, th, h->d_partials, h->max_blocks, h->d_out4, h->stream);
+    e = lbmk::sp_integrals(P, h->p.precision, flow, th, h->d_partials, h->max_blocks, h->d_out4,
+                           (unsigned *)(h->d_out4 + 5), h->stream);
   }
   if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "integrals launch: %s", cudaGetErrorString(e));
   CU(h, cudaMemcpyAsync(h->h_out4, h->d_out4, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

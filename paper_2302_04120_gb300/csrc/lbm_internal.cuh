@@ -97,8 +97,9 @@ cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double 
 cudaError_t sp_moments(const SpParams &P, int prec, int flow, int th, unsigned mask,
                        double *out, cudaStream_t s);
 // Per-block partial integrals (4 doubles per block) then a fixed-order final reduction.
+// counter: a device unsigned that is 0 on entry; the kernel's last block resets it.
 cudaError_t sp_integrals(const SpParams &P, int prec, int flow, int th, double *partials,
-                         int max_blocks, double *out4, cudaStream_t s);
+                         int max_blocks, double *out4, unsigned *counter, cudaStream_t s);
 int sp_integral_blocks(int nx, int ny);
 
 // Convert nx*ny double planes into pitched storage planes (sources, forces).

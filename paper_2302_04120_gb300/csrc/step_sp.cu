@@ -223,8 +223,44 @@ __device__ __forceinline__ void block_partials(double drho, double u2, int bad, 
   }
 }
 
+// Fixed-order sum of the nb per-block partials by one 256-thread block: thread t sums
+// partials t, t + 256, ... in order, then a fixed tree.  mass = (N rho0 + sum (rho -
+// rho0)) dx^2, max |u| = sqrt(max |u|^2).
+__device__ __forceinline__ void final_reduce(const double *partials, int nb, double n_rho0, double area,
+                                             double *out4) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  double a = 0, b = 0, mx = 0, cnt = 0;
+  for (int k = t; k < nb; k += 256) {
+    a += __ldcg(partials + 4 * k + 0);
+    b += __ldcg(partials + 4 * k + 1);
+    mx = fmax(mx, __ldcg(partials + 4 * k + 2));
+    cnt += __ldcg(partials + 4 * k + 3);
+  }
+  __shared__ double sh[4][256];
+  sh[0][t] = a; sh[1][t] = b; sh[2][t] = mx; sh[3][t] = cnt;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) {
+      sh[0][t] += sh[0][t + w];
+      sh[1][t] += sh[1][t + w];
+      sh[2][t] = fmax(sh[2][t], sh[2][t + w]);
+      sh[3][t] += sh[3][t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out4[0] = (n_rho0 + sh[0][0]) * area;
+    out4[1] = sh[1][0];
+    out4[2] = sqrt(sh[2][0]);
+    out4[3] = sh[3][0];
+  }
+}
+
+// Integrals in one launch: every block writes its partials; the block that counts
+// last (a device counter, 0 on entry and reset by that block) makes the final pass.
 template <int PREC, int FLOW, int TH>
-__global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *partials) {
+__global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *partials, double n_rho0, double area,
+                                                   double *out4, unsigned *counter) {
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,37 +285,17 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
     if (bad) { drho = 0.0; u2 = 0.0; }
   }
   block_partials(drho, u2, bad, partials + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
-}
-
-// One block of 256 threads: thread t sums partials t, t + 256, ... in order, then a
-// fixed tree.  mass = (N rho0 + sum (rho - rho0)) dx^2, max |u| = sqrt(max |u|^2).
-__global__ void __launch_bounds__(256) k_final_reduce(const double *partials, int nb, double n_rho0, double area,
-                                                      double *out4) {
-  const int t = threadIdx.x;
-  double a = 0, b = 0, mx = 0, cnt = 0;
-  for (int k = t; k < nb; k += 256) {
-    a += partials[4 * k + 0];
-    b += partials[4 * k + 1];
-    mx = fmax(mx, partials[4 * k + 2]);
-    cnt += partials[4 * k + 3];
+  const unsigned nb = gridDim.x * gridDim.y;
+  __shared__ bool last;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();  // this block's partials before its count
+    last = atomicAdd(counter, 1u) == nb - 1;
   }
-  __shared__ double sh[4][256];
-  sh[0][t] = a; sh[1][t] = b; sh[2][t] = mx; sh[3][t] = cnt;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (t < w) {
-      sh[0][t] += sh[0][t + w];
-      sh[1][t] += sh[1][t + w];
-      sh[2][t] = fmax(sh[2][t], sh[2][t + w]);
-      sh[3][t] += sh[3][t + w];
-    }
-    __syncthreads();
-  }
-  if (t == 0) {
-    out4[0] = (n_rho0 + sh[0][0]) * area;
-    out4[1] = sh[1][0];
-    out4[2] = sqrt(sh[2][0]);
-    out4[3] = sh[3][0];
+  if (last) {
+    __threadfence();
+    final_reduce(partials, (int)nb, n_rho0, area, out4);
+    if (threadIdx.x == 0 && threadIdx.y == 0) *counter = 0u;
   }
 }
 
@@ -369,14 +385,13 @@ int sp_integral_blocks(int nx, int ny) {
 }
 
 cudaError_t sp_integrals(const SpParams &P, int prec, int flow, int th, double *partials, int max_blocks,
-                         double *out4, cudaStream_t s) {
+                         double *out4, unsigned *counter, cudaStream_t s) {
   dim3 grid = grid_for(P.nx, P.ny, kRedBlock);
   if ((int)(grid.x * grid.y) > max_blocks) return cudaErrorInvalidValue;
-#define CALL_INT(A, B, C) k_integrals<A, B, C><<<grid, kRedBlock, 0, s>>>(P, partials)
+  const double n_rho0 = (double)P.nx * P.ny * P.rho0, area = P.dx * P.dx;
+#define CALL_INT(A, B, C) k_integrals<A, B, C><<<grid, kRedBlock, 0, s>>>(P, partials, n_rho0, area, out4, counter)
   LBM_SP_DISPATCH(prec, flow, th, CALL_INT);
 #undef CALL_INT
-  k_final_reduce<<<1, 256, 0, s>>>(partials, (int)(grid.x * grid.y), (double)P.nx * P.ny * P.rho0, P.dx * P.dx,
-                                   out4);
   return cudaGetLastError();
 }
 
