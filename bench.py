@@ -254,9 +254,9 @@ def _adjoint_run(torch):
 
 
 def _two_phase_run(steps, stream, torch):
-    """The bubble workload (512 x 512, saturated water 25 C): per-step time of the two
-    launches (phi pass + collide pass) with an L2 flush between steps, FP32 (FP64 u/p
-    recovery) and FP64; plus a 4096 x 4096 roofline-size run of the same kernels."""
+    """The bubble workload (512 x 512, saturated water 25 C): per-step time of the
+    one-launch two-phase step with an L2 flush between steps, FP32 (FP64 rho/u/p
+    recovery across the interface) and FP64; plus a 4096 x 4096 roofline-size run."""
     from paper_2302_04120_gb300 import lbm
     from paper_2302_04120_gb300 import workloads as wl
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -373,6 +373,28 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     cells = CELLS_NX * CELLS_NY
     launch = _parse_launch(args.launch)
+    from paper_2302_04120_gb300 import lbm
+
+    def wl_bubble(n):
+        from paper_2302_04120_gb300 import workloads as wl
+        return wl.bubble(n=n, R_cells=n / 8, W_cells=5.0, steps=0)
+    if args.profile_two_phase:
+        # only a 1024 x 1024 FP32 bubble (134 MB of state, above L2), for profiler captures
+        w = wl_bubble(1024)
+        s2 = lbm.Solver(w["params"], precision=1, stream=stream.cuda_stream)
+        s2.init(**w["init"])
+        s2.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s2.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_two_phase": "bubble_1024x1024_R128_sat_water_25C", "kernel": "k_mp_collide<1,0>",
+                          "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 5), "status": int(s2.check())}),
+              flush=True)
+        s2.close()
+        return
     if args.profile_step:
         # only the FP32 2048 x 256 leg (first launch local, then `warmup` + `steps`
         # launches of the step kernel), for profiler captures of the timed kernel
@@ -508,6 +530,8 @@ def main():
                     help="fixed step launch instead of the autotuner: grid,BX,BY or tma,TY,STAGES,CTAS")
     ap.add_argument("--profile-step", action="store_true",
                     help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
+    ap.add_argument("--profile-two-phase", action="store_true",
+                    help="run only a 1024x1024 FP32 bubble (for ncu captures of the two-phase kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -167,6 +167,7 @@ static void fill_mp_const(const lbmk::MpParams &P, lbmk::MpConst<R> &k) {
   k.dzeta = (R)(P.rho_l * P.nu_l - P.rho_g * P.nu_g); k.inv_cs2dt = (R)P.inv_cs2dt;
   k.Fx = (R)P.Fx; k.Fy = (R)P.Fy; k.hdt = (R)(0.5 * P.dt); k.pcoef = (R)(P.cs2 * 1.8);
   k.om_h = (R)P.om_h; k.sfac_h = (R)P.sfac_h; k.aint_coef = (R)P.aint_coef; k.inv_dt = (R)P.inv_dt;
+  k.ic = (R)1 / (R)P.c;
 }
 
 static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {

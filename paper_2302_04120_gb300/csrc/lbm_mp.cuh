@@ -9,7 +9,7 @@ namespace lbmk {
 template <typename R>
 struct MpConst {
   R c, dt, inv_cs2, g3, l6, beta, kappa, rho_g, drl, nu_g, dnu, zg, dzeta, inv_cs2dt;
-  R Fx, Fy, hdt, pcoef, om_h, sfac_h, aint_coef, inv_dt;
+  R Fx, Fy, hdt, pcoef, om_h, sfac_h, aint_coef, inv_dt, ic;
 };
 
 // Two-phase solve on a fully periodic grid.  State planes: z_0..8, h_0..4,

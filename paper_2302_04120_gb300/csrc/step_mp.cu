@@ -42,6 +42,29 @@ __device__ __forceinline__ void pull_h(const MpParams &P, const S *src, int i, i
   }
 }
 
+// The same pulls for a node whose sources cannot wrap (blocks away from the grid's
+// periodic seams): sn points at the node in plane 0; every plane offset is uniform.
+template <typename S, typename R>
+__device__ __forceinline__ void pull_h_at(const MpParams &P, const S *sn, R h[5]) {
+  const S *hs = sn + 9ll * P.plane;
+#pragma unroll
+  for (int q = 0; q < 5; q++) h[q] = (R)hs[q * P.plane - (long long)cy5(q) * P.pitch - cx5(q)];
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void pull_z_at(const MpParams &P, const S *sn, R z[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; q++) z[q] = (R)sn[q * P.plane - (long long)cy9(q) * P.pitch - cx9(q)];
+}
+
+// Quotient in the working precision: exact in FP64; in FP32 the approximate
+// reciprocal-based divide (about 2 ulp), which spares the IEEE divide sequence.
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+// 1 / |g| for g2 = |g|^2 > 0, else 0 (same precision split).
+__device__ __forceinline__ double inv_norm(double g2) { return g2 != 0.0 ? 1.0 / sqrt(g2) : 0.0; }
+__device__ __forceinline__ float inv_norm(float g2) { return g2 != 0.0f ? rsqrtf(g2) : 0.0f; }
+
 template <typename S, typename R>
 __device__ __forceinline__ void pull_z(const MpParams &P, const S *src, int i, int j, R z[9]) {
 #pragma unroll
@@ -86,15 +109,16 @@ __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX +
   m.phi = pc;
   // Eq. chemical_potential
   m.mu = (R)4 * K.beta * pc * (pc - (R)1) * (pc - (R)0.5) - K.kappa * lap;
-  const R gn = sqrt(m.gx * m.gx + m.gy * m.gy);
-  m.nxv = gn != (R)0 ? m.gx / gn : (R)0;  // normal only where |grad phi| != 0
-  m.nyv = gn != (R)0 ? m.gy / gn : (R)0;
+  // normal only where |grad phi| != 0
+  const R rg = inv_norm(m.gx * m.gx + m.gy * m.gy);
+  m.nxv = m.gx * rg;
+  m.nyv = m.gy * rg;
   const R drl = K.drl;
   R nu;
   if (P.nu_rule == 0) nu = K.nu_g + pc * K.dnu;
-  else nu = (K.zg + pc * K.dzeta) / (K.rho_g + pc * drl);
+  else nu = qdiv(K.zg + pc * K.dzeta, K.rho_g + pc * drl);
   // tau / dt = nu / (c_s^2 dt) + 1/2 (Eq. eq_kinematic_viscosity)
-  m.wb = (R)1 / (nu * K.inv_cs2dt + (R)0.5);
+  m.wb = qdiv((R)1, nu * K.inv_cs2dt + (R)0.5);
   m.drx = drl * m.gx;
   m.dry = drl * m.gy;
   m.Fx = m.mu * m.gx + K.Fx + fext_x;
@@ -126,7 +150,7 @@ __device__ __forceinline__ void mp_macro(const MpParams &P, const R (*tile)[BX +
     const R jy = c * ((z[2] - z[4]) + (z[5] - z[8]) + (z[6] - z[7]));
     const R znz = ((z[1] + z[2]) + (z[3] + z[4])) + ((z[5] + z[6]) + (z[7] + z[8]));
     const R rho = K.rho_g + pc * K.drl;
-    const R inv = (R)1 / rho;
+    const R inv = qdiv((R)1, rho);
     const R hdt = K.hdt;
     const R ux = (jx + hdt * m.Fx) * inv, uy = (jy + hdt * m.Fy) * inv;
     const R s0 = (R)(4.0 / 9.0) * ((R)-0.5 * (ux * ux + uy * uy) * K.inv_cs2);
@@ -186,7 +210,7 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m
   // MRT on lattice-scaled moments (see step_sp.cu): equilibrium moments of z_eq
   // are M f_eq(rho, u) - rho M w + (p/c_s^2)(M w - M e_0); forcing moments of
   // F_hat^z = w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2.
-  const R ic = (R)1 / c;
+  const R ic = K.ic;
   const R hx = ux * ic, hy = uy * ic, usq = hx * hx + hy * hy;
   const R Pp = m.p * K.inv_cs2;
   const R s14 = (z[1] + z[2]) + (z[3] + z[4]);
@@ -213,7 +237,7 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m
   // q_y by the isotropic reading) and 1/tau for the stress moments
   // omega_q2 dt = 3 (2 - omega_nu dt) / (3 - omega_nu dt), omega_nu dt = dt / tau (Sec. 3)
   const R snu = m.wb;
-  const R sq = (R)3 * ((R)2 - snu) / ((R)3 - snu);
+  const R sq = qdiv((R)3 * ((R)2 - snu), (R)3 - snu);
   const R sqy = P.qy_literal ? (R)1 : sq;
   const R rdt = K.dt, one = (R)1, half = (R)0.5;
   const R d0 = m0 - half * rdt * F0;                 // s = 1: (m - 0) - (1 - 1/2) dt F
@@ -280,12 +304,17 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
   const S *src = (const S *)P.src;
   // phi = sum_i h_i (Eq. zero_moment_h) of the tile and of a one-node periodic halo,
   // from pulled h: this node's h stays in registers for its collision
+  // a block whose tile, halo and their pull sources stay off the periodic seams
+  // (the bulk of the grid) pulls with plain offsets: no wrap, no modulo
+  const bool inner = !P.local && i0 >= 2 && j0 >= 2 && i0 + BX + 2 <= P.nx && j0 + BY + 2 <= P.ny;
   R h[5];
-  {
+  if (inner) {
+    pull_h_at<S, R>(P, src + ((long long)j * P.pitch + i), h);
+  } else {
     const int gi = i < P.nx ? i : modi(i, P.nx), gj = j < P.ny ? j : modi(j, P.ny);
     pull_h<S, R>(P, src, gi, gj, h);
-    tile[threadIdx.y + 1][threadIdx.x + 1] = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
   }
+  tile[threadIdx.y + 1][threadIdx.x + 1] = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
   constexpr int kHalo = 2 * (BX + 2) + 2 * BY;
   for (int t = tid; t < kHalo; t += BX * BY) {
     int tx, ty;
@@ -293,9 +322,13 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
     else if (t < 2 * (BX + 2)) { tx = t - (BX + 2); ty = BY + 1; }  // row above
     else if (t < 2 * (BX + 2) + BY) { tx = 0; ty = t - 2 * (BX + 2) + 1; }  // left column
     else { tx = BX + 1; ty = t - 2 * (BX + 2) - BY + 1; }           // right column
-    const int gi = modi(i0 + tx - 1, P.nx), gj = modi(j0 + ty - 1, P.ny);
     R hh[5];
-    pull_h<S, R>(P, src, gi, gj, hh);
+    if (inner) {
+      pull_h_at<S, R>(P, src + ((long long)(j0 + ty - 1) * P.pitch + (i0 + tx - 1)), hh);
+    } else {
+      const int gi = modi(i0 + tx - 1, P.nx), gj = modi(j0 + ty - 1, P.ny);
+      pull_h<S, R>(P, src, gi, gj, hh);
+    }
     tile[ty][tx] = (hh[0] + hh[1]) + (hh[2] + hh[3]) + hh[4];
   }
   __syncthreads();
@@ -309,7 +342,8 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
       fex = (R)((const S *)P.force)[n];
       fey = (R)((const S *)P.force)[P.plane + n];
     }
-    pull_z<S, R>(P, src, i, j, z);
+    if (inner) pull_z_at<S, R>(P, src + n, z);
+    else pull_z<S, R>(P, src, i, j, z);
     prevx = (R)src[14ll * P.plane + n];
     prevy = (R)src[15ll * P.plane + n];
     MpMacro<R> m;
