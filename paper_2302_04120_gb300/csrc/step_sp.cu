@@ -88,22 +88,22 @@ __host__ __device__ inline int frame_nodes(int nx, int ny) {
   return (ny >= 2 ? 2 : 1) * nx + (nx >= 2 ? 2 : 1) * (ny > 2 ? ny - 2 : 0);
 }
 
-// A step after the first: the first nfb blocks take the boundary frame (the
-// boundary rules, whose gathers and velocity reconstructions make these nodes the
-// longest-running; they start first), the other blocks the interior tiles of a
-// grid of ntx tiles per row, with the boundary code compiled out.  Keeping the
+// A step after the first, on a grid of gridDim.x tiles per row: the first fy rows of
+// blocks take the boundary frame (the boundary rules, whose gathers and velocity
+// reconstructions make these nodes the longest-running; they start first), the
+// other rows the interior tiles, with the boundary code compiled out.  Keeping the
 // frame in warps of its own spares the interior warps that touch the inlet or
 // outlet column from running both paths one after the other.
 template <int PREC, int FLOW, int TH>
-__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_step_split(const SpParams P, int nfb, int ntx) {
-  const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if ((int)blockIdx.x < nfb) {
+__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_step_split(const SpParams P, int fy) {
+  if ((int)blockIdx.y < fy) {
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
     int i, j;
-    if (frame_node(P.nx, P.ny, blockIdx.x * nt + tid, i, j)) step_node<PREC, FLOW, TH>(P, i, j);
+    if (frame_node(P.nx, P.ny, (blockIdx.y * gridDim.x + blockIdx.x) * nt + tid, i, j))
+      step_node<PREC, FLOW, TH>(P, i, j);
     return;
   }
-  const int t = blockIdx.x - nfb;
-  const int i = (t % ntx) * blockDim.x + threadIdx.x, j = (t / ntx) * blockDim.y + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = (blockIdx.y - fy) * blockDim.y + threadIdx.y;
   if (i <= 0 || j <= 0 || i >= P.nx - 1 || j >= P.ny - 1) return;
   step_node<PREC, FLOW, TH, true>(P, i, j);
 }
@@ -307,11 +307,12 @@ static dim3 grid_for(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x,
 
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
   dim3 grid = grid_for(P.nx, P.ny, block);
-  if (!P.local) {
-    const int nt = block.x * block.y;
-    const int nfb = (frame_nodes(P.nx, P.ny) + nt - 1) / nt;
-    const int nblk = nfb + (int)(grid.x * grid.y);
-#define CALL_SPLIT(A, B, C) k_step_split<A, B, C><<<nblk, block, 0, s>>>(P, nfb, (int)grid.x)
+  const int nt = block.x * block.y;
+  const int nfb = (frame_nodes(P.nx, P.ny) + nt - 1) / nt;  // frame blocks
+  const int fy = (nfb + (int)grid.x - 1) / (int)grid.x;      // rows of them
+  if (!P.local && grid.y + fy <= 65535u) {                   // else the one-pass kernel
+    const dim3 g2(grid.x, grid.y + fy);
+#define CALL_SPLIT(A, B, C) k_step_split<A, B, C><<<g2, block, 0, s>>>(P, fy)
     LBM_SP_DISPATCH(prec, flow, th, CALL_SPLIT);
 #undef CALL_SPLIT
     return cudaGetLastError();
