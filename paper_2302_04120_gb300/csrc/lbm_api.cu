@@ -738,16 +738,26 @@ extern "C" lbm_t lbm_batch_channel(lbm_batch_t b, int k) {
 
 extern "C" int lbm_batch_size(lbm_batch_t b) { return b ? b->n : 0; }
 
-// (Re)build the tile list for a tile shape.
+// (Re)build the entry list for a tile shape: every channel's boundary frame in
+// chunks of bx*by nodes first (the longest-running nodes start first), then the
+// interior tiles.
 static lbm_status batch_tiles(lbm_batch_t b, int bx, int by) {
   if (b->d_tiles && b->tiles_bx == bx && b->tiles_by == by) return LBM_OK;
+  const int chunk = bx * by;
   long long total = 0;
-  for (int k = 0; k < b->n; k++)
-    total += (long long)((b->ch[k]->p.nx + bx - 1) / bx) * ((b->ch[k]->p.ny + by - 1) / by);
+  for (int k = 0; k < b->n; k++) {
+    const int nx = b->ch[k]->p.nx, ny = b->ch[k]->p.ny;
+    total += (lbmk::frame_nodes(nx, ny) + chunk - 1) / chunk;
+    total += (long long)((nx + bx - 1) / bx) * ((ny + by - 1) / by);
+  }
   if (total > (1ll << 31) - 1) return bfail(b, LBM_ERR_ARG, "too many tiles");
   int4 *h = (int4 *)malloc(sizeof(int4) * (size_t)total);
   if (!h) return bfail(b, LBM_ERR_NOMEM, "host allocation failed");
   long long t = 0;
+  for (int k = 0; k < b->n; k++) {
+    const int nf = lbmk::frame_nodes(b->ch[k]->p.nx, b->ch[k]->p.ny);
+    for (int f0 = 0; f0 < nf; f0 += chunk) h[t++] = make_int4(k, f0, 0, 1);
+  }
   for (int k = 0; k < b->n; k++) {
     const int nx = b->ch[k]->p.nx, ny = b->ch[k]->p.ny;
     for (int y0 = 0; y0 < ny; y0 += by)

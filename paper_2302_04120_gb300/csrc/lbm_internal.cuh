@@ -68,12 +68,19 @@ template <>
 __device__ __forceinline__ const SpConst<float> &K<float>(const SpParams &P) { return P.kf; }
 
 enum { FLOW_NONE = 0, FLOW_BGK = 1, FLOW_MRT = 2 };
+
+// Nodes of the boundary frame of an nx x ny grid: rows j = 0 and ny - 1, then the
+// columns i = 0 and nx - 1 between them (each node once, also for nx or ny < 3).
+__host__ __device__ inline int frame_nodes(int nx, int ny) {
+  return (ny >= 2 ? 2 : 1) * nx + (nx >= 2 ? 2 : 1) * (ny > 2 ? ny - 2 : 0);
+}
 enum { TH_NONE = 0, TH_BGK = 1, TH_MRT = 2 };
 
 // Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
 // One step of many solves: table[k] holds the parameters (with this step's src/dst)
-// of channel k; tiles lists (channel, x0, y0) of every blockDim-sized tile.
+// of channel k; tiles lists the frame chunks (channel, f0, 0, 1) and the interior
+// tiles (channel, x0, y0, 0) of every channel.
 cudaError_t sp_batch_step(const SpParams *table, const int4 *tiles, int ntiles, int prec, int flow, int th,
                           dim3 block, int grid, cudaStream_t s);
 int sp_batch_occupancy(int prec, int flow, int th, int threads);

@@ -84,9 +84,6 @@ __device__ __forceinline__ bool frame_node(int nx, int ny, int f, int &i, int &j
   return true;
 }
 
-__host__ __device__ inline int frame_nodes(int nx, int ny) {
-  return (ny >= 2 ? 2 : 1) * nx + (nx >= 2 ? 2 : 1) * (ny > 2 ? ny - 2 : 0);
-}
 
 // A step after the first, on a grid of gridDim.x tiles per row: the first fy rows of
 // blocks take the boundary frame (the boundary rules, whose gathers and velocity
@@ -117,20 +114,28 @@ __global__ void __launch_bounds__(256) k_step(const SpParams P) {
   step_node<PREC, FLOW, TH>(P, i, j);
 }
 
-// Many independent solves in one launch: blocks walk a flattened list of
-// (channel, tile origin) entries with a grid stride; each entry is one
-// blockDim.x x blockDim.y tile of one channel, whose parameters (sizes,
-// boundaries, rates, buffers of this parity) sit in a device table.
+// Many independent solves in one launch: blocks walk a flattened list of entries
+// with a grid stride; the channel's parameters (sizes, boundaries, rates, buffers of
+// this parity) sit in a device table.  An entry (channel, x0, y0, 0) is one
+// blockDim.x x blockDim.y tile of the channel's interior; an entry (channel, f0, 0, 1)
+// is blockDim.x * blockDim.y consecutive nodes of its boundary frame from frame
+// index f0 (the list puts these first), as in k_step_split.
 template <int PREC, int FLOW, int TH>
 __global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_batch_step(const SpParams *__restrict__ table, const int4 *__restrict__ tiles,
                                                      int ntiles) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int4 tl = tiles[t];  // (channel, x0, y0, unused)
+    const int4 tl = tiles[t];
     const SpParams &P = table[tl.x];
+    if (tl.w == 1) {
+      int i, j;
+      const int f = tl.y + threadIdx.y * blockDim.x + threadIdx.x;
+      if (frame_node(P.nx, P.ny, f, i, j)) step_node<PREC, FLOW, TH>(P, i, j);
+      continue;
+    }
     const int i = tl.y + threadIdx.x, j = tl.z + threadIdx.y;
-    if (i >= P.nx || j >= P.ny) continue;
-    if (!P.local && i > 0 && j > 0 && i < P.nx - 1 && j < P.ny - 1) step_node<PREC, FLOW, TH, true>(P, i, j);
-    else step_node<PREC, FLOW, TH>(P, i, j);
+    if (i <= 0 || j <= 0 || i >= P.nx - 1 || j >= P.ny - 1) continue;  // frame entries
+    if (P.local) step_node<PREC, FLOW, TH>(P, i, j);
+    else step_node<PREC, FLOW, TH, true>(P, i, j);
   }
 }
 
