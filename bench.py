@@ -315,6 +315,74 @@ def _cpu_baseline(budget_s=12.0):
                 sample=f"channel 256x{CELLS_NY} slice of the 2048x{CELLS_NY} workload, {n} steps, FP64, OpenMP")
 
 
+def _cpu_baseline_1thread(budget_s=6.0):
+    """The same oracle sample on one host thread (a subprocess with OMP_NUM_THREADS=1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = f"import json, bench; print(json.dumps(bench._cpu_baseline({budget_s})))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return dict(value=d["value"], cores=d["cores"], sample=d["sample"])
+
+
+def _roofline_d2q9(steps, warmup, stream, torch, launch=None):
+    """D2Q9 BGK alone (the Poiseuille configuration's lattice and collision) on an
+    8192 x 4096 periodic channel with walls, FP32 deviation storage: 72 B/node,
+    2.4 GB of state (> 129 MB L2, so no flush is needed)."""
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    w = wl.poiseuille(nx=8192, ny=4096, steps=0)
+    s = lbm.Solver(w["params"], precision=1, stream=stream.cuda_stream)
+    for bc in w["bcs"]:
+        s.set_bc(*bc)
+    s.init()
+    s.step(1)
+    if launch is None:
+        s.autotune()
+    else:
+        s.set_launch(*launch)
+    cfg = s.launch_config()
+    with torch.cuda.stream(stream):
+        s.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    chk = s.check()
+    s.close()
+    peak, _ = _peaks()
+    n = 8192 * 4096
+    return {"workload": "poiseuille_d2q9_bgk_8192x4096", "bound": "hbm", "value": round(n / t / 1e6, 1),
+            "unit_value": "MLUPS", "achieved": round(72 * n / t / 1e9, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(72 * n / t / 1e9 / peak, 4), "steps": steps, "status": int(chk),
+            "kernel": "k_step_split<1,FLOW_BGK,TH_NONE>", "launch": _launch_desc(cfg),
+            "l2": "state 2.4 GB, larger than L2; back-to-back steps"}
+
+
+# FP64 work per node of the FP64 step k_step_split<0,2,2> (D2Q9 MRT + D2Q5 MRT) on
+# the 2048 x 256 channel, from one ncu capture (profiles/k_step_split_fp64_channel_2048x256.md):
+# 89.02 DADD + 40.11 DMUL + 69.17 DFMA thread instructions per node.
+FP64_FLOPS_PER_NODE = 267.5   # DADD + DMUL + 2 DFMA
+FP64_INSTR_PER_NODE = 198.3   # FP64-pipe instructions (one issue slot each)
+
+
+def _fp64_alu(cells, avg_s, fma64_gflops):
+    """The FP64 form against its arithmetic bound: executed FP64 flops per second
+    over the probe's FMA rate, and FP64-pipe instructions per second over the probe's
+    instruction rate (half its flop rate: one FMA = 2 flops, one issue)."""
+    ach = FP64_FLOPS_PER_NODE * cells / avg_s / 1e9
+    inst = FP64_INSTR_PER_NODE * cells / avg_s / 1e9
+    return {"bound": "alu", "flops_per_node": FP64_FLOPS_PER_NODE, "achieved_gflops": round(ach, 1),
+            "peak_gflops": round(fma64_gflops, 1), "peak_source": "lbm_probe_fma_rate",
+            "frac": round(ach / fma64_gflops, 4),
+            "fp64_instr_per_node": FP64_INSTR_PER_NODE, "achieved_ginstr": round(inst, 1),
+            "frac_pipe": round(inst / (fma64_gflops / 2), 4)}
+
+
 def _kernel_tag(launch):
     return "k_step_tma" if launch[0] == 1 else "k_step_split"
 
@@ -398,8 +466,9 @@ def run_ours(args):
     if args.profile_step:
         # only the FP32 2048 x 256 leg (first launch local, then `warmup` + `steps`
         # launches of the step kernel), for profiler captures of the timed kernel
-        t32, chk32, l32 = _gpu_run(1, args.steps, args.warmup, stream, torch, launch=launch)
-        print(json.dumps({"profile_step": WORKLOAD, "kernel": _kernel_name(l32), "launch": _launch_desc(l32),
+        t32, chk32, l32 = _gpu_run(args.profile_prec, args.steps, args.warmup, stream, torch, launch=launch)
+        kname = _kernel_name(l32).replace("<1,", f"<{args.profile_prec},", 1)
+        print(json.dumps({"profile_step": WORKLOAD, "kernel": kname, "launch": _launch_desc(l32),
                           "ms_per_step": round(statistics.mean(t32), 5), "status": int(chk32)}), flush=True)
         return
     # FP64 plain form (same grid), fewer steps: it is ALU-bound on GB300
@@ -414,6 +483,9 @@ def run_ours(args):
     # roofline-size variant: 8192 x 4096 nodes, 3.8 GB of state (>> 129 MB L2)
     tsc, chksc, blksc = _gpu_run(1, max(args.steps // 20, 20), args.warmup, stream, torch, nx=8192, ny=4096,
                                  launch=launch)
+    d2q9 = _roofline_d2q9(max(args.steps // 20, 20), args.warmup, stream, torch, launch=launch)
+    fma64 = lbm.lbm_probe_fma_rate(lbm.LBM_FP64)
+    fma32 = lbm.lbm_probe_fma_rate(lbm.LBM_FP32DEV)
     e2e_s, h2d, d2h = _e2e(1, min(args.steps, 500), args.warmup, stream, torch)
     batch = _batch_run(min(args.steps, 100), stream, torch) if not args.no_batch else None
     adjoint = _adjoint_run(torch) if not args.no_adjoint else None
@@ -459,9 +531,12 @@ def run_ours(args):
                             "frac": round(BYTES_PER_CELL[1] * 8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e9 / peak, 4),
                             "steps": len(tsc), "status": int(chksc), "kernel": _kernel_name(blksc),
                             "launch": _launch_desc(blksc)},
+        "roofline_d2q9": d2q9,
         "fp64": {"value": round(cells / avg64 / 1e6, 1), "unit": "MLUPS", "steps": len(t64),
                  "achieved_GBps": round(ach64, 1), "frac": round(ach64 / peak, 4), "dtype": "f64",
-                 "status": int(chk64), "launch": _launch_desc(blk64)},
+                 "status": int(chk64), "launch": _launch_desc(blk64),
+                 "alu": _fp64_alu(cells, avg64, fma64)},
+        "fma_probe_gflops": {"fp64": round(fma64, 1), "fp32": round(fma32, 1)},
         "mixed_over_fp64": round(avg64 / avg32, 2),
         "batch": batch,
         "adjoint": adjoint,
@@ -475,6 +550,7 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline()
+        line["cpu_baseline"]["one_thread"] = _cpu_baseline_1thread()
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -530,6 +606,8 @@ def main():
                     help="fixed step launch instead of the autotuner: grid,BX,BY or tma,TY,STAGES,CTAS")
     ap.add_argument("--profile-step", action="store_true",
                     help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
+    ap.add_argument("--profile-prec", type=int, default=1, choices=[0, 1],
+                    help="precision of --profile-step: 1 FP32 deviation (default), 0 FP64")
     ap.add_argument("--profile-two-phase", action="store_true",
                     help="run only a 1024x1024 FP32 bubble (for ncu captures of the two-phase kernel)")
     args = ap.parse_args()

@@ -195,6 +195,16 @@ lbm_status lbm_step(lbm_t h, long n);
 lbm_status lbm_autotune(lbm_t h, int out_block[2]);
 
 /*
+ * FMA-rate probe (no counterpart in the paper: the arithmetic roofline of the FP64
+ * and FP32 forms on the current device).  Runs eight independent chains of fused
+ * multiply-adds per thread on every SM and returns the rate in GFLOP/s (2 flops per
+ * FMA) in *gflops.  Synchronous; allocates and frees its own scratch.
+ * precision: LBM_FP64 or LBM_FP32DEV.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA (text in
+ * lbm_last_error(NULL)).
+ */
+lbm_status lbm_probe_fma_rate(int precision, double *gflops);
+
+/*
  * Launch configuration of the single-phase step (no counterpart in the paper: a
  * choice of memory pipeline for the same arithmetic).  cfg[4]:
  *  {LBM_LAUNCH_GRID, block_x, block_y, 0}: one thread per node, block_x a multiple

@@ -116,6 +116,8 @@ def _extra_signatures(L):
     L.lbm_batch_destroy.restype = None
     L.lbm_autotune.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
     L.lbm_autotune.restype = C.c_int
+    L.lbm_probe_fma_rate.argtypes = [C.c_int, _dp]
+    L.lbm_probe_fma_rate.restype = C.c_int
     L.lbm_set_launch.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
     L.lbm_set_launch.restype = C.c_int
     L.lbm_launch_config.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
@@ -252,6 +254,13 @@ def lbm_last_error(h=None):
 
 def lbm_destroy(h):
     lib().lbm_destroy(h)
+
+
+def lbm_probe_fma_rate(precision):
+    """GFLOP/s of dependent-chain FMAs on the current device (LBM_FP64 or LBM_FP32DEV)."""
+    out = C.c_double(0.0)
+    _check(None, lib().lbm_probe_fma_rate(int(precision), C.byref(out)))
+    return out.value
 
 
 def lbm_set_launch(h, cfg):
