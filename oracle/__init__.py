@@ -22,8 +22,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_PRESSURE = 0, 1, 2, 3
-TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_PRESSURE, BC_SYMMETRY = 0, 1, 2, 3, 4
+TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW, TBC_SYMMETRY = 0, 1, 2, 3, 4
 
 
 class OrcParams(C.Structure):
@@ -184,14 +184,14 @@ class Oracle:
 
     def dist(self, which: str, post: bool = False):
         w = {"f": 0, "g": 1, "h": 2, "z": 3}[which]
-        q = 9 if w in (0, 3) else 5
+        q = 9 if w in (0, 3) or (w == 1 and int(self.p["thermal"]) == 9) else 5
         out = np.zeros((q, self.ny, self.nx))
         lib().orc_get_dist(self.h, w, int(post), _ptr(out))
         return out
 
     def set_dist(self, which: str, arr):
         w = {"f": 0, "g": 1, "h": 2, "z": 3}[which]
-        q = 9 if w in (0, 3) else 5
+        q = 9 if w in (0, 3) or (w == 1 and int(self.p["thermal"]) == 9) else 5
         a = _arr(arr, q * self.nx * self.ny)
         lib().orc_set_dist(self.h, w, _ptr(a))
 

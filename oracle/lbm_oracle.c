@@ -58,7 +58,7 @@ typedef struct {
   int nx, ny;
   int flow;        /* 0: no momentum LBE (velocity prescribed), 9: D2Q9 f      */
   int flow_op;     /* 0 BGK, 1 MRT                                             */
-  int thermal;     /* 0 none, 5: D2Q5 g                                        */
+  int thermal;     /* 0 none, 5: D2Q5 g, 9: D2Q9 g                            */
   int thermal_op;  /* 0 BGK, 1 MRT                                             */
   int phase;       /* 0 single phase, 5: two-phase, h on D2Q5 and z on D2Q9    */
   int z_op;        /* 0 BGK, 1 MRT for z                                       */
@@ -76,8 +76,8 @@ typedef struct {
   double beta_exp, T_ref, rho_ref;
 } orc_params;
 
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3 };
-enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3, BC_SYMMETRY = 4 };
+enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY = 4 };
 
 /* ------------------------------------------------------------------------- */
 /* Velocity sets                                                             */
@@ -235,8 +235,8 @@ void *orc_create(const orc_params *prm) {
 
   o->f = calloc(9 * N, sizeof(double)); o->fn = calloc(9 * N, sizeof(double));
   o->fpost = calloc(9 * N, sizeof(double));
-  o->g = calloc(5 * N, sizeof(double)); o->gn = calloc(5 * N, sizeof(double));
-  o->gpost = calloc(5 * N, sizeof(double));
+  o->g = calloc(9 * N, sizeof(double)); o->gn = calloc(9 * N, sizeof(double));
+  o->gpost = calloc(9 * N, sizeof(double));
   o->h = calloc(5 * N, sizeof(double)); o->hn = calloc(5 * N, sizeof(double));
   o->hpost = calloc(5 * N, sizeof(double));
   o->z = calloc(9 * N, sizeof(double)); o->zn = calloc(9 * N, sizeof(double));
@@ -319,9 +319,20 @@ static double fhat9(const orc_t *o, int i, double ux, double uy, double Fx, doub
   return W9[i] * (ax * Fx + ay * Fy);
 }
 /* linear g_eq, Eq. geq_geral (D2Q5) */
+static double geq5(const orc_t *o, int i, double T, double ux, double uy) __attribute__((unused));
 static double geq5(const orc_t *o, int i, double T, double ux, double uy) {
   double cu = o->c * (CX5[i] * ux + CY5[i] * uy);
   return W5[i] * T * (1.0 + cu / o->cs2);
+}
+/* The thermal lattice: D2Q5 (thermal = 5) or the paper's D2Q9 (thermal = 9). */
+static int QG(const orc_t *o) { return o->p.thermal == 9 ? 9 : 5; }
+static int cxg(const orc_t *o, int i) { return o->p.thermal == 9 ? CX9[i] : CX5[i]; }
+static int cyg(const orc_t *o, int i) { return o->p.thermal == 9 ? CY9[i] : CY5[i]; }
+static double wg(const orc_t *o, int i) { return o->p.thermal == 9 ? W9[i] : W5[i]; }
+/* linear g_eq, Eq. geq_geral, on the thermal lattice */
+static double geqT(const orc_t *o, int i, double T, double ux, double uy) {
+  double cu = o->c * (cxg(o, i) * ux + cyg(o, i) * uy);
+  return wg(o, i) * T * (1.0 + cu / o->cs2);
 }
 /* s_i(u), Eq. s_i_Liang (D2Q9) */
 static double s9(const orc_t *o, int i, double ux, double uy) {
@@ -340,22 +351,23 @@ static int opp5(int i) { static const int o5[5] = {0, 3, 4, 1, 2}; return o5[i];
 /* Which side a link leaving node (x,y) along (cx,cy) crosses, or -1 when it stays
    inside (after periodic wrap).  An axis is periodic for the momentum lattice when
    both its sides are BC_PERIODIC, for the thermal lattice when both are TBC_NONE.
-   A link leaving through a corner counts as crossing the y-side (reading R10). */
+   A link leaving through a corner counts as crossing the y-side (reading R10),
+   unless that y-side is a symmetry side: the mirror image of such a link also leaves
+   through the x-side, so the x-side rule applies (reading R31). */
 static int crossed_side(const orc_t *o, int thermal, int x, int y, int cx, int cy) {
   int tx = x + cx, ty = y + cy;
   int yper = thermal ? (o->tbc[2] == TBC_NONE && o->tbc[3] == TBC_NONE)
                      : (o->bc[2] == BC_PERIODIC && o->bc[3] == BC_PERIODIC);
   int xper = thermal ? (o->tbc[0] == TBC_NONE && o->tbc[1] == TBC_NONE)
                      : (o->bc[0] == BC_PERIODIC && o->bc[1] == BC_PERIODIC);
-  if (!yper) {
-    if (ty < 0) return 2;
-    if (ty >= o->p.ny) return 3;
+  int xside = -1, yside = -1;
+  if (!yper) yside = ty < 0 ? 2 : (ty >= o->p.ny ? 3 : -1);
+  if (!xper) xside = tx < 0 ? 0 : (tx >= o->p.nx ? 1 : -1);
+  if (yside >= 0 && xside >= 0) {
+    int ysym = thermal ? o->tbc[yside] == TBC_SYMMETRY : o->bc[yside] == BC_SYMMETRY;
+    return ysym ? xside : yside;
   }
-  if (!xper) {
-    if (tx < 0) return 0;
-    if (tx >= o->p.nx) return 1;
-  }
-  return -1;
+  return yside >= 0 ? yside : xside;
 }
 
 /* position of node (x,y) along a side: row index for x-sides, column for y-sides */
@@ -388,7 +400,7 @@ static void moments_single(orc_t *o) {
       /* lagged convective sink of the fuse problem: uses T of the previous step (R24) */
       if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->Tprev[n] - p->T_inf);
       double s = 0;
-      for (int i = 0; i < 5; i++) s += o->g[i * N + n];
+      for (int i = 0; i < QG(o); i++) s += o->g[i * N + n];
       o->T[n] = s + 0.5 * p->dt * qd;                          /* Eq. zero_moment_g */
     }
     if (p->flow) {
@@ -427,6 +439,11 @@ static void collide_single(orc_t *o) {
   /* thermal D2Q5 MRT rates, analogue of [Lambda_T]_dim (reading R4) */
   double wT = 1.0 / o->tauT;
   double LamT[5] = {0.0, wT, wT, 1.0 / dt, 1.0 / dt};
+  /* thermal D2Q9 MRT, Sec. 2.2: [Lambda_T] = diag(0, 1, 1, omega_T, 1, omega_T, 1, 1, 1)
+     with omega_T = 1/tau_T and the unit rates read as 1/dt (reading R3), on the
+     momentum transformation matrices */
+  double LamT9[9] = {0.0, 1.0 / dt, 1.0 / dt, wT, 1.0 / dt, wT, 1.0 / dt, 1.0 / dt, 1.0 / dt};
+  const int qg = QG(o);
   /* S_g prefactor uses tau_T (reading R1); literal print uses tau */
   double tau_sg = (p->literal & 1) ? o->tau : o->tauT;
 #pragma omp parallel for schedule(static)
@@ -461,12 +478,23 @@ static void collide_single(orc_t *o) {
     if (p->thermal) {
       double T = o->T[n];
       double qd = qdot_at(o, n);
-      double gv[5], ge[5];
-      for (int i = 0; i < 5; i++) { gv[i] = o->g[i * N + n]; ge[i] = geq5(o, i, T, ux, uy); }
+      double gv[9], ge[9];
+      for (int i = 0; i < qg; i++) { gv[i] = o->g[i * N + n]; ge[i] = geqT(o, i, T, ux, uy); }
       if (p->thermal_op == 0) {
         /* Eqs. eq_lattice_boltzmann_BGK_T and forcing_term_g */
-        for (int i = 0; i < 5; i++)
-          o->gpost[i * N + n] = gv[i] - dt / o->tauT * (gv[i] - ge[i]) + dt * (1.0 - dt / (2.0 * tau_sg)) * W5[i] * qd;
+        for (int i = 0; i < qg; i++)
+          o->gpost[i * N + n] = gv[i] - dt / o->tauT * (gv[i] - ge[i]) + dt * (1.0 - dt / (2.0 * tau_sg)) * wg(o, i) * qd;
+      } else if (qg == 9) {
+        /* Eq. colisao_MRT for g with [Lambda_T] and the source Delta t (I - dt Lambda/2) M (w qdot) */
+        double sv[9], m[9], me[9], Sm[9], ms[9], gs[9];
+        for (int i = 0; i < 9; i++) sv[i] = W9[i] * qd;
+        matvec(9, o->Md, gv, m);
+        matvec(9, o->Md, ge, me);
+        matvec(9, o->Md, sv, Sm);
+        for (int k = 0; k < 9; k++)
+          ms[k] = m[k] - dt * LamT9[k] * (m[k] - me[k]) + dt * (1.0 - 0.5 * dt * LamT9[k]) * Sm[k];
+        matvec(9, o->Mdinv, ms, gs);
+        for (int i = 0; i < 9; i++) o->gpost[i * N + n] = gs[i];
       } else {
         /* D2Q5 MRT analogue of Eq. colisao_MRT with source w_i qdot (reading R4) */
         double sv[5], m[5], me[5], Sm[5], ms[5], gs[5];
@@ -519,8 +547,8 @@ static double flow_boundary_value(const orc_t *o, int side, int x, int y, int i)
   }
 }
 
-/* Thermal (D2Q5): value entering node opposite to outgoing i through `side`;
-   OUTFLOW is resolved after streaming. */
+/* Thermal: value entering node opposite to outgoing i through `side`;
+   OUTFLOW and SYMMETRY are resolved after streaming. */
 static double thermal_boundary_value(const orc_t *o, int side, int x, int y, int i) {
   int n = idx(o, x, y);
   int N = o->N;
@@ -529,20 +557,63 @@ static double thermal_boundary_value(const orc_t *o, int side, int x, int y, int
   int len = side_len(o, side);
   switch (o->tbc[side]) {
     case TBC_FLUX: {
-      /* Eq. BB_T, lambda for the single unknown of D2Q5 = 1 (reading R5), rho = rho0 */
+      /* Eq. BB_T, rho = rho0; lambda_i = 2 w_i / (c_s^2 / c^2) = 6 w_i on D2Q9 (4/6 axial,
+         1/6 diagonal), 1 for the single unknown of D2Q5 (reading R5) */
       double qflux = o->bct[side][a];
-      return gs + 1.0 * (o->p.dt / o->p.dx) * qflux / (o->p.rho0 * o->p.cp);
+      double lam = QG(o) == 9 ? 6.0 * W9[i] : 1.0;
+      return gs + lam * (o->p.dt / o->p.dx) * qflux / (o->p.rho0 * o->p.cp);
     }
     case TBC_TEMP: {
       /* Eq. anti_BB_T with the side's velocity (zero at a wall) */
       double Tw = o->bct[side][a];
       double uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
-      double cu = o->c * (CX5[i] * uwx + CY5[i] * uwy);
+      double cu = o->c * (cxg(o, i) * uwx + cyg(o, i) * uwy);
       double uu = uwx * uwx + uwy * uwy;
-      return -gs + 2.0 * W5[i] * Tw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
+      return -gs + 2.0 * wg(o, i) * Tw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
     }
     default:
       return gs; /* OUTFLOW placeholder, overwritten after streaming */
+  }
+}
+
+/* mirror of direction q across a side normal to x (axis 0) or y (axis 1) */
+static int mirror_dir(int q9, int axis, int q) {
+  static const int MX9[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7}, MY9[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+  static const int MX5[5] = {0, 3, 2, 1, 4}, MY5[5] = {0, 1, 4, 3, 2};
+  if (q9) return axis == 0 ? MX9[q] : MY9[q];
+  return axis == 0 ? MX5[q] : MY5[q];
+}
+
+static void symmetry_gather(orc_t *o, int thermal) {
+  const orc_params *p = &o->p;
+  int N = o->N, nx = p->nx, ny = p->ny;
+  int q9 = thermal ? QG(o) == 9 : 1;
+  int nq = q9 ? 9 : 5;
+  double *dst = thermal ? o->gn : o->fn;
+  const double *post = thermal ? o->gpost : o->fpost;
+  for (int side = 0; side < 4; side++) {
+    int kind = thermal ? o->tbc[side] : o->bc[side];
+    if (kind != (thermal ? TBC_SYMMETRY : BC_SYMMETRY)) continue;
+    int len = side_len(o, side);
+    /* the tangential axis wraps where that axis is periodic for this lattice */
+    int tper = side < 2 ? (thermal ? (o->tbc[2] == TBC_NONE && o->tbc[3] == TBC_NONE)
+                                   : (o->bc[2] == BC_PERIODIC && o->bc[3] == BC_PERIODIC))
+                        : (thermal ? (o->tbc[0] == TBC_NONE && o->tbc[1] == TBC_NONE)
+                                   : (o->bc[0] == BC_PERIODIC && o->bc[1] == BC_PERIODIC));
+    for (int a = 0; a < len; a++) {
+      int x = side == 0 ? 0 : side == 1 ? nx - 1 : a;
+      int y = side == 2 ? 0 : side == 3 ? ny - 1 : a;
+      for (int j = 1; j < nq; j++) {
+        int cx = q9 ? CX9[j] : CX5[j], cy = q9 ? CY9[j] : CY5[j];
+        if (crossed_side(o, thermal, x, y, -cx, -cy) != side) continue;  /* j does not enter here */
+        int i = mirror_dir(q9, side < 2 ? 0 : 1, j);
+        int sx = x, sy = y;
+        if (side < 2) sy = y - cy; else sx = x - cx;                     /* x - c_{j,tan} dt */
+        if (side < 2) { if (sy < 0 || sy >= ny) sy = tper ? (sy + ny) % ny : y; }
+        else { if (sx < 0 || sx >= nx) sx = tper ? (sx + nx) % nx : x; }
+        dst[j * N + idx(o, x, y)] = post[i * N + idx(o, sx, sy)];
+      }
+    }
   }
 }
 
@@ -558,23 +629,30 @@ static void stream_single(orc_t *o) {
           if (side < 0) {
             int tx = (x + CX9[i] + nx) % nx, ty = (y + CY9[i] + ny) % ny;  /* periodic wrap */
             o->fn[i * N + idx(o, tx, ty)] = o->fpost[i * N + n];
-          } else {
+          } else if (o->bc[side] != BC_SYMMETRY) {
             o->fn[opp9(i) * N + n] = flow_boundary_value(o, side, x, y, i);
           }
         }
       }
       if (p->thermal) {
-        for (int i = 0; i < 5; i++) {
-          int side = crossed_side(o, 1, x, y, CX5[i], CY5[i]);
+        for (int i = 0; i < QG(o); i++) {
+          int side = crossed_side(o, 1, x, y, cxg(o, i), cyg(o, i));
           if (side < 0) {
-            int tx = (x + CX5[i] + nx) % nx, ty = (y + CY5[i] + ny) % ny;
+            int tx = (x + cxg(o, i) + nx) % nx, ty = (y + cyg(o, i) + ny) % ny;
             o->gn[i * N + idx(o, tx, ty)] = o->gpost[i * N + n];
-          } else {
-            o->gn[opp5(i) * N + n] = thermal_boundary_value(o, side, x, y, i);
+          } else if (o->tbc[side] != TBC_SYMMETRY) {
+            int oi = QG(o) == 9 ? opp9(i) : opp5(i);
+            o->gn[oi * N + n] = thermal_boundary_value(o, side, x, y, i);
           }
         }
       }
     }
+  /* symmetry sides, Eq. simetria: the population j entering node x through the
+     side is the post-collision population i = mirror(j) (same tangential, opposite
+     normal velocity) of the node x - c_{j,tan} dt (wrapped where the tangential axis
+     is periodic; where it still falls outside, the node's own f_i*, reading R31) */
+  symmetry_gather(o, 0);
+  if (p->thermal) symmetry_gather(o, 1);
   /* thermal outlet: first-order extrapolation of the unknown populations,
      g_i(x_b, t+dt) = g_i(x_{b-1}, t+dt) (Sec. 2.2; reading R9) */
   if (p->thermal) {
@@ -582,12 +660,16 @@ static void stream_single(orc_t *o) {
       if (o->tbc[side] != TBC_OUTFLOW) continue;
       int len = side_len(o, side);
       for (int a = 0; a < len; a++) {
-        int x, y, xi, yi, q;
-        if (side == 0) { x = 0; y = a; xi = 1; yi = a; q = 1; }
-        else if (side == 1) { x = nx - 1; y = a; xi = nx - 2; yi = a; q = 3; }
-        else if (side == 2) { x = a; y = 0; xi = a; yi = 1; q = 2; }
-        else { x = a; y = ny - 1; xi = a; yi = ny - 2; q = 4; }
-        o->gn[q * N + idx(o, x, y)] = o->gn[q * N + idx(o, xi, yi)];
+        int x, y, xi, yi;
+        if (side == 0) { x = 0; y = a; xi = 1; yi = a; }
+        else if (side == 1) { x = nx - 1; y = a; xi = nx - 2; yi = a; }
+        else if (side == 2) { x = a; y = 0; xi = a; yi = 1; }
+        else { x = a; y = ny - 1; xi = a; yi = ny - 2; }
+        for (int q = 1; q < QG(o); q++) {
+          /* the unknowns: links that enter (x, y) through this side */
+          if (crossed_side(o, 1, x, y, -cxg(o, q), -cyg(o, q)) != side) continue;
+          o->gn[q * N + idx(o, x, y)] = o->gn[q * N + idx(o, xi, yi)];
+        }
       }
     }
   }
@@ -765,7 +847,7 @@ void orc_init(void *handle, const double *a, const double *ux, const double *uy,
     if (p->thermal) {
       double T = b ? b[n] : p->T0;
       o->T[n] = T; o->Tprev[n] = T;
-      for (int i = 0; i < 5; i++) o->g[i * N + n] = geq5(o, i, T, u0, v0);
+      for (int i = 0; i < QG(o); i++) o->g[i * N + n] = geqT(o, i, T, u0, v0);
     }
   }
   o->steps = 0;
@@ -845,7 +927,7 @@ void orc_moments(void *handle, double *rho, double *ux, double *uy, double *T, d
    1 post-collision values of the last step (valid after >= 1 step). */
 void orc_get_dist(void *handle, int which, int post, double *out) {
   orc_t *o = (orc_t *)handle;
-  int q = (which == 0 || which == 3) ? 9 : 5;
+  int q = (which == 0 || which == 3 || (which == 1 && o->p.thermal == 9)) ? 9 : 5;
   double *src;
   if (which == 0) src = post ? o->fpost : o->f;
   else if (which == 1) src = post ? o->gpost : o->g;
@@ -857,7 +939,7 @@ void orc_get_dist(void *handle, int which, int post, double *out) {
 /* Overwrite the current pre-collision distributions (for planted-mistake tests). */
 void orc_set_dist(void *handle, int which, const double *in) {
   orc_t *o = (orc_t *)handle;
-  int q = (which == 0 || which == 3) ? 9 : 5;
+  int q = (which == 0 || which == 3 || (which == 1 && o->p.thermal == 9)) ? 9 : 5;
   double *dst = which == 0 ? o->f : which == 1 ? o->g : which == 2 ? o->h : o->z;
   memcpy(dst, in, sizeof(double) * q * o->N);
 }

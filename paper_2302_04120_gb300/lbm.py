@@ -22,8 +22,8 @@ LBM_ERR_CUDA, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = -4, -5, -6, -7
 LBM_NONE, LBM_D2Q5, LBM_D2Q9 = 0, 5, 9
 LBM_BGK, LBM_MRT = 0, 1
 LBM_FP64, LBM_FP32DEV = 0, 1
-LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE = 0, 1, 2, 3
-LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW = 0, 1, 2, 3
+LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE, LBM_BC_SYMMETRY = 0, 1, 2, 3, 4
+LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW, LBM_TBC_SYMMETRY = 0, 1, 2, 3, 4
 LBM_RHO, LBM_UX, LBM_UY, LBM_T, LBM_P, LBM_PHI = 1, 2, 4, 8, 16, 32
 LBM_LAUNCH_GRID, LBM_LAUNCH_TMA = 0, 1
 _MOMENT_BITS = [("rho", 1), ("ux", 2), ("uy", 4), ("T", 8), ("p", 16), ("phi", 32)]

@@ -21,8 +21,8 @@ from __future__ import annotations
 import numpy as np
 
 # boundary kinds (same numbering as include/lbm.h and the oracle)
-BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_PRESSURE = 0, 1, 2, 3
-TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_PRESSURE, BC_SYMMETRY = 0, 1, 2, 3, 4
+TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW, TBC_SYMMETRY = 0, 1, 2, 3, 4
 
 # Water of the forced-convection workload (rho, c_p, k) and Pr = 7.
 WATER = dict(rho0=1000.0, cp=4180.0, k=0.6)
@@ -97,6 +97,66 @@ def channel(nx=2048, ny=256, steps=50000, Re=100.0, Pr=7.0, qflux=4e4, T_in=300.
     init = dict(a=None, ux=ux0, uy=np.zeros((ny, nx)), b=np.full((ny, nx), T_in))
     return dict(name=f"channel_d2q9mrt_d2q5_{nx}x{ny}", params=params, bcs=bcs, init=init,
                 q3=q3, steps=steps, u_m=u_m, H=H, nu=nu, alpha=alpha, qflux=qflux, T_in=T_in)
+
+
+# ---------------------------------------------------------------------------
+# The paper's heated-channel cases (Sec. 4.2): D2Q9 BGK flow + D2Q9 MRT thermal
+# ---------------------------------------------------------------------------
+# Water at 301 K (property table of Sec. 4.2).
+WATER_301K = dict(rho0=996.279, nu=8.382e-7, k=0.611, cp=4180.333)
+
+
+def heated_channel(case=2, nx=None, ny=None, steps=0, half=True, flow_op=0, thermal=9, thermal_op=1,
+                   q_mean=4e4, dq=4e4, L_h=1e-3, T_in=300.0, H=5e-4, L=1e-2):
+    """Forced convection between two plates heated with the same flux (Sec. 4.2).
+
+    case 1: hydrodynamically and thermally developed inlet, u(y) = 6 u_m (y/H - y^2/H^2)
+            with u_m = 0.2 m/s and the developed T(y) of Eq. temp_prof; oscillating flux
+            q''(x) = q_mean + dq sign(sin(2 pi x / L_h)) (Eq. var_flux); dx = 5e-6, dt = 2e-6.
+    case 2: developing flow, uniform inlet u_m = 0.02 m/s and T_in; constant flux q_mean;
+            dx = 2.5e-6, dt = 6.25e-7.
+    case 3: case 2 with the oscillating flux.
+    half=True simulates the lower half (y in [0, H/2]) with a symmetry top, as the paper
+    does; half=False the full channel with two heated walls.  nx, ny default to the
+    paper's L/dx and (H/2)/dx (H/dx for the full channel); smaller values give a
+    shorter channel with the same dx, dt and inlet data.  Initial state: the inlet
+    fields everywhere.
+    """
+    w = WATER_301K
+    rho0, nu, k, cp = w["rho0"], w["nu"], w["k"], w["cp"]
+    dx, dt, u_m = (5e-6, 2e-6, 0.2) if case == 1 else (2.5e-6, 6.25e-7, 0.02)
+    if nx is None:
+        nx = int(round(L / dx))
+    if ny is None:
+        ny = int(round((H / 2 if half else H) / dx))
+    y = node_y(ny, dx)                        # from the bottom plate
+    s = y / H
+    if case == 1:
+        uin = 6.0 * u_m * (s - s * s)
+        Tin = T_in + q_mean * H / k * (-s ** 4 + 2 * s ** 3 - s + 0.243)   # Eq. temp_prof
+    else:
+        uin = np.full(ny, u_m)
+        Tin = np.full(ny, T_in)
+    x = node_x(nx, dx)
+    if case in (1, 3):
+        qw = q_mean + dq * np.sign(np.sin(2.0 * np.pi * x / L_h))          # Eq. var_flux
+    else:
+        qw = np.full(nx, q_mean)
+    params = dict(nx=nx, ny=ny, flow=9, flow_op=flow_op, thermal=thermal, thermal_op=thermal_op, phase=0,
+                  dx=dx, dt=dt, rho0=rho0, nu=nu, cp=cp, k=k, T0=T_in)
+    bcs = [
+        (0, BC_VELOCITY, np.concatenate([uin, np.zeros(ny)]), rho0, TBC_TEMP, Tin.copy()),
+        (1, BC_PRESSURE, None, rho0, TBC_OUTFLOW, None),
+        (2, BC_WALL, None, rho0, TBC_FLUX, qw.copy()),
+    ]
+    if half:
+        bcs.append((3, BC_SYMMETRY, None, rho0, TBC_SYMMETRY, None))
+    else:
+        bcs.append((3, BC_WALL, None, rho0, TBC_FLUX, qw.copy()))
+    init = dict(a=None, ux=np.tile(uin[:, None], (1, nx)), uy=np.zeros((ny, nx)),
+                b=np.tile(Tin[:, None], (1, nx)))
+    return dict(name=f"heated_channel_case{case}_{nx}x{ny}{'_half' if half else ''}", params=params, bcs=bcs,
+                init=init, q3=None, steps=steps, u_m=u_m, H=H, qwall=qw, T_in=T_in, k=k, dx=dx)
 
 
 # ---------------------------------------------------------------------------

@@ -231,6 +231,132 @@ def test_heat_flux_wall_linear_profile(op, ny):
 
 
 # ---------------------------------------------------------------------------
+# D2Q9 thermal lattice (Sec. 2.2: the paper's thermal scheme) and symmetry sides
+# ---------------------------------------------------------------------------
+def _rod9(nx, ny, dx, dt, k, rho, cp, op, bcs, q3=None, thermal=9, u=(0.0, 0.0)):
+    o = oracle.Oracle(dict(nx=nx, ny=ny, flow=0, thermal=thermal, thermal_op=op, dx=dx, dt=dt,
+                           rho0=rho, cp=cp, k=k, T0=300.0, u_prescribed=u))
+    for side, tkind, tw in bcs:
+        ln = ny if side < 2 else nx
+        o.set_bc(side, oracle.BC_PERIODIC, uw=np.concatenate([np.full(ln, u[0]), np.full(ln, u[1])]),
+                 tkind=tkind, tw=np.full(ln, tw))
+    if q3 is not None:
+        o.set_source(q3=np.full(nx * ny, q3))
+    o.init()
+    return o
+
+
+def test_thermal_d2q9_equilibrium_moments():
+    """Eq. geq_geral on D2Q9: sum g_eq = T, sum c g_eq = T u (closed form)."""
+    rng = np.random.default_rng(3)
+    nx, ny, dx, dt = 5, 4, 1e-5, 1e-6
+    o = oracle.Oracle(dict(nx=nx, ny=ny, flow=0, thermal=9, thermal_op=1, dx=dx, dt=dt, rho0=1000.0,
+                           cp=4180.0, k=0.6, T0=300.0))
+    T = 300 + rng.standard_normal((ny, nx))
+    ux, uy = 0.1 * rng.standard_normal((ny, nx)), 0.1 * rng.standard_normal((ny, nx))
+    o.init(ux=ux, uy=uy, b=T)
+    g = o.dist("g")
+    c = dx / dt
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])[:, None, None] * c
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])[:, None, None] * c
+    assert np.max(np.abs(g.sum(0) - T)) < 1e-12 * 300
+    assert np.max(np.abs((cx * g).sum(0) - T * ux)) < 1e-12 * 300 * c
+    assert np.max(np.abs((cy * g).sum(0) - T * uy)) < 1e-12 * 300 * c
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_thermal_d2q9_single_row_reduces_to_d1q3(op):
+    """On one periodic row with u = 0, D2Q9 and D2Q5 aggregate to the same D1Q3
+    (weights 4/6, 1/6, 1/6; the D2Q9 heat-flux lambdas 4/6 + 1/6 + 1/6 = 1): the
+    source-heated rod between an anti-bounce-back wall and a flux wall agrees with
+    the D2Q5 run to rounding, for BGK and for the MRT forms."""
+    L, k, rho, cp, q3, nx = 0.08, 150.0, 2700.0, 900.0, 1e7, 10
+    dx = L / nx
+    dt = 0.3 * dx * dx / (3 * k / (rho * cp))
+    bcs = [(0, oracle.TBC_TEMP, 300.0), (1, oracle.TBC_FLUX, 2e5)]
+    a = _rod9(nx, 1, dx, dt, k, rho, cp, op, bcs, q3=q3, thermal=9)
+    b = _rod9(nx, 1, dx, dt, k, rho, cp, op, bcs, q3=q3, thermal=5)
+    a.step(3000)
+    b.step(3000)
+    Ta, Tb = a.moments()["T"][0], b.moments()["T"][0]
+    assert np.max(np.abs(Ta - Tb)) <= 1e-12 * np.max(np.abs(Tb - 300))
+
+
+@pytest.mark.parametrize("nx,tau_bar", [(8, 0.8), (12, 1.4)])
+def test_thermal_d2q9_bgk_heat_source_exact(nx, tau_bar):
+    """The closed form of the D1Q3 rod with a source (see the D2Q5 pin) holds for
+    D2Q9 thermal BGK on one periodic row."""
+    L, k, rho, cp, q3 = 0.08, 150.0, 2700.0, 900.0, 1e7
+    dx = L / nx
+    dt = (tau_bar - 0.5) * dx * dx / (3 * k / (rho * cp))
+    o = _rod9(nx, 1, dx, dt, k, rho, cp, 0, [(0, oracle.TBC_TEMP, 300.0), (1, oracle.TBC_TEMP, 300.0)], q3=q3)
+    T = _steady(o, lambda s: s.moments()["T"][0], offset=300.0)
+    x = (np.arange(nx) + 0.5) * dx
+    ex = 300 + q3 * x * (L - x) / (2 * k) + q3 * dx * dx / k * (16 * (tau_bar - 0.5) ** 2 - 3) / 24
+    assert np.max(np.abs(T - ex)) / np.max(ex - 300) < 1e-11
+
+
+@pytest.mark.parametrize("op,ny", [(0, 3), (1, 4)])
+def test_thermal_d2q9_flux_wall_linear_profile(op, ny):
+    """Eq. BB_T with lambda_i = 6 w_i on D2Q9 across a 2D strip (periodic along the
+    wall): steady T = T_w + q'' x / k exactly; a wrong lambda or thermal rate changes
+    the slope."""
+    k, rho, cp, nx, dx, qf = 0.6, 1000.0, 4180.0, 16, 1e-4, 5e3
+    dt = 0.4 * dx * dx / (3 * k / (rho * cp))
+    o = _rod9(nx, ny, dx, dt, k, rho, cp, op, [(0, oracle.TBC_TEMP, 300.0), (1, oracle.TBC_FLUX, qf)])
+    T = _steady(o, lambda s: s.moments()["T"][0], offset=300.0)
+    x = (np.arange(nx) + 0.5) * dx
+    ex = 300 + qf * x / k
+    assert np.max(np.abs(T - ex)) / np.max(ex - 300) < 1e-10
+
+
+def test_thermal_d2q9_mrt_equals_bgk_at_unit_rates():
+    """With tau_T = dt every rate of [Lambda_T] is 1/dt, so the MRT of Sec. 2.2 is
+    the BGK operator (no source): a 2D advected hot spot agrees to rounding."""
+    nx, ny, dx, rho, cp = 12, 10, 1e-5, 1000.0, 4180.0
+    dt = 1e-6
+    cs2 = (dx / dt) ** 2 / 3
+    k = rho * cp * 0.5 * dt * cs2             # alpha = (tau_T - dt/2) c_s^2 with tau_T = dt
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    T0 = 300 + np.exp(-((X - 6e-5) ** 2 + (Y - 5e-5) ** 2) / (2 * (2e-5) ** 2))
+    out = []
+    for op in (0, 1):
+        o = oracle.Oracle(dict(nx=nx, ny=ny, flow=0, thermal=9, thermal_op=op, dx=dx, dt=dt, rho0=rho,
+                               cp=cp, k=k, T0=300.0, u_prescribed=(0.3, -0.2)))
+        o.init(ux=np.full((ny, nx), 0.3), uy=np.full((ny, nx), -0.2), b=T0)
+        o.step(60)
+        out.append(o.moments()["T"])
+    assert np.max(np.abs(out[0] - out[1])) <= 1e-12 * 300
+
+
+@pytest.mark.parametrize("thermal,thermal_op", [(9, 1), (5, 1), (9, 0)])
+def test_symmetry_half_channel_equals_full_channel(thermal, thermal_op):
+    """Eq. simetria: a heated channel simulated on its lower half with a symmetry top
+    reproduces the lower half of the full channel with two identical heated walls
+    (developing flow, oscillating flux, outlet corners included) to rounding."""
+    nx, nyh, steps = 40, 6, 300
+    full = wl.heated_channel(3, nx=nx, ny=2 * nyh, half=False, thermal=thermal, thermal_op=thermal_op)
+    half = wl.heated_channel(3, nx=nx, ny=nyh, half=True, thermal=thermal, thermal_op=thermal_op)
+    # the full channel's inlet data are the mirrored half's
+    mo = []
+    for w in (full, half):
+        o = oracle.Oracle(w["params"])
+        for bc in w["bcs"]:
+            o.set_bc(*bc)
+        o.init(**w["init"])
+        o.step(steps)
+        mo.append(o.moments())
+    mf, mh = mo
+    sp = np.max(np.hypot(mh["ux"], mh["uy"]))
+    assert np.max(np.abs(mf["ux"][:nyh] - mh["ux"])) <= 1e-12 * sp
+    assert np.max(np.abs(mf["uy"][:nyh] - mh["uy"])) <= 1e-12 * sp
+    dT = np.max(np.abs(mh["T"] - 300.0))
+    assert np.max(np.abs(mf["T"][:nyh] - mh["T"])) <= 1e-11 * dT
+    # and the full solution is mirror-symmetric (the half problem is the right one)
+    assert np.max(np.abs(mf["ux"][::-1][:nyh] - mh["ux"])) <= 1e-12 * sp
+
+
+# ---------------------------------------------------------------------------
 # The paper's own problems
 # ---------------------------------------------------------------------------
 def _paper():
