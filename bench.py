@@ -417,7 +417,7 @@ def _traffic_from_profile(kernel_tag):
     if not os.path.exists(path):
         return None
     h = hashlib.sha1()
-    for f in ("step_sp.cu", "step_tma.cu", "sp_device.cuh", "lattice.cuh", "lbm_internal.cuh"):
+    for f in ("sp_kernels.cuh", "tma_kernels.cuh", "sp_device.cuh", "lattice.cuh", "lbm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2302_04120_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     cur = h.hexdigest()[:12]

@@ -59,14 +59,18 @@ enum {
   LBM_BC_PERIODIC = 0, /* Sec. 2.1: f_i(x_b) = f_i*(x_b + L - c_i dt); both sides of an axis */
   LBM_BC_WALL = 1,     /* half-way bounce-back with wall velocity, Eq. BB_vel               */
   LBM_BC_VELOCITY = 2, /* velocity inlet, Eq. BB_vel with u_w = inlet velocity              */
-  LBM_BC_PRESSURE = 3  /* outlet, Eq. anti_BB_vel; u_w = u(x_b) + (u(x_b) - u(x_b-1))/2      */
+  LBM_BC_PRESSURE = 3, /* outlet, Eq. anti_BB_vel; u_w = u(x_b) + (u(x_b) - u(x_b-1))/2      */
+  LBM_BC_SYMMETRY = 4  /* symmetry plane, Eq. simetria: mirrored populations of the
+                          tangential neighbour; at a corner with another side the link
+                          that crosses both takes that side's rule                       */
 };
 /* thermal boundary kinds, per side (LBM_TBC_NONE = periodic for the thermal lattice) */
 enum {
   LBM_TBC_NONE = 0,
   LBM_TBC_FLUX = 1,    /* prescribed heat flux into the fluid, Eq. BB_T                     */
   LBM_TBC_TEMP = 2,    /* prescribed temperature, Eq. anti_BB_T                             */
-  LBM_TBC_OUTFLOW = 3  /* first-order extrapolation of the unknown populations (Sec. 2.2)   */
+  LBM_TBC_OUTFLOW = 3, /* first-order extrapolation of the unknown populations (Sec. 2.2)   */
+  LBM_TBC_SYMMETRY = 4 /* symmetry plane for the thermal lattice, Eq. simetria              */
 };
 /* sides */
 enum { LBM_SIDE_XMIN = 0, LBM_SIDE_XMAX = 1, LBM_SIDE_YMIN = 2, LBM_SIDE_YMAX = 3 };
@@ -81,11 +85,14 @@ enum { LBM_RHO = 1, LBM_UX = 2, LBM_UY = 4, LBM_T = 8, LBM_P = 16, LBM_PHI = 32 
  *             [M]_dim of Eq. M_matrix_dim and the dimensional rates of Sec. 3:
  *             omega_nu = 1/tau, omega_q = (3/dt)(2/dt - omega_nu)/(3/dt - omega_nu),
  *             omega_e = omega_e_dt/dt, omega_eps = omega_eps_dt/dt).
- *  thermal    LBM_NONE or LBM_D2Q5 (double-distribution thermal LBE, Sec. 2.2, on D2Q5:
- *             w = 1/3, 1/6 x4, c_s^2 = c^2/3; linear g_eq of Eq. geq_geral).
- *  thermal_op LBM_BGK (Eq. eq_lattice_boltzmann_BGK_T) or LBM_MRT (D2Q5 analogue of
- *             [Lambda_T]_dim: moments (1, c_x, c_y, 5|c|^2-4c^2, c_x^2-c_y^2) relaxed at
- *             (0, 1/tau_T, 1/tau_T, 1/dt, 1/dt)).
+ *  thermal    LBM_NONE, LBM_D2Q5 or LBM_D2Q9 (double-distribution thermal LBE, Sec. 2.2,
+ *             linear g_eq of Eq. geq_geral; D2Q5: w = 1/3, 1/6 x4, c_s^2 = c^2/3; D2Q9, the
+ *             paper's lattice, needs flow = D2Q9).
+ *  thermal_op LBM_BGK (Eq. eq_lattice_boltzmann_BGK_T) or LBM_MRT: on D2Q9 the thermal MRT
+ *             of Sec. 2.2, [Lambda_T] = diag(0, 1, 1, 1/tau_T, 1, 1/tau_T, 1, 1, 1) with
+ *             the unit rates taken as 1/dt, on the momentum matrices; on D2Q5 its analogue,
+ *             moments (1, c_x, c_y, 5|c|^2-4c^2, c_x^2-c_y^2) relaxed at (0, 1/tau_T, 1/tau_T,
+ *             1/dt, 1/dt).  Both with the source dt (I - dt Lambda/2) M (w qdot).
  *  phase      LBM_NONE (single phase) or LBM_D2Q5 (two-phase model of Sec. 2.3: Allen-Cahn
  *             h_i on D2Q5, pressure-evolution z_i on D2Q9 with operator z_op).
  *  nu_rule    two-phase viscosity: 0 linear in phi, 1 nu = zeta/rho with zeta linear in phi.
@@ -108,7 +115,7 @@ enum { LBM_RHO = 1, LBM_UX = 2, LBM_UY = 4, LBM_T = 8, LBM_P = 16, LBM_PHI = 32 
  *  gravity, beta_exp, T_ref, rho_ref: Boussinesq two-way coupling of App. D, Eq. buoyancy_force:
  *             F_b = -rho_ref beta_exp (T - T_ref) g added to the momentum force with the
  *             node's temperature of the same step (beta_exp = 0 disables it).  Needs
- *             flow = D2Q9 and thermal = D2Q5.
+ *             flow = D2Q9 and a thermal LBE.
  */
 typedef struct {
   int flow, flow_op, thermal, thermal_op, phase, z_op, nu_rule, literal, precision;
@@ -145,8 +152,11 @@ lbm_status lbm_create(const lbm_params *p, void *stream, lbm_t *out);
  *        thermal anti-bounce-back; NULL = zero.
  *  tkind thermal rule (LBM_TBC_*); tw host array of len doubles: q'' [W m^-2, positive
  *        into the fluid] for FLUX, T_w [K] for TEMP, ignored otherwise; NULL = zero.
+ *        FLUX on D2Q9 weights the unknowns with lambda_i = 6 w_i (4/6 axial, 1/6
+ *        diagonal), on D2Q5 the single unknown with 1.
  * Both sides of an axis must be periodic together, for each lattice.  A link that
- * leaves through a corner takes the y-side rule.  The arrays are copied before the
+ * leaves through a corner takes the y-side rule, unless the y-side is a symmetry
+ * side: then the other side's rule.  The arrays are copied before the
  * call returns (through pinned staging, without synchronising the stream); the new
  * values apply to steps enqueued after the call.
  * Errors: LBM_ERR_ARG (side, kind, pairing), LBM_ERR_CUDA.

@@ -97,6 +97,13 @@ extern "C" void lbm_params_default(lbm_params *p) {
 
 static int two_phase(const lbm_t h) { return h->p.phase != LBM_NONE; }
 
+// Thermal kernel kind of a parameter set: lattice (D2Q5 / D2Q9) x operator.
+static int th_kind(const lbm_params &p) {
+  if (!p.thermal) return lbmk::TH_NONE;
+  if (p.thermal == LBM_D2Q9) return p.thermal_op == LBM_MRT ? lbmk::TH_MRT9 : lbmk::TH_BGK9;
+  return p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK;
+}
+
 static int axis_periodic(const lbm_t h, int axis, int thermal) {
   int a = axis == 0 ? 0 : 2, b = a + 1;
   if (thermal) return h->tbc[a] == LBM_TBC_NONE && h->tbc[b] == LBM_TBC_NONE;
@@ -121,6 +128,9 @@ static SpParams sp_params(const lbm_t h, int from_buf) {
   P.xper = axis_periodic(h, 0, 0); P.yper = axis_periodic(h, 1, 0);
   P.txper = axis_periodic(h, 0, 1); P.typer = axis_periodic(h, 1, 1);
   P.gbase = p.flow == LBM_D2Q9 ? 9 : 0;
+  P.qg = p.thermal ? p.thermal : 0;
+  P.fysym = (h->bc[2] == LBM_BC_SYMMETRY ? 1 : 0) | (h->bc[3] == LBM_BC_SYMMETRY ? 2 : 0);
+  P.tysym = (h->tbc[2] == LBM_TBC_SYMMETRY ? 1 : 0) | (h->tbc[3] == LBM_TBC_SYMMETRY ? 2 : 0);
   for (int s = 0; s < 4; s++) {
     P.side[s].kind = h->bc[s];
     P.side[s].tkind = h->tbc[s];
@@ -214,7 +224,10 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   if (!(p.dx > 0) || !(p.dt > 0)) return fail(NULL, LBM_ERR_ARG, "dx and dt must be positive");
   if (p.precision != LBM_FP64 && p.precision != LBM_FP32DEV) return fail(NULL, LBM_ERR_ARG, "precision");
   if (p.flow != LBM_D2Q9 && p.flow != LBM_NONE) return fail(NULL, LBM_ERR_ARG, "flow lattice must be D2Q9 or NONE");
-  if (p.thermal != LBM_D2Q5 && p.thermal != LBM_NONE) return fail(NULL, LBM_ERR_ARG, "thermal lattice must be D2Q5 or NONE");
+  if (p.thermal != LBM_D2Q5 && p.thermal != LBM_D2Q9 && p.thermal != LBM_NONE)
+    return fail(NULL, LBM_ERR_ARG, "thermal lattice must be D2Q5, D2Q9 or NONE");
+  if (p.thermal == LBM_D2Q9 && p.flow != LBM_D2Q9)
+    return fail(NULL, LBM_ERR_ARG, "a D2Q9 thermal LBE needs the D2Q9 momentum LBE");
   if (p.phase != LBM_D2Q5 && p.phase != LBM_NONE) return fail(NULL, LBM_ERR_ARG, "phase lattice must be D2Q5 or NONE");
   if (p.flow_op != LBM_BGK && p.flow_op != LBM_MRT) return fail(NULL, LBM_ERR_ARG, "flow_op");
   if (p.thermal_op != LBM_BGK && p.thermal_op != LBM_MRT) return fail(NULL, LBM_ERR_ARG, "thermal_op");
@@ -228,8 +241,8 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   } else if (!(p.rho0 > 0)) {
     return fail(NULL, LBM_ERR_ARG, "rho0 must be positive");
   }
-  if (p.beta_exp != 0.0 && (p.flow != LBM_D2Q9 || p.thermal != LBM_D2Q5 || p.phase != LBM_NONE))
-    return fail(NULL, LBM_ERR_ARG, "buoyancy needs a single-phase D2Q9 flow with a D2Q5 thermal LBE");
+  if (p.beta_exp != 0.0 && (p.flow != LBM_D2Q9 || p.thermal == LBM_NONE || p.phase != LBM_NONE))
+    return fail(NULL, LBM_ERR_ARG, "buoyancy needs a single-phase D2Q9 flow with a thermal LBE");
   if (!(p.omega_e_dt > 0 && p.omega_e_dt < 2) || !(p.omega_eps_dt > 0 && p.omega_eps_dt < 2))
     return fail(NULL, LBM_ERR_ARG, "free MRT rates times dt must lie in (0, 2)");
 
@@ -260,7 +273,7 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   h->pitch = (p.nx + 31) / 32 * 32;
   h->plane = (long long)h->pitch * p.ny;
   if (p.phase) h->nq = 9 + 5 + 2;   // z, h, (phi u)_prev
-  else h->nq = (p.flow ? 9 : 0) + (p.thermal ? 5 : 0);
+  else h->nq = (p.flow ? 9 : 0) + (p.thermal ? p.thermal : 0);
   h->block = dim3(64, 4);
   for (int s = 0; s < 4; s++) {
     h->bc[s] = LBM_BC_PERIODIC;
@@ -305,7 +318,7 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   h->tmap_ty = 0;
   if (!p.phase && (p.flow || p.thermal)) {
     int fk = p.flow ? (p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
-    int tk = p.thermal ? (p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
+    int tk = th_kind(p);
     lbmk::sp_tma_prepare(p.precision, fk, tk);  // failure leaves only the grid launch usable
     cudaGetLastError();
   }
@@ -346,8 +359,8 @@ extern "C" lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, 
                                  const double *tw) {
   if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
   if (side < 0 || side > 3) return fail(h, LBM_ERR_ARG, "side must be 0..3");
-  if (kind < LBM_BC_PERIODIC || kind > LBM_BC_PRESSURE) return fail(h, LBM_ERR_ARG, "kind");
-  if (tkind < LBM_TBC_NONE || tkind > LBM_TBC_OUTFLOW) return fail(h, LBM_ERR_ARG, "tkind");
+  if (kind < LBM_BC_PERIODIC || kind > LBM_BC_SYMMETRY) return fail(h, LBM_ERR_ARG, "kind");
+  if (tkind < LBM_TBC_NONE || tkind > LBM_TBC_SYMMETRY) return fail(h, LBM_ERR_ARG, "tkind");
   if (two_phase(h) && (kind != LBM_BC_PERIODIC || tkind != LBM_TBC_NONE))
     return fail(h, LBM_ERR_ARG, "two-phase solves support periodic sides only");
   const int len = side < 2 ? h->p.ny : h->p.nx;
@@ -466,7 +479,7 @@ extern "C" lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux
   } else {
     SpParams P = sp_params(h, 1);
     int flow = h->p.flow ? (h->p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
-    int th = h->p.thermal ? (h->p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
+    int th = th_kind(h->p);
     e = lbmk::sp_init(P, h->p.precision, flow, th, d_in[0], d_in[1], d_in[2], d_in[3], h->block, h->stream);
   }
   if (tmp) {
@@ -484,7 +497,7 @@ extern "C" lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux
 
 static void sp_kinds(const lbm_t h, int *flow, int *th) {
   *flow = h->p.flow ? (h->p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
-  *th = h->p.thermal ? (h->p.thermal_op == LBM_MRT ? lbmk::TH_MRT : lbmk::TH_BGK) : lbmk::TH_NONE;
+  *th = th_kind(h->p);
 }
 
 static int *step_flag(lbm_t h) { return (int *)(h->d_out4 + 4); }
@@ -940,6 +953,9 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
   const lbm_params &p = h->p;
   if (p.phase || p.flow != LBM_D2Q9 || p.flow_op != LBM_MRT || p.thermal != LBM_D2Q5 || p.thermal_op != LBM_MRT)
     return fail(h, LBM_ERR_ARG, "the adjoint covers single-phase D2Q9 MRT + D2Q5 MRT solves");
+  for (int s = 0; s < 4; s++)
+    if (h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY)
+      return fail(h, LBM_ERR_ARG, "the adjoint does not cover symmetry sides");
   if (p.precision != LBM_FP64) return fail(h, LBM_ERR_ARG, "the adjoint runs in FP64");
   if (p.beta_exp != 0.0) return fail(h, LBM_ERR_ARG, "the adjoint does not cover the buoyancy coupling");
   if (p.nx < 2) return fail(h, LBM_ERR_ARG, "nx must be >= 2 (loss on the x+ column)");

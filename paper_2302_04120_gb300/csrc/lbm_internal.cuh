@@ -33,6 +33,9 @@ struct SpParams {
   int xper, yper;         // momentum lattice periodic along x / y
   int txper, typer;       // thermal lattice periodic along x / y
   int gbase;              // plane index of g_0 (9 with a momentum LBE, else 0)
+  int qg;                 // thermal populations (5 or 9; 0 without a thermal LBE)
+  int fysym, tysym;       // y-sides that are symmetry planes (bit 0: y = 0, bit 1: y = ny - 1),
+                          // momentum and thermal lattice
   DevSide side[4];
   // SI constants
   double c, cs2, dt, dx;
@@ -74,7 +77,12 @@ enum { FLOW_NONE = 0, FLOW_BGK = 1, FLOW_MRT = 2 };
 __host__ __device__ inline int frame_nodes(int nx, int ny) {
   return (ny >= 2 ? 2 : 1) * nx + (nx >= 2 ? 2 : 1) * (ny > 2 ? ny - 2 : 0);
 }
-enum { TH_NONE = 0, TH_BGK = 1, TH_MRT = 2 };
+enum { TH_NONE = 0, TH_BGK = 1, TH_MRT = 2, TH_BGK9 = 3, TH_MRT9 = 4 };
+// populations of the thermal lattice of a TH kind: D2Q5, or the paper's D2Q9
+template <int TH>
+struct ThLat {
+  static constexpr int Q = (TH == TH_BGK9 || TH == TH_MRT9) ? 9 : 5;
+};
 
 // Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);

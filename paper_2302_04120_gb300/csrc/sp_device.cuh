@@ -9,8 +9,8 @@
 
 namespace lbmk {
 
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3 };
-enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3, BC_SYMMETRY = 4 };
+enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY = 4 };
 
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -24,18 +24,37 @@ __device__ __forceinline__ bool on_side(const SpParams &P, int s, int i, int j) 
 }
 
 // Which side the link arriving at (i, j) along c = (cx, cy) comes through (source
-// node (i - cx, j - cy) outside the domain), or -1.  y-sides win at corners.
-__device__ __forceinline__ int entry_side(int i, int j, int cx, int cy, int nx, int ny, int xper, int yper) {
-  int si = i - cx, sj = j - cy;
-  if (!yper) {
-    if (sj < 0) return 2;
-    if (sj >= ny) return 3;
+// node (i - cx, j - cy) outside the domain), or -1.  A link through a corner takes
+// the y-side, unless that y-side is a symmetry side (ysym: bit 0 for y = 0, bit 1
+// for y = ny - 1): the mirror image of the link also comes through the x-side, whose
+// rule then applies.
+__device__ __forceinline__ int entry_side(int i, int j, int cx, int cy, int nx, int ny, int xper, int yper,
+                                          int ysym = 0) {
+  const int si = i - cx, sj = j - cy;
+  const int ys = yper ? -1 : (sj < 0 ? 2 : (sj >= ny ? 3 : -1));
+  const int xs = xper ? -1 : (si < 0 ? 0 : (si >= nx ? 1 : -1));
+  if (ys >= 0 && xs >= 0) return ((ysym >> (ys - 2)) & 1) ? xs : ys;
+  return ys >= 0 ? ys : xs;
+}
+
+// Source of a link entering node (i, j) through symmetry side `side` (Eq. simetria):
+// population mirror(q) of the tangential neighbour (i, j) - c_{q,tan} dt, wrapped
+// where the tangential axis is periodic, else the node itself where the neighbour
+// falls outside.  Returns the element offset of that value.
+template <int Q>
+__device__ __forceinline__ long long symmetry_source(const SpParams &P, int side, int q, int i, int j, int tper) {
+  const int cx = Q == 9 ? cx9(q) : cx5(q), cy = Q == 9 ? cy9(q) : cy5(q);
+  int si = i, sj = j, qm;
+  if (side >= 2) {
+    qm = Q == 9 ? my9(q) : my5(q);
+    si = i - cx;
+    if (si < 0 || si >= P.nx) si = tper ? wrap(si, P.nx) : i;
+  } else {
+    qm = Q == 9 ? mx9(q) : mx5(q);
+    sj = j - cy;
+    if (sj < 0 || sj >= P.ny) sj = tper ? wrap(sj, P.ny) : j;
   }
-  if (!xper) {
-    if (si < 0) return 0;
-    if (si >= nx) return 1;
-  }
-  return -1;
+  return qm * P.plane + (long long)sj * P.pitch + si;
 }
 
 // Pre-collision velocity of time t at node n rebuilt from its post-collision
@@ -62,8 +81,7 @@ __device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, i
     // buoyancy of T(t) = T0 + sum g* - dt qdot / 2 at this node
     const S *gs = src + (long long)P.gbase * P.plane;
     R sg = (R)0;
-#pragma unroll
-    for (int q = 0; q < 5; q++) sg += (R)gs[q * P.plane + n];
+    for (int q = 0; q < P.qg; q++) sg += (R)gs[q * P.plane + n];
     const R qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
     const R dT = (K<R>(P).T0 - K<R>(P).T_ref) + sg - (R)0.5 * K<R>(P).dt * qd;
     Fx += K<R>(P).bgx * dT;
@@ -91,14 +109,20 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
   // 1. gather, branch-free so that all nine loads are in flight together: the
   //    streaming source (periodic wrap included), or for a link entering through a
   //    side the outgoing population o = opp(q) of this node
+  //    (a symmetry side gives the mirrored population of the tangential neighbour)
   int side[9];
+  bool sym[9];
   R raw[9];
 #pragma unroll
   for (int q = 0; q < 9; q++) {
-    side[q] = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper);
-    const long long at = side[q] < 0
-                             ? q * P.plane + (long long)wrap(j - cy9(q), P.ny) * P.pitch + wrap(i - cx9(q), P.nx)
-                             : opp9(q) * P.plane + n;
+    side[q] = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper, P.fysym);
+    sym[q] = false;
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+      if (side[q] == s) sym[q] = P.side[s].kind == BC_SYMMETRY;
+    long long at = side[q] < 0 ? q * P.plane + (long long)wrap(j - cy9(q), P.ny) * P.pitch + wrap(i - cx9(q), P.nx)
+                               : opp9(q) * P.plane + n;
+    if (sym[q]) at = symmetry_source<9>(P, side[q], q, i, j, side[q] >= 2 ? P.xper : P.yper);
     raw[q] = (R)src[at];
   }
   // 2. wall / inlet velocities of the sides this node lies on, loaded up front
@@ -130,7 +154,7 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
   // 4. boundary links (side values picked with compile-time side indices)
 #pragma unroll
   for (int q = 0; q < 9; q++) {
-    if (side[q] < 0) {
+    if (side[q] < 0 || sym[q]) {
       f[q] = raw[q];
       continue;
     }
@@ -160,42 +184,53 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
   }
 }
 
-// Pull of the D2Q5 thermal populations at node (i, j) with boundary links.
-template <typename S, typename R>
-__device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, int j, bool interior, R g[5]) {
+// Pull of the thermal populations (QT = 5: D2Q5, 9: D2Q9) at node (i, j) with
+// boundary links.
+template <typename S, typename R, int QT = 5>
+__device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, int j, bool interior, R g[QT]) {
   const long long n = (long long)j * P.pitch + i;
   const S *gsrc = src + (long long)P.gbase * P.plane;
   if (interior) {
 #pragma unroll
-    for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n - (long long)cy5(q) * P.pitch - cx5(q)];
+    for (int q = 0; q < QT; q++) g[q] = (R)gsrc[q * P.plane + n - (long long)cyT(QT, q) * P.pitch - cxT(QT, q)];
     return;
   }
   if (P.local) {
 #pragma unroll
-    for (int q = 0; q < 5; q++) g[q] = (R)gsrc[q * P.plane + n];
+    for (int q = 0; q < QT; q++) g[q] = (R)gsrc[q * P.plane + n];
     return;
   }
   const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
-  // 1. gather (branch-free, all five loads in flight together)
-  int side[5], tk[5];
-  R raw[5];
+  // 1. gather (branch-free, all loads in flight together)
+  int side[QT], tk[QT];
+  R raw[QT];
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
-    side[q] = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
+  for (int q = 0; q < QT; q++) {
+    side[q] = entry_side(i, j, cxT(QT, q), cyT(QT, q), P.nx, P.ny, P.txper, P.typer, P.tysym);
     tk[q] = TBC_NONE;
 #pragma unroll
     for (int s = 0; s < 4; s++)
       if (side[q] == s) tk[q] = P.side[s].tkind;
     long long at;
     if (side[q] < 0) {
-      at = q * P.plane + (long long)wrap(j - cy5(q), P.ny) * P.pitch + wrap(i - cx5(q), P.nx);
+      at = q * P.plane + (long long)wrap(j - cyT(QT, q), P.ny) * P.pitch + wrap(i - cxT(QT, q), P.nx);
+    } else if (tk[q] == TBC_SYMMETRY) {
+      at = symmetry_source<QT>(P, side[q], q, i, j, side[q] >= 2 ? P.txper : P.typer);
     } else if (tk[q] == TBC_OUTFLOW) {
-      // g_q(x_b, t+dt) = g_q(x_b-1, t+dt) = g_q*(x_b-1 - c_q dt, t) (Sec. 2.2, outlet)
+      // g_q(x_b, t+dt) = g_q(x_b-1, t+dt): the inner node's pull of q (Sec. 2.2, outlet);
+      // where that pull itself crosses a symmetry side (the outlet's corner with a
+      // symmetry plane) it is that side's mirrored value
       const int ii = i + (side[q] == 0) - (side[q] == 1), jj = j + (side[q] == 2) - (side[q] == 3);
-      const int si = min(max(ii - cx5(q), 0), P.nx - 1), sj = min(max(jj - cy5(q), 0), P.ny - 1);
-      at = q * P.plane + (long long)sj * P.pitch + si;
+      const int si = ii - cxT(QT, q), sj = jj - cyT(QT, q);
+      const int cs = entry_side(ii, jj, cxT(QT, q), cyT(QT, q), P.nx, P.ny, P.txper, P.typer, P.tysym);
+      bool csym = false;
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+        if (cs == s) csym = P.side[s].tkind == TBC_SYMMETRY;
+      at = q * P.plane + (long long)min(max(sj, 0), P.ny - 1) * P.pitch + min(max(si, 0), P.nx - 1);
+      if (csym) at = symmetry_source<QT>(P, cs, q, ii, jj, cs >= 2 ? P.txper : P.typer);
     } else {
-      at = opp5(q) * P.plane + n;
+      at = oppT(QT, q) * P.plane + n;
     }
     raw[q] = (R)gsrc[at];
   }
@@ -212,12 +247,12 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
   }
   // 3. boundary links
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
-    if (side[q] < 0 || tk[q] == TBC_OUTFLOW) {
+  for (int q = 0; q < QT; q++) {
+    if (side[q] < 0 || tk[q] == TBC_OUTFLOW || tk[q] == TBC_SYMMETRY) {
       g[q] = raw[q];
       continue;
     }
-    const int o = opp5(q);
+    const int o = oppT(QT, q);
     const R go = raw[q];
     R Tw = 0, ux = 0, uy = 0;
 #pragma unroll
@@ -230,11 +265,14 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
     }
     if (tk[q] == TBC_TEMP) {
       // Eq. anti_BB_T in deviation form
-      R cu = c * ((R)cx5(o) * ux + (R)cy5(o) * uy);
+      R cu = c * ((R)cxT(QT, o) * ux + (R)cyT(QT, o) * uy);
       R uu = ux * ux + uy * uy;
-      g[q] = -go + (R)2 * w5<R>(o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - K<R>(P).T0);
+      g[q] = -go + (R)2 * wT<R>(QT, o) * (Tw * ((R)1 + (R)0.5 * cu * cu * inv_cs2 * inv_cs2 - (R)0.5 * uu * inv_cs2) - K<R>(P).T0);
+    } else if (QT == 9) {
+      // Eq. BB_T with lambda_o = 6 w_o on D2Q9 (4/6 axial, 1/6 diagonal; FLUX, zero flux = adiabatic)
+      g[q] = go + (R)6 * w9<R>(o) * K<R>(P).flux_coef * Tw;
     } else {
-      // Eq. BB_T with lambda = 1 for the single unknown (FLUX; zero flux = adiabatic)
+      // Eq. BB_T with lambda = 1 for the single D2Q5 unknown (FLUX; zero flux = adiabatic)
       g[q] = go + K<R>(P).flux_coef * Tw;
     }
   }
@@ -262,10 +300,11 @@ __device__ __forceinline__ void load_sources(const SpParams &P, long long n, Mac
 }
 
 template <typename R, int FLOW, int TH>
-__device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R g[5], Macro<R> &m) {
+__device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R *g, Macro<R> &m) {
   if (TH != TH_NONE) {
     // Eq. zero_moment_g
-    m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
+    if (ThLat<TH>::Q == 9) m.sumg = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    else m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
     m.T = K<R>(P).T0 + m.sumg + (R)0.5 * K<R>(P).dt * m.qd;
     if (FLOW != FLOW_NONE && P.buoy) {
       // Boussinesq buoyancy with this step's temperature (Eq. buoyancy_force)
@@ -368,24 +407,76 @@ __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &
   f[8] -= dg + p34 - p56 - a8;
 }
 
-template <typename R>
-__device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &m, R g[5]) {
+// Thermal BGK with source (Eqs. eq_lattice_boltzmann_BGK_T, forcing_term_g,
+// geq_geral) on the thermal lattice QT.
+template <typename R, int QT = 5>
+__device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &m, R *g) {
   const R c = K<R>(P).c, inv_cs2 = (R)3 / (c * c);
   const R om = K<R>(P).omegaT;
   const R src = K<R>(P).tsrc_fac * K<R>(P).dt * m.qd;
   const R dT = m.T - K<R>(P).T0;
   R geq_sum = 0, s_sum = 0;
 #pragma unroll
-  for (int q = 1; q < 5; q++) {
-    const R cu = c * ((R)cx5(q) * m.ux + (R)cy5(q) * m.uy);
-    const R geq = w5<R>(q) * (dT + m.T * cu * inv_cs2);  // Eq. geq_geral minus w T0
-    const R sq = w5<R>(q) * src;                         // Eq. forcing_term_g
+  for (int q = 1; q < QT; q++) {
+    const R cu = c * ((R)cxT(QT, q) * m.ux + (R)cyT(QT, q) * m.uy);
+    const R geq = wT<R>(QT, q) * (dT + m.T * cu * inv_cs2);  // Eq. geq_geral minus w T0
+    const R sq = wT<R>(QT, q) * src;                         // Eq. forcing_term_g
     geq_sum += geq;
     s_sum += sq;
     g[q] = g[q] - om * (g[q] - geq) + sq;
   }
   // rest population from the remainders: sum g_eq = T - T0, sum S = source, exactly
   g[0] = g[0] - om * (g[0] - (dT - geq_sum)) + (src - s_sum);
+}
+
+// Thermal MRT on D2Q9 (Sec. 2.2): the momentum transformation matrices and
+// [Lambda_T] = diag(0, 1, 1, omega_T, 1, omega_T, 1, 1, 1), the unit rates read as
+// 1/dt; source Delta t (I - dt Lambda/2) M (w qdot).  Lattice-scaled moments of the
+// deviations g - w T0; equilibrium moments of g_eq - w T0 from Eq. geq_geral:
+// (T - T0, -2 (T - T0), T - T0, T u_x/c, -T u_x/c, T u_y/c, -T u_y/c, 0, 0).
+template <typename R>
+__device__ __forceinline__ void collide_mrt9T(const SpParams &P, const Macro<R> &m, R g[9]) {
+  const R ic = (R)1 / K<R>(P).c, dt = K<R>(P).dt;
+  const R dT = m.T - K<R>(P).T0;
+  const R sT = K<R>(P).omegaT;  // dt / tau_T
+  const R qd = m.qd;
+  const R s14 = (g[1] + g[2]) + (g[3] + g[4]);
+  const R s58 = (g[5] + g[6]) + (g[7] + g[8]);
+  const R m_e = -(R)4 * g[0] - s14 + (R)2 * s58;
+  const R m_ep = (R)4 * g[0] - (R)2 * s14 + s58;
+  const R d58 = g[5] - g[7], d68 = g[6] - g[8];
+  const R m_jx = (g[1] - g[3]) + d58 - d68;
+  const R m_jy = (g[2] - g[4]) + d58 + d68;
+  const R m_qx = (R)2 * (g[3] - g[1]) + d58 - d68;
+  const R m_qy = (R)2 * (g[4] - g[2]) + d58 + d68;
+  const R m_xx = (g[1] + g[3]) - (g[2] + g[4]);
+  const R m_xy = (g[5] + g[7]) - (g[6] + g[8]);
+  const R Tux = m.T * m.ux * ic, Tuy = m.T * m.uy * ic;
+  // Delta m_k = dt Lambda_k (m_k - m_k^eq) - dt (1 - dt Lambda_k / 2) S_k, S = qdot (1, -2, 1, 0, ...)
+  const R d0 = -dt * qd;                                       // Lambda_0 = 0
+  const R d_e = (m_e + (R)2 * dT) + dt * qd;                   // rate 1/dt: -(dt/2)(-2 qdot)
+  const R d_ep = (m_ep - dT) - (R)0.5 * dt * qd;
+  const R d_jx = sT * (m_jx - Tux), d_jy = sT * (m_jy - Tuy);  // rate omega_T
+  const R d_qx = m_qx + Tux, d_qy = m_qy + Tuy;                // rate 1/dt, eq -T u/c
+  const R d_xx = m_xx, d_xy = m_xy;                            // rate 1/dt, eq 0
+  // back to populations: M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  const R a0 = d0 * ((R)1 / (R)9);
+  const R a1 = d_e * ((R)1 / (R)36), a2 = d_ep * ((R)1 / (R)36);
+  const R a3 = d_jx * ((R)1 / (R)6), a4 = d_qx * ((R)1 / (R)12);
+  const R a5 = d_jy * ((R)1 / (R)6), a6 = d_qy * ((R)1 / (R)12);
+  const R a7 = d_xx * (R)0.25, a8 = d_xy * (R)0.25;
+  const R ax = a0 - a1 - (R)2 * a2;  // common to i = 1..4
+  const R dg = a0 + (R)2 * a1 + a2;  // common to i = 5..8
+  g[0] -= a0 + (R)4 * (a2 - a1);
+  g[1] -= ax + a3 - (R)2 * a4 + a7;
+  g[2] -= ax + a5 - (R)2 * a6 - a7;
+  g[3] -= ax - a3 + (R)2 * a4 + a7;
+  g[4] -= ax - a5 + (R)2 * a6 - a7;
+  const R p34 = a3 + a4, p56 = a5 + a6;
+  g[5] -= dg + p34 + p56 + a8;
+  g[6] -= dg - p34 + p56 - a8;
+  g[7] -= dg - p34 - p56 + a8;
+  g[8] -= dg + p34 - p56 - a8;
 }
 
 template <typename R>
@@ -413,11 +504,13 @@ __device__ __forceinline__ void collide_mrt5(const SpParams &P, const Macro<R> &
 }
 
 template <typename R, int FLOW, int TH>
-__device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R f[9], R g[5]) {
+__device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R f[9], R *g) {
   if (FLOW == FLOW_BGK) collide_bgk9<R>(P, m, f);
   if (FLOW == FLOW_MRT) collide_mrt9<R>(P, m, f);
-  if (TH == TH_BGK) collide_bgk5<R>(P, m, g);
+  if (TH == TH_BGK) collide_bgk5<R, 5>(P, m, g);
   if (TH == TH_MRT) collide_mrt5<R>(P, m, g);
+  if (TH == TH_BGK9) collide_bgk5<R, 9>(P, m, g);
+  if (TH == TH_MRT9) collide_mrt9T<R>(P, m, g);
 }
 
 // Dispatch of a launcher body over the supported (precision, momentum operator,
@@ -433,6 +526,10 @@ __device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R 
       else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(0, FLOW_MRT, TH_MRT); }     \
       else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(0, FLOW_NONE, TH_BGK); }   \
       else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(0, FLOW_NONE, TH_MRT); }   \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK9) { CALL(0, FLOW_BGK, TH_BGK9); }   \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT9) { CALL(0, FLOW_BGK, TH_MRT9); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK9) { CALL(0, FLOW_MRT, TH_BGK9); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT9) { CALL(0, FLOW_MRT, TH_MRT9); }   \
       else return cudaErrorInvalidValue;                                              \
     } else {                                                                          \
       if (FLOW_ == FLOW_BGK && TH_ == TH_NONE) { CALL(1, FLOW_BGK, TH_NONE); }        \
@@ -443,6 +540,10 @@ __device__ __forceinline__ void collide(const SpParams &P, const Macro<R> &m, R 
       else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT) { CALL(1, FLOW_MRT, TH_MRT); }     \
       else if (FLOW_ == FLOW_NONE && TH_ == TH_BGK) { CALL(1, FLOW_NONE, TH_BGK); }   \
       else if (FLOW_ == FLOW_NONE && TH_ == TH_MRT) { CALL(1, FLOW_NONE, TH_MRT); }   \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_BGK9) { CALL(1, FLOW_BGK, TH_BGK9); }   \
+      else if (FLOW_ == FLOW_BGK && TH_ == TH_MRT9) { CALL(1, FLOW_BGK, TH_MRT9); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_BGK9) { CALL(1, FLOW_MRT, TH_BGK9); }   \
+      else if (FLOW_ == FLOW_MRT && TH_ == TH_MRT9) { CALL(1, FLOW_MRT, TH_MRT9); }   \
       else return cudaErrorInvalidValue;                                              \
     }                                                                                 \
   } while (0)

@@ -419,7 +419,10 @@ class Solver:
             w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
             out["f"] = a[0:9] + w9[:, None, None] * p.get("rho0", 1000.0)
             k = 9
-        if p.get("thermal", 0):
+        if p.get("thermal", 0) == 9:
+            w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+            out["g"] = a[k:k + 9] + w9[:, None, None] * p.get("T0", 300.0)
+        elif p.get("thermal", 0):
             w5 = np.array([1 / 3] + [1 / 6] * 4)
             out["g"] = a[k:k + 5] + w5[:, None, None] * p.get("T0", 300.0)
         return out

@@ -107,7 +107,7 @@ WATER_301K = dict(rho0=996.279, nu=8.382e-7, k=0.611, cp=4180.333)
 
 
 def heated_channel(case=2, nx=None, ny=None, steps=0, half=True, flow_op=0, thermal=9, thermal_op=1,
-                   q_mean=4e4, dq=4e4, L_h=1e-3, T_in=300.0, H=5e-4, L=1e-2):
+                   q_mean=4e4, dq=4e4, L_h=1e-3, T_in=300.0, H=5e-4, L=1e-2, u_m=None):
     """Forced convection between two plates heated with the same flux (Sec. 4.2).
 
     case 1: hydrodynamically and thermally developed inlet, u(y) = 6 u_m (y/H - y^2/H^2)
@@ -119,12 +119,13 @@ def heated_channel(case=2, nx=None, ny=None, steps=0, half=True, flow_op=0, ther
     half=True simulates the lower half (y in [0, H/2]) with a symmetry top, as the paper
     does; half=False the full channel with two heated walls.  nx, ny default to the
     paper's L/dx and (H/2)/dx (H/dx for the full channel); smaller values give a
-    shorter channel with the same dx, dt and inlet data.  Initial state: the inlet
-    fields everywhere.
+    shorter channel with the same dx, dt and inlet data; u_m overrides the case's mean
+    inlet speed.  Initial state: the inlet fields everywhere.
     """
     w = WATER_301K
     rho0, nu, k, cp = w["rho0"], w["nu"], w["k"], w["cp"]
-    dx, dt, u_m = (5e-6, 2e-6, 0.2) if case == 1 else (2.5e-6, 6.25e-7, 0.02)
+    dx, dt, um = (5e-6, 2e-6, 0.2) if case == 1 else (2.5e-6, 6.25e-7, 0.02)
+    u_m = um if u_m is None else u_m
     if nx is None:
         nx = int(round(L / dx))
     if ny is None:
