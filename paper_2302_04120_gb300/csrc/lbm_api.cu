@@ -131,6 +131,8 @@ static SpParams sp_params(const lbm_t h, int from_buf) {
   P.qg = p.thermal ? p.thermal : 0;
   P.fysym = (h->bc[2] == LBM_BC_SYMMETRY ? 1 : 0) | (h->bc[3] == LBM_BC_SYMMETRY ? 2 : 0);
   P.tysym = (h->tbc[2] == LBM_TBC_SYMMETRY ? 1 : 0) | (h->tbc[3] == LBM_TBC_SYMMETRY ? 2 : 0);
+  P.sym = 0;
+  for (int s = 0; s < 4; s++) P.sym |= h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY;
   for (int s = 0; s < 4; s++) {
     P.side[s].kind = h->bc[s];
     P.side[s].tkind = h->tbc[s];

@@ -36,6 +36,8 @@ struct SpParams {
   int qg;                 // thermal populations (5 or 9; 0 without a thermal LBE)
   int fysym, tysym;       // y-sides that are symmetry planes (bit 0: y = 0, bit 1: y = ny - 1),
                           // momentum and thermal lattice
+  int sym;                // any side of either lattice is a symmetry plane (selects the
+                          // kernels compiled with the symmetry rules)
   DevSide side[4];
   // SI constants
   double c, cs2, dt, dx;

@@ -91,8 +91,10 @@ __device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, i
   uy = (jy - (R)0.5 * K<R>(P).dt * Fy) / rho;
 }
 
-// Pull of all momentum populations at node (i, j), with boundary links.
-template <typename S, typename R>
+// Pull of all momentum populations at node (i, j), with boundary links.  SYM: the
+// solve has symmetry sides (compiled separately, so that solves without them run the
+// shorter boundary code).
+template <typename S, typename R, bool SYM = false>
 __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, int j, bool interior, R f[9]) {
   const long long n = (long long)j * P.pitch + i;
   if (interior) {
@@ -115,11 +117,13 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
   R raw[9];
 #pragma unroll
   for (int q = 0; q < 9; q++) {
-    side[q] = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper, P.fysym);
+    side[q] = entry_side(i, j, cx9(q), cy9(q), P.nx, P.ny, P.xper, P.yper, SYM ? P.fysym : 0);
     sym[q] = false;
+    if (SYM) {
 #pragma unroll
-    for (int s = 0; s < 4; s++)
-      if (side[q] == s) sym[q] = P.side[s].kind == BC_SYMMETRY;
+      for (int s = 0; s < 4; s++)
+        if (side[q] == s) sym[q] = P.side[s].kind == BC_SYMMETRY;
+    }
     long long at = side[q] < 0 ? q * P.plane + (long long)wrap(j - cy9(q), P.ny) * P.pitch + wrap(i - cx9(q), P.nx)
                                : opp9(q) * P.plane + n;
     if (sym[q]) at = symmetry_source<9>(P, side[q], q, i, j, side[q] >= 2 ? P.xper : P.yper);
@@ -186,7 +190,7 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
 
 // Pull of the thermal populations (QT = 5: D2Q5, 9: D2Q9) at node (i, j) with
 // boundary links.
-template <typename S, typename R, int QT = 5>
+template <typename S, typename R, int QT = 5, bool SYM = false>
 __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, int j, bool interior, R g[QT]) {
   const long long n = (long long)j * P.pitch + i;
   const S *gsrc = src + (long long)P.gbase * P.plane;
@@ -206,7 +210,7 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
   R raw[QT];
 #pragma unroll
   for (int q = 0; q < QT; q++) {
-    side[q] = entry_side(i, j, cxT(QT, q), cyT(QT, q), P.nx, P.ny, P.txper, P.typer, P.tysym);
+    side[q] = entry_side(i, j, cxT(QT, q), cyT(QT, q), P.nx, P.ny, P.txper, P.typer, SYM ? P.tysym : 0);
     tk[q] = TBC_NONE;
 #pragma unroll
     for (int s = 0; s < 4; s++)
@@ -214,7 +218,7 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
     long long at;
     if (side[q] < 0) {
       at = q * P.plane + (long long)wrap(j - cyT(QT, q), P.ny) * P.pitch + wrap(i - cxT(QT, q), P.nx);
-    } else if (tk[q] == TBC_SYMMETRY) {
+    } else if (SYM && tk[q] == TBC_SYMMETRY) {
       at = symmetry_source<QT>(P, side[q], q, i, j, side[q] >= 2 ? P.txper : P.typer);
     } else if (tk[q] == TBC_OUTFLOW) {
       // g_q(x_b, t+dt) = g_q(x_b-1, t+dt): the inner node's pull of q (Sec. 2.2, outlet);
@@ -222,13 +226,15 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
       // symmetry plane) it is that side's mirrored value
       const int ii = i + (side[q] == 0) - (side[q] == 1), jj = j + (side[q] == 2) - (side[q] == 3);
       const int si = ii - cxT(QT, q), sj = jj - cyT(QT, q);
-      const int cs = entry_side(ii, jj, cxT(QT, q), cyT(QT, q), P.nx, P.ny, P.txper, P.typer, P.tysym);
-      bool csym = false;
-#pragma unroll
-      for (int s = 0; s < 4; s++)
-        if (cs == s) csym = P.side[s].tkind == TBC_SYMMETRY;
       at = q * P.plane + (long long)min(max(sj, 0), P.ny - 1) * P.pitch + min(max(si, 0), P.nx - 1);
-      if (csym) at = symmetry_source<QT>(P, cs, q, ii, jj, cs >= 2 ? P.txper : P.typer);
+      if (SYM) {
+        const int cs = entry_side(ii, jj, cxT(QT, q), cyT(QT, q), P.nx, P.ny, P.txper, P.typer, P.tysym);
+        bool csym = false;
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+          if (cs == s) csym = P.side[s].tkind == TBC_SYMMETRY;
+        if (csym) at = symmetry_source<QT>(P, cs, q, ii, jj, cs >= 2 ? P.txper : P.typer);
+      }
     } else {
       at = oppT(QT, q) * P.plane + n;
     }
@@ -248,7 +254,7 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
   // 3. boundary links
 #pragma unroll
   for (int q = 0; q < QT; q++) {
-    if (side[q] < 0 || tk[q] == TBC_OUTFLOW || tk[q] == TBC_SYMMETRY) {
+    if (side[q] < 0 || tk[q] == TBC_OUTFLOW || (SYM && tk[q] == TBC_SYMMETRY)) {
       g[q] = raw[q];
       continue;
     }

@@ -17,7 +17,7 @@ namespace lbmk {
 // ----------------------------------------------------------------------------
 // One node: pull with boundary links, moments, collision, store.  INNER: the
 // caller guarantees an interior node of a non-local step (no boundary code).
-template <int PREC, int FLOW, int TH, bool INNER = false>
+template <int PREC, int FLOW, int TH, bool INNER = false, bool SYM = false>
 __device__ __forceinline__ void step_node(const SpParams &P, int i, int j) {
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
@@ -26,8 +26,8 @@ __device__ __forceinline__ void step_node(const SpParams &P, int i, int j) {
   S *dst = (S *)P.dst;
   const bool interior = INNER || (!P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1));
   R f[9], g[9];
-  if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
-  if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q>(P, src, i, j, interior, g);
+  if (FLOW != FLOW_NONE) pull_f<S, R, SYM>(P, src, i, j, interior, f);
+  if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q, SYM>(P, src, i, j, interior, g);
   Macro<R> m;
   load_sources<S, R>(P, n, m);
   moments<R, FLOW, TH>(P, f, g, m);
@@ -68,13 +68,13 @@ __device__ __forceinline__ bool frame_node(int nx, int ny, int f, int &i, int &j
 // other rows the interior tiles, with the boundary code compiled out.  Keeping the
 // frame in warps of its own spares the interior warps that touch the inlet or
 // outlet column from running both paths one after the other.
-template <int PREC, int FLOW, int TH>
+template <int PREC, int FLOW, int TH, bool SYM>
 __global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_step_split(const SpParams P, int fy) {
   if ((int)blockIdx.y < fy) {
     const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
     int i, j;
     if (frame_node(P.nx, P.ny, (blockIdx.y * gridDim.x + blockIdx.x) * nt + tid, i, j))
-      step_node<PREC, FLOW, TH>(P, i, j);
+      step_node<PREC, FLOW, TH, false, SYM>(P, i, j);
     return;
   }
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = (blockIdx.y - fy) * blockDim.y + threadIdx.y;
@@ -83,12 +83,12 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_step_split(const SpP
 }
 
 // Every node in one pass (the first step after initialisation, whose pull is local).
-template <int PREC, int FLOW, int TH>
+template <int PREC, int FLOW, int TH, bool SYM>
 __global__ void __launch_bounds__(256) k_step(const SpParams P) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= P.nx || j >= P.ny) return;
-  step_node<PREC, FLOW, TH>(P, i, j);
+  step_node<PREC, FLOW, TH, false, SYM>(P, i, j);
 }
 
 // Many independent solves in one launch: blocks walk a flattened list of entries
@@ -106,12 +106,14 @@ __global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_batch_step(const SpP
     if (tl.w == 1) {
       int i, j;
       const int f = tl.y + threadIdx.y * blockDim.x + threadIdx.x;
-      if (frame_node(P.nx, P.ny, f, i, j)) step_node<PREC, FLOW, TH>(P, i, j);
+      if (!frame_node(P.nx, P.ny, f, i, j)) continue;
+      if (P.sym) step_node<PREC, FLOW, TH, false, true>(P, i, j);
+      else step_node<PREC, FLOW, TH>(P, i, j);
       continue;
     }
     const int i = tl.y + threadIdx.x, j = tl.z + threadIdx.y;
     if (i <= 0 || j <= 0 || i >= P.nx - 1 || j >= P.ny - 1) continue;  // frame entries
-    if (P.local) step_node<PREC, FLOW, TH>(P, i, j);
+    if (P.local) step_node<PREC, FLOW, TH>(P, i, j);  // local pull: no boundary links
     else step_node<PREC, FLOW, TH, true>(P, i, j);
   }
 }
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(256) k_init(const SpParams P, const double *A,
 }
 
 // Macroscopic fields of the current time: pull (with boundary rules) + moments.
-template <int PREC, int FLOW, int TH>
+template <int PREC, int FLOW, int TH, bool SYM>
 __global__ void __launch_bounds__(256) k_moments(const SpParams P, unsigned mask, double *out) {
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
@@ -164,8 +166,8 @@ __global__ void __launch_bounds__(256) k_moments(const SpParams P, unsigned mask
   const S *src = (const S *)P.src;
   const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
   R f[9], g[9];
-  if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
-  if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q>(P, src, i, j, interior, g);
+  if (FLOW != FLOW_NONE) pull_f<S, R, SYM>(P, src, i, j, interior, f);
+  if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q, SYM>(P, src, i, j, interior, g);
   Macro<R> m;
   load_sources<S, R>(P, n, m);
   moments<R, FLOW, TH>(P, f, g, m);
@@ -241,7 +243,7 @@ __device__ __forceinline__ void final_reduce(const double *partials, int nb, dou
 
 // Integrals in one launch: every block writes its partials; the block that counts
 // last (a device counter, 0 on entry and reset by that block) makes the final pass.
-template <int PREC, int FLOW, int TH>
+template <int PREC, int FLOW, int TH, bool SYM>
 __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *partials, double n_rho0, double area,
                                                    double *out4, unsigned *counter) {
   typedef typename Prec<PREC>::S S;
@@ -255,8 +257,8 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
     const S *src = (const S *)P.src;
     const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
     R f[9], g[9];
-    if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, interior, f);
-    if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q>(P, src, i, j, interior, g);
+    if (FLOW != FLOW_NONE) pull_f<S, R, SYM>(P, src, i, j, interior, f);
+    if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q, SYM>(P, src, i, j, interior, g);
     Macro<R> m;
     load_sources<S, R>(P, n, m);
     moments<R, FLOW, TH>(P, f, g, m);
@@ -295,9 +297,11 @@ cudaError_t SpOps<PREC, FLOW, TH>::step(const SpParams &P, dim3 block, cudaStrea
   const int nfb = (frame_nodes(P.nx, P.ny) + nt - 1) / nt;  // frame blocks
   const int fy = (nfb + (int)grid.x - 1) / (int)grid.x;      // rows of them
   if (!P.local && grid.y + fy <= 65535u) {                   // else the one-pass kernel
-    k_step_split<PREC, FLOW, TH><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
+    if (P.sym) k_step_split<PREC, FLOW, TH, true><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
+    else k_step_split<PREC, FLOW, TH, false><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
   } else {
-    k_step<PREC, FLOW, TH><<<grid, block, 0, s>>>(P);
+    if (P.sym) k_step<PREC, FLOW, TH, true><<<grid, block, 0, s>>>(P);
+    else k_step<PREC, FLOW, TH, false><<<grid, block, 0, s>>>(P);
   }
   return cudaGetLastError();
 }
@@ -327,7 +331,8 @@ cudaError_t SpOps<PREC, FLOW, TH>::init(const SpParams &P, const double *a, cons
 template <int PREC, int FLOW, int TH>
 cudaError_t SpOps<PREC, FLOW, TH>::moments(const SpParams &P, unsigned mask, double *out, cudaStream_t s) {
   const dim3 block(64, 4);
-  k_moments<PREC, FLOW, TH><<<grid_for(P.nx, P.ny, block), block, 0, s>>>(P, mask, out);
+  if (P.sym) k_moments<PREC, FLOW, TH, true><<<grid_for(P.nx, P.ny, block), block, 0, s>>>(P, mask, out);
+  else k_moments<PREC, FLOW, TH, false><<<grid_for(P.nx, P.ny, block), block, 0, s>>>(P, mask, out);
   return cudaGetLastError();
 }
 
@@ -336,7 +341,9 @@ cudaError_t SpOps<PREC, FLOW, TH>::integrals(const SpParams &P, double *partials
                                              cudaStream_t s) {
   const dim3 block(kRedBX, kRedBY);
   const double n_rho0 = (double)P.nx * P.ny * P.rho0, area = P.dx * P.dx;
-  k_integrals<PREC, FLOW, TH><<<grid_for(P.nx, P.ny, block), block, 0, s>>>(P, partials, n_rho0, area, out4, counter);
+  const dim3 grid = grid_for(P.nx, P.ny, block);
+  if (P.sym) k_integrals<PREC, FLOW, TH, true><<<grid, block, 0, s>>>(P, partials, n_rho0, area, out4, counter);
+  else k_integrals<PREC, FLOW, TH, false><<<grid, block, 0, s>>>(P, partials, n_rho0, area, out4, counter);
   return cudaGetLastError();
 }
 

@@ -133,8 +133,13 @@ __device__ __forceinline__ void step_node_staged(const SpParams &P, int i, int j
       for (int q = 0; q < QT; q++) g[q] = (R)gs[q * sp + so + stage_dx(cxT(QT, q))];
     }
   } else {
-    if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, false, f);
-    if (TH != TH_NONE) pull_g<S, R, QT>(P, src, i, j, false, g);
+    if (P.sym) {
+      if (FLOW != FLOW_NONE) pull_f<S, R, true>(P, src, i, j, false, f);
+      if (TH != TH_NONE) pull_g<S, R, QT, true>(P, src, i, j, false, g);
+    } else {
+      if (FLOW != FLOW_NONE) pull_f<S, R>(P, src, i, j, false, f);
+      if (TH != TH_NONE) pull_g<S, R, QT>(P, src, i, j, false, g);
+    }
   }
   Macro<R> m;
   load_sources<S, R>(P, n, m);
