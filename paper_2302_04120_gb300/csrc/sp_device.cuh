@@ -31,10 +31,12 @@ __device__ __forceinline__ bool on_side(const SpParams &P, int s, int i, int j) 
 __device__ __forceinline__ int entry_side(int i, int j, int cx, int cy, int nx, int ny, int xper, int yper,
                                           int ysym = 0) {
   const int si = i - cx, sj = j - cy;
-  const int ys = yper ? -1 : (sj < 0 ? 2 : (sj >= ny ? 3 : -1));
   const int xs = xper ? -1 : (si < 0 ? 0 : (si >= nx ? 1 : -1));
-  if (ys >= 0 && xs >= 0) return ((ysym >> (ys - 2)) & 1) ? xs : ys;
-  return ys >= 0 ? ys : xs;
+  if (!yper) {
+    if (sj < 0) return (ysym & 1) && xs >= 0 ? xs : 2;
+    if (sj >= ny) return (ysym & 2) && xs >= 0 ? xs : 3;
+  }
+  return xs;
 }
 
 // Source of a link entering node (i, j) through symmetry side `side` (Eq. simetria):
@@ -81,7 +83,9 @@ __device__ __forceinline__ void post_velocity(const SpParams &P, const S *src, i
     // buoyancy of T(t) = T0 + sum g* - dt qdot / 2 at this node
     const S *gs = src + (long long)P.gbase * P.plane;
     R sg = (R)0;
-    for (int q = 0; q < P.qg; q++) sg += (R)gs[q * P.plane + n];
+#pragma unroll
+    for (int q = 0; q < 9; q++)
+      if (q < P.qg) sg += (R)gs[q * P.plane + n];
     const R qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
     const R dT = (K<R>(P).T0 - K<R>(P).T_ref) + sg - (R)0.5 * K<R>(P).dt * qd;
     Fx += K<R>(P).bgx * dT;
