@@ -37,6 +37,7 @@
  *                                            s_i_Liang, forcing_term_pressure_evolution,
  *                                            p_Liang, u_Liang
  *   chemical potential, stencils ........... Eqs. chemical_potential, gradient, laplacian
+ *   two-phase walls (layered flow) ......... Sec. 4.4 (rule: readings R34, R35)
  *   dimensional M and rates ................ Sec. 3, Eq. M_matrix_dim, App. A Eq. Minv_matrix_dim
  *
  * Readings where the paper is silent, ambiguous or misprinted are listed in the
@@ -688,13 +689,17 @@ static void moments_two_phase(orc_t *o, double *gx, double *gy, double *lap) {
     o->phi[n] = s;
   }
   /* isotropic gradient and Laplacian with D2Q9 weights, Eqs. gradient and
-     laplacian (reading R23); periodic neighbours */
+     laplacian (reading R23); periodic neighbours, and across a wall the mirror
+     image of the boundary node, phi(-1) = phi(0) (reading R35) */
+  int xwall = o->bc[0] != BC_PERIODIC, ywall = o->bc[2] != BC_PERIODIC;
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       int n = idx(o, x, y);
       double sx = 0, sy = 0, sl = 0;
       for (int i = 1; i < 9; i++) {
-        int tx = (x + CX9[i] + nx) % nx, ty = (y + CY9[i] + ny) % ny;
+        int tx = x + CX9[i], ty = y + CY9[i];
+        if (tx < 0 || tx >= nx) tx = xwall ? (tx < 0 ? 0 : nx - 1) : (tx + nx) % nx;
+        if (ty < 0 || ty >= ny) ty = ywall ? (ty < 0 ? 0 : ny - 1) : (ty + ny) % ny;
         double pn = o->phi[idx(o, tx, ty)];
         sx += W9[i] * o->c * CX9[i] * pn;
         sy += W9[i] * o->c * CY9[i] * pn;
@@ -793,17 +798,25 @@ static void step_two_phase(orc_t *o) {
     o->phiux_prev[n] = phi * ux;
     o->phiuy_prev[n] = phi * uy;
   }
-  /* push streaming, periodic in both directions */
+  /* push streaming: periodic axes wrap; a link that leaves through a wall (at
+     rest, half-way) returns to its node as the opposite population, for z as in
+     Eq. BB_vel with u_w = 0 and for h likewise, so no phi crosses the wall
+     (reading R34) */
+  int xw = o->bc[0] != BC_PERIODIC, yw = o->bc[2] != BC_PERIODIC;
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       int n = idx(o, x, y);
       for (int i = 0; i < 5; i++) {
-        int tx = (x + CX5[i] + nx) % nx, ty = (y + CY5[i] + ny) % ny;
-        o->hn[i * N + idx(o, tx, ty)] = o->hpost[i * N + n];
+        int tx = x + CX5[i], ty = y + CY5[i];
+        int out = (xw && (tx < 0 || tx >= nx)) || (yw && (ty < 0 || ty >= ny));
+        if (out) o->hn[opp5(i) * N + n] = o->hpost[i * N + n];
+        else o->hn[i * N + idx(o, (tx + nx) % nx, (ty + ny) % ny)] = o->hpost[i * N + n];
       }
       for (int i = 0; i < 9; i++) {
-        int tx = (x + CX9[i] + nx) % nx, ty = (y + CY9[i] + ny) % ny;
-        o->zn[i * N + idx(o, tx, ty)] = o->zpost[i * N + n];
+        int tx = x + CX9[i], ty = y + CY9[i];
+        int out = (xw && (tx < 0 || tx >= nx)) || (yw && (ty < 0 || ty >= ny));
+        if (out) o->zn[opp9(i) * N + n] = o->zpost[i * N + n];
+        else o->zn[i * N + idx(o, (tx + nx) % nx, (ty + ny) % ny)] = o->zpost[i * N + n];
       }
     }
   double *t;

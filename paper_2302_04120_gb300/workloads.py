@@ -26,8 +26,14 @@ TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW, TBC_SYMMETRY = 0, 1, 2, 3, 4
 
 # Water of the forced-convection workload (rho, c_p, k) and Pr = 7.
 WATER = dict(rho0=1000.0, cp=4180.0, k=0.6)
-# Saturated water at 25 C (two-phase property table of Sec. 4.3).
+# The four two-phase systems of the property table of Sec. 4.3 (rho_g, rho_l in
+# kg m^-3, nu_g, nu_l in m^2 s^-1, sigma in N m^-1).
+AIR_WATER_25C = dict(rho_g=1.184, rho_l=997.048, nu_g=155.770e-7, nu_l=8.927e-7, sigma=0.072)
+SAT_WATER_100C = dict(rho_g=0.598, rho_l=958.349, nu_g=204.493e-7, nu_l=2.938e-7, sigma=0.059)
+SAT_WATER_80C = dict(rho_g=0.294, rho_l=971.766, nu_g=392.919e-7, nu_l=3.643e-7, sigma=0.063)
 SAT_WATER_25C = dict(rho_g=0.023, rho_l=997.003, nu_g=4204.120e-7, nu_l=8.927e-7, sigma=0.072)
+TWO_PHASE_SYSTEMS = {"air_water_25C": AIR_WATER_25C, "sat_water_100C": SAT_WATER_100C,
+                     "sat_water_80C": SAT_WATER_80C, "sat_water_25C": SAT_WATER_25C}
 
 
 def node_y(ny, dx):
@@ -184,6 +190,37 @@ def bubble(n=512, R_cells=64.0, W_cells=5.0, steps=100000, dx=5e-6, dt=1e-7, mob
     init = dict(a=phi0, ux=None, uy=None, b=None)
     return dict(name=f"bubble_{nx}x{ny}_R{R_cells:g}", params=params, bcs=[], init=init, q3=None,
                 steps=steps, R=R, W=W, r=r, xc=xc, yc=yc)
+
+
+# ---------------------------------------------------------------------------
+# Workload 3b: layered two-phase Poiseuille flow (Sec. 4.4)
+# ---------------------------------------------------------------------------
+def layered_poiseuille(fluid="air_water_25C", H=0.5e-3, dx=1.25e-6, dt=1.25e-7, nx=10, W=25e-6,
+                       mobility=1e-5, u_c=1e-4, steps=0, z_op=1, literal=0):
+    """Channel of height H between resting walls (y sides), periodic in x, liquid in
+    the lower half and gas in the upper half.
+
+    phi(y) = 1/2 - 1/2 tanh((2y - H)/W) (Eq. diffuse_interface across the plane y = H/2,
+    liquid below), so zeta = phi zeta_l + (1 - phi) zeta_g is the profile of
+    Eq. viscosity_prof; nu = zeta/rho (nu_rule 1); body force F_x = u_c (zeta_l +
+    zeta_g)/H^2; u = 0 and p = 0 at t = 0.  The paper uses 10 columns, W = 25 um,
+    M = 1e-5 m^2/s, dx = 1.25 um and dt = 1.25e-7 s (1.25e-8 s in its refinement
+    study), D2Q5 h with BGK and MRT for the momentum (z) equation.
+    """
+    fl = TWO_PHASE_SYSTEMS[fluid] if isinstance(fluid, str) else fluid
+    ny = int(round(H / dx))
+    y = node_y(ny, dx)
+    phi_y = 0.5 - 0.5 * np.tanh((2.0 * y - H) / W)
+    phi0 = np.repeat(phi_y[:, None], nx, axis=1)
+    zeta_l, zeta_g = fl["rho_l"] * fl["nu_l"], fl["rho_g"] * fl["nu_g"]
+    Fx = u_c * (zeta_l + zeta_g) / H ** 2
+    params = dict(nx=nx, ny=ny, flow=9, flow_op=1, thermal=0, phase=5, z_op=z_op, nu_rule=1, literal=literal,
+                  dx=dx, dt=dt, rho0=fl["rho_l"], W=W, mobility=mobility, Fb=(Fx, 0.0), **fl)
+    bcs = [(2, BC_WALL, None, fl["rho_l"], TBC_NONE, None), (3, BC_WALL, None, fl["rho_l"], TBC_NONE, None)]
+    init = dict(a=phi0, ux=None, uy=None, b=None)
+    name = fluid if isinstance(fluid, str) else "custom"
+    return dict(name=f"layered_poiseuille_{name}_{nx}x{ny}", params=params, bcs=bcs, init=init, q3=None,
+                steps=steps, H=H, W=W, Fx=Fx, zeta_l=zeta_l, zeta_g=zeta_g, u_c=u_c, y=y)
 
 
 # ---------------------------------------------------------------------------
