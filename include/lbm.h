@@ -156,10 +156,15 @@ lbm_status lbm_create(const lbm_params *p, void *stream, lbm_t *out);
  *        diagonal), on D2Q5 the single unknown with 1.
  * Both sides of an axis must be periodic together, for each lattice.  A link that
  * leaves through a corner takes the y-side rule, unless the y-side is a symmetry
- * side: then the other side's rule.  The arrays are copied before the
- * call returns (through pinned staging, without synchronising the stream); the new
- * values apply to steps enqueued after the call.
- * Errors: LBM_ERR_ARG (side, kind, pairing), LBM_ERR_CUDA.
+ * side: then the other side's rule.
+ * Two-phase solves (Sec. 4.4, layered flow between plates) take LBM_BC_PERIODIC or
+ * LBM_BC_WALL at rest (uw NULL or zero) and LBM_TBC_NONE: half-way bounce-back of z
+ * and h, and phi beyond the wall mirrored from the boundary node in the gradient
+ * and Laplacian stencils; an axis with a wall on either side is walled.
+ * The arrays are copied before the call returns (through pinned staging, without
+ * synchronising the stream); the new values apply to steps enqueued after the call.
+ * Errors: LBM_ERR_ARG (side, kind, pairing, a moving or non-wall two-phase side),
+ * LBM_ERR_CUDA.
  */
 lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, double rho_w, int tkind,
                       const double *tw);
@@ -187,8 +192,8 @@ lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux, const dou
 
 /*
  * Advance n >= 0 time steps: fused pull-stream + boundary links + moments + collision
- * (Eqs. eq_lattice_boltzmann_geral, colisao_MRT, ...), one kernel launch per step
- * for single-phase solves and two for two-phase solves, asynchronous on the stream.
+ * (Eqs. eq_lattice_boltzmann_geral, colisao_MRT, ...), one kernel launch per step,
+ * asynchronous on the stream.
  * Errors: LBM_ERR_STATE (not initialised), LBM_ERR_CUDA.
  */
 lbm_status lbm_step(lbm_t h, long n);

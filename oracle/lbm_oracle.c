@@ -691,7 +691,8 @@ static void moments_two_phase(orc_t *o, double *gx, double *gy, double *lap) {
   /* isotropic gradient and Laplacian with D2Q9 weights, Eqs. gradient and
      laplacian (reading R23); periodic neighbours, and across a wall the mirror
      image of the boundary node, phi(-1) = phi(0) (reading R35) */
-  int xwall = o->bc[0] != BC_PERIODIC, ywall = o->bc[2] != BC_PERIODIC;
+  int xwall = o->bc[0] != BC_PERIODIC || o->bc[1] != BC_PERIODIC;
+  int ywall = o->bc[2] != BC_PERIODIC || o->bc[3] != BC_PERIODIC;
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       int n = idx(o, x, y);
@@ -802,7 +803,8 @@ static void step_two_phase(orc_t *o) {
      rest, half-way) returns to its node as the opposite population, for z as in
      Eq. BB_vel with u_w = 0 and for h likewise, so no phi crosses the wall
      (reading R34) */
-  int xw = o->bc[0] != BC_PERIODIC, yw = o->bc[2] != BC_PERIODIC;
+  int xw = o->bc[0] != BC_PERIODIC || o->bc[1] != BC_PERIODIC;
+  int yw = o->bc[2] != BC_PERIODIC || o->bc[3] != BC_PERIODIC;
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       int n = idx(o, x, y);

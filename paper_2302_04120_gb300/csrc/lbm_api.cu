@@ -51,8 +51,25 @@ struct lbm_s {
   int nsm;
   CUtensorMap tmap[2];  // one per state buffer, boxes 36 x tmap_ty
   int tmap_ty;          // 0 until encoded
+  // Replay of kGraphSteps consecutive grid-launched steps as one CUDA graph, captured
+  // on a private stream (capture only records) and launched on `stream`.  One graph
+  // per parity of the buffer a run starts from; each stays valid while the launch
+  // parameters it was captured with (gkey) are unchanged.
+  cudaStream_t cap_stream;
+  cudaGraphExec_t gexec[2];
+  struct StepKey *gkey[2];
   char err[512];
 };
+
+// Everything a run of grid-launched steps depends on besides device memory contents:
+// the kernel choice and the parameter blocks of both buffer parities.
+struct StepKey {
+  int two_phase, prec, flow, th;
+  dim3 block;
+  lbmk::MpParams mp[2];
+  SpParams sp[2];
+};
+static constexpr long kGraphSteps = 64;  // even: the ping-pong buffers end where they start
 
 static char g_create_err[512];
 
@@ -204,6 +221,8 @@ static lbmk::MpParams mp_params(const lbm_t h, int from_buf) {
   P.nu_rule = p.nu_rule;
   P.z_mrt = p.z_op == LBM_MRT;
   P.qy_literal = (p.literal & 2) ? 1 : 0;
+  P.xwall = h->bc[0] != LBM_BC_PERIODIC || h->bc[1] != LBM_BC_PERIODIC;
+  P.ywall = h->bc[2] != LBM_BC_PERIODIC || h->bc[3] != LBM_BC_PERIODIC;
   P.Fx = p.body_force[0]; P.Fy = p.body_force[1];
   P.force = h->d_force;
   P.local = h->pre;
@@ -348,6 +367,11 @@ extern "C" void lbm_destroy(lbm_t h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_out4);
   if (h->h_out4) cudaFreeHost(h->h_out4);
+  for (int k = 0; k < 2; k++) {
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    free(h->gkey[k]);
+  }
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   free(h);
 }
 
@@ -363,9 +387,13 @@ extern "C" lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, 
   if (side < 0 || side > 3) return fail(h, LBM_ERR_ARG, "side must be 0..3");
   if (kind < LBM_BC_PERIODIC || kind > LBM_BC_SYMMETRY) return fail(h, LBM_ERR_ARG, "kind");
   if (tkind < LBM_TBC_NONE || tkind > LBM_TBC_SYMMETRY) return fail(h, LBM_ERR_ARG, "tkind");
-  if (two_phase(h) && (kind != LBM_BC_PERIODIC || tkind != LBM_TBC_NONE))
-    return fail(h, LBM_ERR_ARG, "two-phase solves support periodic sides only");
   const int len = side < 2 ? h->p.ny : h->p.nx;
+  if (two_phase(h)) {
+    if ((kind != LBM_BC_PERIODIC && kind != LBM_BC_WALL) || tkind != LBM_TBC_NONE)
+      return fail(h, LBM_ERR_ARG, "two-phase solves support periodic sides and resting walls only");
+    for (int k = 0; uw && k < 2 * len; k++)
+      if (uw[k] != 0.0) return fail(h, LBM_ERR_ARG, "two-phase walls are at rest (uw must be NULL or zero)");
+  }
   const int normal_len = side < 2 ? h->p.nx : h->p.ny;
   if ((kind == LBM_BC_PRESSURE || tkind == LBM_TBC_OUTFLOW) && normal_len < 2)
     return fail(h, LBM_ERR_ARG, "pressure/outflow sides need at least 2 nodes along the normal");
@@ -504,14 +532,76 @@ static void sp_kinds(const lbm_t h, int *flow, int *th) {
 
 static int *step_flag(lbm_t h) { return (int *)(h->d_out4 + 4); }
 
+// One grid-launched step reading buffer `from` (two-phase or single phase).
+static cudaError_t launch_grid_step(const lbm_t h, int from, int flow, int th, cudaStream_t st) {
+  if (two_phase(h)) return lbmk::mp_step(mp_params(h, from), h->p.precision, st);
+  return lbmk::sp_step(sp_params(h, from), h->p.precision, flow, th, h->block, st);
+}
+
+static void step_key(const lbm_t h, int flow, int th, StepKey *k) {
+  memset(k, 0, sizeof(*k));
+  k->two_phase = two_phase(h);
+  k->prec = h->p.precision;
+  k->flow = flow;
+  k->th = th;
+  k->block = h->block;
+  for (int b = 0; b < 2; b++) {
+    const int from = (h->cur + b) & 1;
+    if (k->two_phase) k->mp[b] = mp_params(h, from);
+    else k->sp[b] = sp_params(h, from);
+  }
+}
+
+// The graph of kGraphSteps steps starting from buffer h->cur, captured now if absent
+// or stale; NULL if capture is not possible (the caller then launches step by step).
+static cudaGraphExec_t step_graph(lbm_t h, int flow, int th) {
+  StepKey key;
+  step_key(h, flow, th, &key);
+  const int slot = h->cur;
+  if (h->gexec[slot] && memcmp(h->gkey[slot], &key, sizeof(key)) == 0) return h->gexec[slot];
+  if (h->gexec[slot]) {
+    cudaGraphExecDestroy(h->gexec[slot]);
+    h->gexec[slot] = NULL;
+  }
+  if (!h->gkey[slot] && !(h->gkey[slot] = (StepKey *)malloc(sizeof(StepKey)))) return NULL;
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->cap_stream = NULL;
+    return NULL;
+  }
+  if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return NULL;
+  cudaError_t e = cudaSuccess;
+  for (long s = 0; s < kGraphSteps && e == cudaSuccess; s++) e = launch_grid_step(h, (h->cur + s) & 1, flow, th, h->cap_stream);
+  cudaGraph_t g = NULL;
+  const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &g);
+  cudaGraphExec_t x = NULL;
+  if (e == cudaSuccess && ec == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) != cudaSuccess) x = NULL;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();  // a failed capture leaves no sticky error; clear the last one
+  if (!x) return NULL;
+  h->gexec[slot] = x;
+  memcpy(h->gkey[slot], &key, sizeof(key));
+  return x;
+}
+
 extern "C" lbm_status lbm_step(lbm_t h, long n) {
   if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
   if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
   if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_init_fields has not been called");
   int flow, th;
   sp_kinds(h, &flow, &th);
-  for (long s = 0; s < n; s++) {
+  for (long s = 0; s < n;) {
     cudaError_t e;
+    // long runs of grid-launched steps replay a captured graph (no per-step host work)
+    if (!h->pre && n - s >= kGraphSteps && (two_phase(h) || h->launch_kind != LBM_LAUNCH_TMA)) {
+      cudaGraphExec_t x = step_graph(h, flow, th);
+      if (x) {
+        e = cudaGraphLaunch(x, h->stream);
+        if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "step graph launch: %s", cudaGetErrorString(e));
+        s += kGraphSteps;
+        h->steps += kGraphSteps;
+        continue;
+      }
+    }
     if (two_phase(h)) {
       lbmk::MpParams P = mp_params(h, h->cur);
       e = lbmk::mp_step(P, h->p.precision, h->stream);
@@ -527,6 +617,7 @@ extern "C" lbm_status lbm_step(lbm_t h, long n) {
     h->cur = 1 - h->cur;
     h->pre = 0;
     h->steps++;
+    s++;
   }
   return LBM_OK;
 }

@@ -12,8 +12,8 @@ struct MpConst {
   R Fx, Fy, hdt, pcoef, om_h, sfac_h, aint_coef, inv_dt, ic;
 };
 
-// Two-phase solve on a fully periodic grid.  State planes: z_0..8, h_0..4,
-// (phi u)_x, (phi u)_y of the previous step.
+// Two-phase solve; each axis periodic or bounded by resting half-way walls on both
+// sides.  State planes: z_0..8, h_0..4, (phi u)_x, (phi u)_y of the previous step.
 struct MpParams {
   int nx, ny, pitch;
   long long plane;
@@ -24,6 +24,7 @@ struct MpParams {
   // (1 - dt/(2 tau_phi)) dt, 4 c_s^2 / W, 1/dt
   double inv_cs2, g3, l6, inv_cs2dt, om_h, sfac_h, aint_coef, inv_dt;
   int nu_rule, z_mrt, qy_literal;
+  int xwall, ywall;  // 1: the axis ends at resting walls (bounce-back, mirrored phi)
   double Fx, Fy;
   MpConst<double> kd;
   MpConst<float> kf;

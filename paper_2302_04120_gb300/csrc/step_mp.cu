@@ -3,7 +3,8 @@
 // of Martins, Alvarino & Cabezas-Gomez (arXiv:2302.04120), all in SI units.
 //
 // A step is ONE launch (k_mp_collide) over 32 x 8 tiles:
-//   * pull h_i for the tile and for a one-node periodic halo ring and stage
+//   * pull h_i for the tile and for a one-node halo ring (periodic, or beyond a
+//     resting wall the mirror image of the boundary node) and stage
 //     phi = sum h_i (Eq. zero_moment_h) in shared memory (the node's own h stay
 //     in registers; halo h re-reads hit L2, so DRAM sees each h once);
 //   * isotropic gradient and Laplacian (Eqs. gradient, laplacian, D2Q9 weights),
@@ -32,14 +33,31 @@ constexpr int BX = 32, BY = 8;
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 __device__ __forceinline__ int modi(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 
+// Source of the pull of population q (velocity (cx, cy), opposite o) at node (i, j):
+// the upstream node, wrapped on a periodic axis; on a walled axis a link whose
+// upstream node lies beyond the wall is the node's own opposite population
+// (half-way bounce-back at a resting wall).  Returns the element offset.
+__device__ __forceinline__ long long pull_src(const MpParams &P, int q, int o, int cx, int cy, int i, int j) {
+  if (P.local) return q * P.plane + (long long)j * P.pitch + i;
+  const int si = i - cx, sj = j - cy;
+  const bool out = (P.xwall && (si < 0 || si >= P.nx)) || (P.ywall && (sj < 0 || sj >= P.ny));
+  if (out) return o * P.plane + (long long)j * P.pitch + i;
+  return q * P.plane + (long long)wrapi(sj, P.ny) * P.pitch + wrapi(si, P.nx);
+}
+
+// Node whose phi stands at stencil position a along an axis of n nodes: wrapped on a
+// periodic axis; on a walled axis the mirror image of the boundary node for the one
+// layer beyond the wall (further positions are never read by a live node).
+__device__ __forceinline__ int stencil_node(int a, int n, int wall) {
+  if (wall) return a < 0 ? 0 : (a >= n ? n - 1 : a);
+  return a < 0 || a >= n ? modi(a, n) : a;
+}
+
 template <typename S, typename R>
 __device__ __forceinline__ void pull_h(const MpParams &P, const S *src, int i, int j, R h[5]) {
   const S *hs = src + 9ll * P.plane;
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
-    int si = P.local ? i : wrapi(i - cx5(q), P.nx), sj = P.local ? j : wrapi(j - cy5(q), P.ny);
-    h[q] = (R)hs[q * P.plane + (long long)sj * P.pitch + si];
-  }
+  for (int q = 0; q < 5; q++) h[q] = (R)hs[pull_src(P, q, opp5(q), cx5(q), cy5(q), i, j)];
 }
 
 // The same pulls for a node whose sources cannot wrap (blocks away from the grid's
@@ -68,10 +86,7 @@ __device__ __forceinline__ float inv_norm(float g2) { return g2 != 0.0f ? rsqrtf
 template <typename S, typename R>
 __device__ __forceinline__ void pull_z(const MpParams &P, const S *src, int i, int j, R z[9]) {
 #pragma unroll
-  for (int q = 0; q < 9; q++) {
-    int si = P.local ? i : wrapi(i - cx9(q), P.nx), sj = P.local ? j : wrapi(j - cy9(q), P.ny);
-    z[q] = (R)src[q * P.plane + (long long)sj * P.pitch + si];
-  }
+  for (int q = 0; q < 9; q++) z[q] = (R)src[pull_src(P, q, opp9(q), cx9(q), cy9(q), i, j)];
 }
 
 // Macroscopic state of a node.  The order parameter, its stencils, the chemical
@@ -311,8 +326,7 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
   if (inner) {
     pull_h_at<S, R>(P, src + ((long long)j * P.pitch + i), h);
   } else {
-    const int gi = i < P.nx ? i : modi(i, P.nx), gj = j < P.ny ? j : modi(j, P.ny);
-    pull_h<S, R>(P, src, gi, gj, h);
+    pull_h<S, R>(P, src, stencil_node(i, P.nx, P.xwall), stencil_node(j, P.ny, P.ywall), h);
   }
   tile[threadIdx.y + 1][threadIdx.x + 1] = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
   constexpr int kHalo = 2 * (BX + 2) + 2 * BY;
@@ -326,8 +340,7 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
     if (inner) {
       pull_h_at<S, R>(P, src + ((long long)(j0 + ty - 1) * P.pitch + (i0 + tx - 1)), hh);
     } else {
-      const int gi = modi(i0 + tx - 1, P.nx), gj = modi(j0 + ty - 1, P.ny);
-      pull_h<S, R>(P, src, gi, gj, hh);
+      pull_h<S, R>(P, src, stencil_node(i0 + tx - 1, P.nx, P.xwall), stencil_node(j0 + ty - 1, P.ny, P.ywall), hh);
     }
     tile[ty][tx] = (hh[0] + hh[1]) + (hh[2] + hh[3]) + hh[4];
   }
