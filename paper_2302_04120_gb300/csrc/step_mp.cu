@@ -28,7 +28,10 @@ namespace lbmk {
 
 namespace {
 
-constexpr int BX = 32, BY = 8;
+// Tiles are 32 nodes wide and BY = 8 rows high, or 2 rows on grids too small to give
+// every SM several 32 x 8 tiles (the FP64 collision is then spread over more SMs).
+constexpr int BX = 32;
+constexpr int kSmallGridBlocks = 608;  // 4 x 152 SMs: fewer 32 x 8 tiles take BY = 2
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 __device__ __forceinline__ int modi(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
@@ -285,6 +288,7 @@ __device__ __forceinline__ void collide_z(const MpParams &P, const MpMacro<R> &m
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 2, MODE_INTEGRALS = 3 };
 
+template <int BY>
 __device__ __forceinline__ void reduce4_block(double v[4], double *out) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -305,7 +309,7 @@ __device__ __forceinline__ void reduce4_block(double v[4], double *out) {
 }
 
 // pass 2 (and its init / moments / integrals variants)
-template <int PREC, int MODE>
+template <int PREC, int MODE, int BY>
 __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const double *A, const double *UX,
                                                          const double *UY, const double *B, unsigned mask,
                                                          double *out) {
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
       red[3] = bad ? 1.0 : 0.0;
     }
   }
-  if (MODE == MODE_INTEGRALS) reduce4_block(red, out + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
+  if (MODE == MODE_INTEGRALS) reduce4_block<BY>(red, out + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 __global__ void k_mp_final(const double *partials, int nb, double *out4) {
@@ -441,52 +445,50 @@ __global__ void k_mp_init(const MpParams P, const double *A, const double *UX, c
   dst[15ll * P.plane + n] = (S)(ph * v0);
 }
 
-dim3 mp_grid(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
+dim3 mp_grid(int nx, int ny, int by) { return dim3((nx + BX - 1) / BX, (ny + by - 1) / by); }
+int mp_rows(int nx, int ny) { return (int)(mp_grid(nx, ny, 8).x * mp_grid(nx, ny, 8).y) >= kSmallGridBlocks ? 8 : 2; }
+
+template <int PREC, int MODE>
+void launch_collide(const MpParams &P, unsigned mask, double *out, cudaStream_t s) {
+  const int by = mp_rows(P.nx, P.ny);
+  const dim3 g = mp_grid(P.nx, P.ny, by);
+  if (by == 8) k_mp_collide<PREC, MODE, 8><<<g, dim3(BX, 8), 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
+  else k_mp_collide<PREC, MODE, 2><<<g, dim3(BX, 2), 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
+}
 
 }  // namespace
 
 int mp_integral_blocks(int nx, int ny) {
-  dim3 g = mp_grid(nx, ny);
+  dim3 g = mp_grid(nx, ny, mp_rows(nx, ny));
   return (int)(g.x * g.y);
 }
 
 cudaError_t mp_step(const MpParams &P, int prec, cudaStream_t s) {
-  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
-  if (prec == 0) {
-    k_mp_collide<0, MODE_STEP><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
-  } else {
-    k_mp_collide<1, MODE_STEP><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
-  }
+  if (prec == 0) launch_collide<0, MODE_STEP>(P, 0u, nullptr, s);
+  else launch_collide<1, MODE_STEP>(P, 0u, nullptr, s);
   return cudaGetLastError();
 }
 
 cudaError_t mp_init(const MpParams &P, int prec, const double *phi0, const double *ux0, const double *uy0,
                     const double *p0, cudaStream_t s) {
-  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
+  dim3 b(BX, 8), g = mp_grid(P.nx, P.ny, 8);
   if (prec == 0) k_mp_init<double><<<g, b, 0, s>>>(P, phi0, ux0, uy0, p0);
   else k_mp_init<float><<<g, b, 0, s>>>(P, phi0, ux0, uy0, p0);
   return cudaGetLastError();
 }
 
 cudaError_t mp_moments(const MpParams &P, int prec, unsigned mask, double *out, cudaStream_t s) {
-  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
-  if (prec == 0) {
-    k_mp_collide<0, MODE_MOMENTS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
-  } else {
-    k_mp_collide<1, MODE_MOMENTS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, mask, out);
-  }
+  if (prec == 0) launch_collide<0, MODE_MOMENTS>(P, mask, out, s);
+  else launch_collide<1, MODE_MOMENTS>(P, mask, out, s);
   return cudaGetLastError();
 }
 
 cudaError_t mp_integrals(const MpParams &P, int prec, double *partials, int max_blocks, double *out4, cudaStream_t s) {
-  dim3 b(BX, BY), g = mp_grid(P.nx, P.ny);
-  if ((int)(g.x * g.y) > max_blocks) return cudaErrorInvalidValue;
-  if (prec == 0) {
-    k_mp_collide<0, MODE_INTEGRALS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, partials);
-  } else {
-    k_mp_collide<1, MODE_INTEGRALS><<<g, b, 0, s>>>(P, nullptr, nullptr, nullptr, nullptr, 0u, partials);
-  }
-  k_mp_final<<<1, 32, 0, s>>>(partials, (int)(g.x * g.y), out4);
+  const int nb = mp_integral_blocks(P.nx, P.ny);
+  if (nb > max_blocks) return cudaErrorInvalidValue;
+  if (prec == 0) launch_collide<0, MODE_INTEGRALS>(P, 0u, partials, s);
+  else launch_collide<1, MODE_INTEGRALS>(P, 0u, partials, s);
+  k_mp_final<<<1, 32, 0, s>>>(partials, nb, out4);
   return cudaGetLastError();
 }
 

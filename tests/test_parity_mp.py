@@ -66,6 +66,21 @@ def test_bubble_fp64_short(z_op):
     assert rel_max(st["z"], o.dist("z", post=True)) < 1e-12
 
 
+def test_bubble_fp64_large_grid():
+    """1024 x 160 box (640 tiles of 32 x 8 rows: the 8-row tile variant; the smaller
+    grids above run the 2-row one), bubble R = 40, W = 4, 10 steps: FP64 parity to
+    1e-12 on phi, p - mean p and u."""
+    w = wl.bubble(n=1024, ny=160, R_cells=40.0, W_cells=4.0, steps=10)
+    o = run_oracle(w)
+    s = run_gpu(w, 0)
+    mo, mg = o.moments(), s.moments()
+    assert rel_max(mg["phi"], mo["phi"]) < 1e-12
+    assert rel_max(mg["p"], mo["p"], mo["p"] - mo["p"].mean()) < 1e-12
+    sp = np.hypot(mo["ux"], mo["uy"])
+    assert rel_max(mg["ux"], mo["ux"], sp) < 1e-12
+    assert rel_max(mg["uy"], mo["uy"], sp) < 1e-12
+
+
 def test_bubble_fp64_long_within_envelope():
     """300 steps: GPU-vs-oracle differences stay within 10x the oracle's own spread
     under a 1e-15 perturbation of phi0 (and below 1e-6 outright)."""
