@@ -78,7 +78,7 @@ typedef struct {
 } orc_params;
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3, BC_SYMMETRY = 4 };
-enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY = 4 };
+enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY = 4, TBC_WETNODE = 5 };
 
 /* ------------------------------------------------------------------------- */
 /* Velocity sets                                                             */
@@ -549,7 +549,7 @@ static double flow_boundary_value(const orc_t *o, int side, int x, int y, int i)
 }
 
 /* Thermal: value entering node opposite to outgoing i through `side`;
-   OUTFLOW and SYMMETRY are resolved after streaming. */
+   OUTFLOW, SYMMETRY and WETNODE are resolved after streaming. */
 static double thermal_boundary_value(const orc_t *o, int side, int x, int y, int i) {
   int n = idx(o, x, y);
   int N = o->N;
@@ -573,7 +573,7 @@ static double thermal_boundary_value(const orc_t *o, int side, int x, int y, int
       return -gs + 2.0 * wg(o, i) * Tw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
     }
     default:
-      return gs; /* OUTFLOW placeholder, overwritten after streaming */
+      return gs; /* OUTFLOW / WETNODE placeholder, overwritten after streaming */
   }
 }
 
@@ -671,6 +671,24 @@ static void stream_single(orc_t *o) {
           if (crossed_side(o, 1, x, y, -cxg(o, q), -cyg(o, q)) != side) continue;
           o->gn[q * N + idx(o, x, y)] = o->gn[q * N + idx(o, xi, yi)];
         }
+      }
+    }
+    /* wet-node Dirichlet side (App. B, Eq. BCs_1D_advection_diffusion): the boundary
+       node lies on the boundary and its single unknown D2Q5 population closes the
+       zeroth moment so that the node's T of Eq. zero_moment_g equals T_w:
+       g_unknown = T_w - dt qdot/2 - (sum of the others), qdot that of the next step
+       (its lag is this step's T); x-sides only (reading R37) */
+    for (int side = 0; side < 2; side++) {
+      if (o->tbc[side] != TBC_WETNODE) continue;
+      int x = side == 0 ? 0 : nx - 1, q = side == 0 ? 1 : 3;
+      for (int y = 0; y < ny; y++) {
+        int n = idx(o, x, y);
+        double qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;
+        if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->T[n] - p->T_inf);
+        double others = 0.0;
+        for (int i = 0; i < 5; i++)
+          if (i != q) others += o->gn[i * N + n];
+        o->gn[q * N + n] = o->bct[side][y] - 0.5 * p->dt * qd - others;
       }
     }
   }

@@ -22,7 +22,7 @@ import numpy as np
 
 # boundary kinds (same numbering as include/lbm.h and the oracle)
 BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_PRESSURE, BC_SYMMETRY = 0, 1, 2, 3, 4
-TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW, TBC_SYMMETRY = 0, 1, 2, 3, 4
+TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW, TBC_SYMMETRY, TBC_WETNODE = 0, 1, 2, 3, 4, 5
 
 # Water of the forced-convection workload (rho, c_p, k) and Pr = 7.
 WATER = dict(rho0=1000.0, cp=4180.0, k=0.6)
