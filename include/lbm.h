@@ -70,7 +70,11 @@ enum {
   LBM_TBC_FLUX = 1,    /* prescribed heat flux into the fluid, Eq. BB_T                     */
   LBM_TBC_TEMP = 2,    /* prescribed temperature, Eq. anti_BB_T                             */
   LBM_TBC_OUTFLOW = 3, /* first-order extrapolation of the unknown populations (Sec. 2.2)   */
-  LBM_TBC_SYMMETRY = 4 /* symmetry plane for the thermal lattice, Eq. simetria              */
+  LBM_TBC_SYMMETRY = 4, /* symmetry plane for the thermal lattice, Eq. simetria             */
+  LBM_TBC_WETNODE = 5   /* wet-node Dirichlet T_w (App. B): the boundary node lies on the
+                           boundary (x = 0 or x = L) and its single unknown population is
+                           T_w - dt qdot/2 - (sum of the others), so its T is T_w; D2Q5,
+                           x-sides only                                                  */
 };
 /* sides */
 enum { LBM_SIDE_XMIN = 0, LBM_SIDE_XMAX = 1, LBM_SIDE_YMIN = 2, LBM_SIDE_YMAX = 3 };
@@ -177,6 +181,22 @@ lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, double rho_
  * are device pointers.  Errors: LBM_ERR_ARG, LBM_ERR_NOMEM, LBM_ERR_CUDA.
  */
 lbm_status lbm_set_source(lbm_t h, const double *q3, const double *force, int on_device);
+
+/*
+ * Lagged linear heat sink of the fuse problem (Sec. 4.1, Eq. conver_energy_fuse):
+ * qdot(t) = q'''/(rho0 cp) - conv_coef (T(t - dt) - T_inf), the temperature of the
+ * previous step, so that the update stays explicit.  Before every step (and before
+ * lbm_moments) a kernel rebuilds T(t - dt) at each node from its own post-collision
+ * populations, T = T0 + sum g* - dt qdot/2 (the collision adds dt qdot to sum g), and
+ * writes this step's qdot; after lbm_init_fields T(-dt) is the initial T.
+ *  conv_coef [s^-1] (4 hbar / (rho cp d) for the fuse); 0 removes the sink.
+ *  T_inf     [K].
+ * q''' of lbm_set_source stays the base of qdot.  Needs a thermal LBE; not with
+ * buoyancy, the literal thermal-source flag (literal bit 0) or the adjoint.
+ * After lbm_set_state the lag restarts from the base qdot.
+ * Errors: LBM_ERR_ARG, LBM_ERR_NOMEM, LBM_ERR_CUDA.
+ */
+lbm_status lbm_set_lagged_sink(lbm_t h, double conv_coef, double T_inf);
 
 /*
  * Initialise every distribution at its equilibrium (Eqs. feq_geral, geq_geral,

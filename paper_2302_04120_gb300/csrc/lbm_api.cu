@@ -37,6 +37,10 @@ struct lbm_s {
   int uw_zero[4], tw_zero[4];  // the device array holds zeros (no upload since the last fill)
   // sources (storage precision, pitched)
   void *d_qdot, *d_force;
+  // lagged heat sink (lbm_set_lagged_sink): qdot = qbase - conv (T(t - dt) - T_inf); the
+  // two qdot fields ping-pong with buf[]: d_qs[b] is the one the step writing buf[b] used
+  double sink_conv, sink_Tinf;
+  void *d_qbase, *d_qs[2];
   // reductions
   double *d_partials;
   int max_blocks;
@@ -66,6 +70,7 @@ struct lbm_s {
 struct StepKey {
   int two_phase, prec, flow, th;
   dim3 block;
+  double sink_conv, sink_Tinf;
   lbmk::MpParams mp[2];
   SpParams sp[2];
 };
@@ -149,7 +154,9 @@ static SpParams sp_params(const lbm_t h, int from_buf) {
   P.fysym = (h->bc[2] == LBM_BC_SYMMETRY ? 1 : 0) | (h->bc[3] == LBM_BC_SYMMETRY ? 2 : 0);
   P.tysym = (h->tbc[2] == LBM_TBC_SYMMETRY ? 1 : 0) | (h->tbc[3] == LBM_TBC_SYMMETRY ? 2 : 0);
   P.sym = 0;
-  for (int s = 0; s < 4; s++) P.sym |= h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY;
+  // the boundary-rule variant of the kernels: symmetry sides and wet-node sides
+  for (int s = 0; s < 4; s++)
+    P.sym |= h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY || h->tbc[s] == LBM_TBC_WETNODE;
   for (int s = 0; s < 4; s++) {
     P.side[s].kind = h->bc[s];
     P.side[s].tkind = h->tbc[s];
@@ -178,7 +185,7 @@ static SpParams sp_params(const lbm_t h, int from_buf) {
       P.T_ref = p.T_ref;
     }
   }
-  P.qdot = h->d_qdot;
+  P.qdot = h->sink_conv != 0.0 ? h->d_qs[1 - from_buf] : h->d_qdot;
   P.force = h->d_force;
   fill_const(P, P.kd);
   fill_const(P, P.kf);
@@ -363,6 +370,9 @@ extern "C" void lbm_destroy(lbm_t h) {
     if (h->stage_done[s]) cudaEventDestroy(h->stage_done[s]);
   }
   cudaFree(h->d_qdot);
+  cudaFree(h->d_qbase);
+  cudaFree(h->d_qs[0]);
+  cudaFree(h->d_qs[1]);
   cudaFree(h->d_force);
   cudaFree(h->d_partials);
   cudaFree(h->d_out4);
@@ -386,7 +396,9 @@ extern "C" lbm_status lbm_set_bc(lbm_t h, int side, int kind, const double *uw, 
   if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
   if (side < 0 || side > 3) return fail(h, LBM_ERR_ARG, "side must be 0..3");
   if (kind < LBM_BC_PERIODIC || kind > LBM_BC_SYMMETRY) return fail(h, LBM_ERR_ARG, "kind");
-  if (tkind < LBM_TBC_NONE || tkind > LBM_TBC_SYMMETRY) return fail(h, LBM_ERR_ARG, "tkind");
+  if (tkind < LBM_TBC_NONE || tkind > LBM_TBC_WETNODE) return fail(h, LBM_ERR_ARG, "tkind");
+  if (tkind == LBM_TBC_WETNODE && (side > 1 || h->p.thermal != LBM_D2Q5))
+    return fail(h, LBM_ERR_ARG, "wet-node sides are x-sides of a D2Q5 thermal lattice");
   const int len = side < 2 ? h->p.ny : h->p.nx;
   if (two_phase(h)) {
     if ((kind != LBM_BC_PERIODIC && kind != LBM_BC_WALL) || tkind != LBM_TBC_NONE)
@@ -456,9 +468,12 @@ extern "C" lbm_status lbm_set_source(lbm_t h, const double *q3, const double *fo
   lbm_status st;
   if (q3) {
     if (!h->p.thermal) return fail(h, LBM_ERR_ARG, "heat source needs a thermal LBE");
-    // qdot = q'''/(rho c_p) in K/s (Sec. 2.2)
-    st = upload_field(h, q3, 1, on_device, &h->d_qdot, 1.0 / (h->p.rho0 * h->p.cp));
+    // qdot = q'''/(rho c_p) in K/s (Sec. 2.2); with a lagged sink it is the sink's base
+    st = upload_field(h, q3, 1, on_device, h->sink_conv != 0.0 ? &h->d_qbase : &h->d_qdot,
+                      1.0 / (h->p.rho0 * h->p.cp));
     if (st != LBM_OK) return st;
+  } else if (h->sink_conv != 0.0) {
+    CU(h, cudaMemsetAsync(h->d_qbase, 0, (size_t)h->plane * h->elem, h->stream));
   } else if (h->d_qdot) {
     CU(h, cudaStreamSynchronize(h->stream));
     cudaFree(h->d_qdot);
@@ -473,6 +488,47 @@ extern "C" lbm_status lbm_set_source(lbm_t h, const double *q3, const double *fo
     cudaFree(h->d_force);
     h->d_force = NULL;
   }
+  CU(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_lagged_sink(lbm_t h, double conv_coef, double T_inf) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  const lbm_params &p = h->p;
+  if (!p.thermal) return fail(h, LBM_ERR_ARG, "the lagged sink needs a thermal LBE");
+  if (!isfinite(conv_coef) || !isfinite(T_inf)) return fail(h, LBM_ERR_ARG, "non-finite sink coefficients");
+  const size_t bytes = (size_t)h->plane * h->elem;
+  if (conv_coef == 0.0) {
+    if (h->sink_conv != 0.0) {  // back to the plain source field, which is the base
+      CU(h, cudaStreamSynchronize(h->stream));
+      cudaFree(h->d_qdot);
+      h->d_qdot = h->d_qbase;
+      h->d_qbase = NULL;
+      cudaFree(h->d_qs[0]);
+      cudaFree(h->d_qs[1]);
+      h->d_qs[0] = h->d_qs[1] = NULL;
+    }
+    h->sink_conv = 0.0;
+    return LBM_OK;
+  }
+  if (p.literal & 1) return fail(h, LBM_ERR_ARG, "the lagged sink needs the tau_T source factor (literal bit 0 off)");
+  if (p.beta_exp != 0.0) return fail(h, LBM_ERR_ARG, "the lagged sink is not combined with buoyancy");
+  if (h->sink_conv == 0.0) {
+    void **f[3] = {&h->d_qbase, &h->d_qs[0], &h->d_qs[1]};
+    for (int k = 0; k < 3; k++) {
+      if (cudaMalloc(f[k], bytes) != cudaSuccess) {
+        *f[k] = NULL;
+        return fail(h, LBM_ERR_NOMEM, "cudaMalloc lagged-sink field");
+      }
+      CU(h, cudaMemsetAsync(*f[k], 0, bytes, h->stream));
+    }
+    if (h->d_qdot) {  // the source so far is the base and the field the last step used
+      CU(h, cudaMemcpyAsync(h->d_qbase, h->d_qdot, bytes, cudaMemcpyDeviceToDevice, h->stream));
+      CU(h, cudaMemcpyAsync(h->d_qs[h->cur], h->d_qdot, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    }
+  }
+  h->sink_conv = conv_coef;
+  h->sink_Tinf = T_inf;
   CU(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
@@ -532,9 +588,21 @@ static void sp_kinds(const lbm_t h, int *flow, int *th) {
 
 static int *step_flag(lbm_t h) { return (int *)(h->d_out4 + 4); }
 
+// qdot of the lagged sink for the step (or moments) that reads buffer `from`
+// (pre: the buffer holds the initial state itself); nothing without a sink.
+static cudaError_t sink_refresh(const lbm_t h, int from, int pre, cudaStream_t st) {
+  if (h->sink_conv == 0.0) return cudaSuccess;
+  const lbm_params &p = h->p;
+  return lbmk::lagged_qdot(h->buf[from], h->d_qs[from], h->d_qbase, h->d_qs[1 - from], p.nx, p.ny, h->pitch, h->plane,
+                           p.flow == LBM_D2Q9 ? 9 : 0, p.thermal, p.T0, p.dt, h->sink_conv, h->sink_Tinf, pre,
+                           p.precision, st);
+}
+
 // One grid-launched step reading buffer `from` (two-phase or single phase).
 static cudaError_t launch_grid_step(const lbm_t h, int from, int flow, int th, cudaStream_t st) {
   if (two_phase(h)) return lbmk::mp_step(mp_params(h, from), h->p.precision, st);
+  const cudaError_t e = sink_refresh(h, from, 0, st);
+  if (e != cudaSuccess) return e;
   return lbmk::sp_step(sp_params(h, from), h->p.precision, flow, th, h->block, st);
 }
 
@@ -545,6 +613,8 @@ static void step_key(const lbm_t h, int flow, int th, StepKey *k) {
   k->flow = flow;
   k->th = th;
   k->block = h->block;
+  k->sink_conv = h->sink_conv;
+  k->sink_Tinf = h->sink_Tinf;
   for (int b = 0; b < 2; b++) {
     const int from = (h->cur + b) & 1;
     if (k->two_phase) k->mp[b] = mp_params(h, from);
@@ -602,6 +672,10 @@ extern "C" lbm_status lbm_step(lbm_t h, long n) {
         continue;
       }
     }
+    if (!two_phase(h)) {
+      e = sink_refresh(h, h->cur, h->pre, h->stream);
+      if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "sink launch: %s", cudaGetErrorString(e));
+    }
     if (two_phase(h)) {
       lbmk::MpParams P = mp_params(h, h->cur);
       e = lbmk::mp_step(P, h->p.precision, h->stream);
@@ -641,7 +715,8 @@ extern "C" lbm_status lbm_moments(lbm_t h, unsigned mask, double *out, int on_de
     int flow, th;
     sp_kinds(h, &flow, &th);
     SpParams P = sp_params(h, h->cur);
-    e = lbmk::sp_moments(P, h->p.precision, flow, th, mask, dout, h->stream);
+    e = sink_refresh(h, h->cur, h->pre, h->stream);
+    if (e == cudaSuccess) e = lbmk::sp_moments(P, h->p.precision, flow, th, mask, dout, h->stream);
   }
   if (e != cudaSuccess) {
     if (!on_device) cudaFree(dout);
@@ -715,6 +790,8 @@ static lbm_status state_copy(lbm_t h, void *host, size_t bytes, int unpack) {
   if (e != cudaSuccess || e2 != cudaSuccess)
     return fail(h, LBM_ERR_CUDA, "state copy: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
   if (unpack) { h->initialised = 1; h->pre = 0; }
+  if (unpack && h->sink_conv != 0.0)  // the lag restarts from the base qdot
+    CU(h, cudaMemcpyAsync(h->d_qs[h->cur], h->d_qbase, (size_t)h->plane * h->elem, cudaMemcpyDeviceToDevice, h->stream));
   return LBM_OK;
 }
 
@@ -1047,8 +1124,9 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
   if (p.phase || p.flow != LBM_D2Q9 || p.flow_op != LBM_MRT || p.thermal != LBM_D2Q5 || p.thermal_op != LBM_MRT)
     return fail(h, LBM_ERR_ARG, "the adjoint covers single-phase D2Q9 MRT + D2Q5 MRT solves");
   for (int s = 0; s < 4; s++)
-    if (h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY)
-      return fail(h, LBM_ERR_ARG, "the adjoint does not cover symmetry sides");
+    if (h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY || h->tbc[s] == LBM_TBC_WETNODE)
+      return fail(h, LBM_ERR_ARG, "the adjoint does not cover symmetry or wet-node sides");
+  if (h->sink_conv != 0.0) return fail(h, LBM_ERR_ARG, "the adjoint does not cover the lagged sink");
   if (p.precision != LBM_FP64) return fail(h, LBM_ERR_ARG, "the adjoint runs in FP64");
   if (p.beta_exp != 0.0) return fail(h, LBM_ERR_ARG, "the adjoint does not cover the buoyancy coupling");
   if (p.nx < 2) return fail(h, LBM_ERR_ARG, "nx must be >= 2 (loss on the x+ column)");

@@ -88,6 +88,12 @@ struct ThLat {
 
 // Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
+// qdot of the lagged heat sink for the step reading `src` (csrc/sink.cu): qnext =
+// qbase - conv (T(t - dt) - T_inf), T(t - dt) rebuilt from src and qprev (pre: src
+// holds the initial state itself).  Storage precision fields, one plane each.
+cudaError_t lagged_qdot(const void *src, const void *qprev, const void *qbase, void *qnext, int nx, int ny, int pitch,
+                        long long plane, int gbase, int qg, double T0, double dt, double conv, double Tinf, int pre,
+                        int precision, cudaStream_t s);
 // One step of many solves: table[k] holds the parameters (with this step's src/dst)
 // of channel k; tiles lists the frame chunks (channel, f0, 0, 1) and the interior
 // tiles (channel, x0, y0, 0) of every channel.

@@ -10,7 +10,7 @@
 namespace lbmk {
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_VELOCITY = 2, BC_PRESSURE = 3, BC_SYMMETRY = 4 };
-enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY = 4 };
+enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY = 4, TBC_WETNODE = 5 };
 
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -258,7 +258,7 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
   // 3. boundary links
 #pragma unroll
   for (int q = 0; q < QT; q++) {
-    if (side[q] < 0 || tk[q] == TBC_OUTFLOW || (SYM && tk[q] == TBC_SYMMETRY)) {
+    if (side[q] < 0 || tk[q] == TBC_OUTFLOW || (SYM && (tk[q] == TBC_SYMMETRY || tk[q] == TBC_WETNODE))) {
       g[q] = raw[q];
       continue;
     }
@@ -284,6 +284,22 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
     } else {
       // Eq. BB_T with lambda = 1 for the single D2Q5 unknown (FLUX; zero flux = adiabatic)
       g[q] = go + K<R>(P).flux_coef * Tw;
+    }
+  }
+  // 4. wet-node x-sides (App. B, Eq. BCs_1D_advection_diffusion): the boundary node lies
+  //    on the boundary; its single D2Q5 unknown closes T of Eq. zero_moment_g at T_w,
+  //    g_unknown = T_w - dt qdot/2 - (sum of the others), in deviation form
+  if (SYM && QT == 5) {
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+      if (P.side[s].tkind != TBC_WETNODE || i != (s == 0 ? 0 : P.nx - 1)) continue;
+      const int qu = s == 0 ? 1 : 3;
+      R others = (R)0;
+#pragma unroll
+      for (int k = 0; k < QT; k++)
+        if (k != qu) others += g[k];
+      const R qd = P.qdot ? (R)((const S *)P.qdot)[n] : (R)0;
+      g[qu] = (tws[s] - K<R>(P).T0) - (R)0.5 * K<R>(P).dt * qd - others;
     }
   }
 }

@@ -23,7 +23,7 @@ LBM_NONE, LBM_D2Q5, LBM_D2Q9 = 0, 5, 9
 LBM_BGK, LBM_MRT = 0, 1
 LBM_FP64, LBM_FP32DEV = 0, 1
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE, LBM_BC_SYMMETRY = 0, 1, 2, 3, 4
-LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW, LBM_TBC_SYMMETRY = 0, 1, 2, 3, 4
+LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW, LBM_TBC_SYMMETRY, LBM_TBC_WETNODE = 0, 1, 2, 3, 4, 5
 LBM_RHO, LBM_UX, LBM_UY, LBM_T, LBM_P, LBM_PHI = 1, 2, 4, 8, 16, 32
 LBM_LAUNCH_GRID, LBM_LAUNCH_TMA = 0, 1
 _MOMENT_BITS = [("rho", 1), ("ux", 2), ("uy", 4), ("T", 8), ("p", 16), ("phi", 32)]
@@ -67,6 +67,7 @@ def lib():
         L.lbm_create.argtypes = [C.POINTER(lbm_params), C.c_void_p, C.POINTER(C.c_void_p)]
         L.lbm_set_bc.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_int, C.c_void_p]
         L.lbm_set_source.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.lbm_set_lagged_sink.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.lbm_init_fields.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.lbm_step.argtypes = [C.c_void_p, C.c_long]
         L.lbm_steps_done.argtypes = [C.c_void_p]
@@ -84,7 +85,7 @@ def lib():
         L.lbm_last_error.restype = C.c_char_p
         L.lbm_destroy.argtypes = [C.c_void_p]
         L.lbm_destroy.restype = None
-        for name in ("lbm_create", "lbm_set_bc", "lbm_set_source", "lbm_init_fields", "lbm_step",
+        for name in ("lbm_create", "lbm_set_bc", "lbm_set_source", "lbm_set_lagged_sink", "lbm_init_fields", "lbm_step",
                      "lbm_moments", "lbm_integrals", "lbm_check", "lbm_get_state", "lbm_set_state",
                      "lbm_constants", "lbm_synchronize"):
             getattr(L, name).restype = C.c_int
@@ -183,6 +184,10 @@ def lbm_set_source(h, q3=None, force=None, n=None):
     if (q3 is not None and force is not None) and da != db:
         raise ValueError("q3 and force must both be host or both be device arrays")
     _check(h, lib().lbm_set_source(h, pa, pb, on_dev))
+
+
+def lbm_set_lagged_sink(h, conv_coef, T_inf):
+    _check(h, lib().lbm_set_lagged_sink(h, float(conv_coef), float(T_inf)))
 
 
 def lbm_init_fields(h, a=None, ux=None, uy=None, b=None, n=None):
@@ -360,6 +365,9 @@ class Solver:
 
     def set_source(self, q3=None, force=None):
         lbm_set_source(self.h, q3, force, n=self.n)
+
+    def set_lagged_sink(self, conv_coef, T_inf):
+        lbm_set_lagged_sink(self.h, conv_coef, T_inf)
 
     def init(self, a=None, ux=None, uy=None, b=None):
         lbm_init_fields(self.h, a, ux, uy, b, n=self.n)

@@ -1,0 +1,179 @@
+"""GPU vs FP64 CPU oracle: the paper's one-dimensional cases on the D1Q3-equivalent
+D2Q5 row (Sec. 4.1 fuse with the lagged convective sink, App. B advection-diffusion
+with wet-node ends), and wet-node sides on a 2D strip.
+
+FP64: T - T_ref to 1e-12 relative max-norm (1e-11 where T_ref is 25x smaller than T
+and 1500 steps accumulate contraction differences: 1500 x 2^-53 x 25 = 4e-12).  FP32
+deviation storage: each step rounds the stored deviations once, so after N steps the
+bound is N x 2^-24 relative (1.8e-4 at 3000 steps; 5e-5 to 6e-5 measured).  Full runs
+against the closed forms: the fuse's steady state within the paper's E2 = 0.0029 %,
+App. B within 1.5 x the paper's 0.030 %."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from _helpers import rel_max
+
+pytestmark = pytest.mark.gpu
+
+lbm = pytest.importorskip("paper_2302_04120_gb300.lbm")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_04120_gb300 import build
+    build.build()
+
+
+def _paper():
+    with open(GOLDEN) as fh:
+        return json.load(fh)
+
+
+def _fuse():
+    fp = _paper()["fuse_problem"]
+    Tinf = 273.15 + fp["T_inf_C"]
+    q3 = 16 * fp["I"] ** 2 * fp["res"] / (np.pi ** 2 * fp["d"] ** 4)
+    conv = 4 * fp["hbar"] / (fp["rho"] * fp["cp"] * fp["d"])
+    nx = int(round(fp["L"] / fp["dx"]))
+    params = dict(nx=nx, ny=1, flow=0, thermal=5, thermal_op=0, dx=fp["dx"], dt=fp["dt"], rho0=fp["rho"],
+                  cp=fp["cp"], k=fp["k"], T0=Tinf)
+    return fp, params, Tinf, q3, conv
+
+
+def _both(params, bcs, q3=None, conv=0.0, Tinf=0.0, steps=0, precision=0, moments_every=None):
+    o = oracle.Oracle(dict(params, conv_coef=conv, T_inf=Tinf))
+    s = lbm.Solver(params, precision=precision)
+    for side, tkind, tw, u in bcs:
+        ln = params["ny"] if side < 2 else params["nx"]
+        uw = np.concatenate([np.full(ln, u[0]), np.full(ln, u[1])])
+        o.set_bc(side, oracle.BC_PERIODIC, uw=uw, tkind=tkind, tw=np.full(ln, tw))
+        s.set_bc(side, lbm.LBM_BC_PERIODIC, uw, params.get("rho0", 1000.0), tkind, np.full(ln, tw))
+    if q3 is not None:
+        q = np.full(params["nx"] * params["ny"], q3)
+        o.set_source(q3=q)
+        s.set_source(q.reshape(params["ny"], params["nx"]))
+    if conv:
+        s.set_lagged_sink(conv, Tinf)
+    o.init()
+    s.init()
+    done = 0
+    for chunk in ([steps] if not moments_every else [moments_every] * (steps // moments_every)):
+        o.step(chunk)
+        s.step(chunk)
+        done += chunk
+        if moments_every:
+            s.moments()  # refreshes the lagged qdot: must not change what follows
+    return o, s
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_fuse_fp64_parity(op):
+    fp, params, Tinf, q3, conv = _fuse()
+    params = dict(params, thermal_op=op)
+    bcs = [(0, lbm.LBM_TBC_TEMP, Tinf, (0, 0)), (1, lbm.LBM_TBC_TEMP, Tinf, (0, 0))]
+    o, s = _both(params, bcs, q3=q3, conv=conv, Tinf=Tinf, steps=3000, moments_every=700 if op == 0 else None)
+    To, Tg = o.moments()["T"], s.moments()["T"]
+    assert rel_max(Tg - Tinf, To - Tinf) < 1e-12
+    s.close()
+
+
+def test_fuse_fp32():
+    fp, params, Tinf, q3, conv = _fuse()
+    bcs = [(0, lbm.LBM_TBC_TEMP, Tinf, (0, 0)), (1, lbm.LBM_TBC_TEMP, Tinf, (0, 0))]
+    o, s = _both(params, bcs, q3=q3, conv=conv, Tinf=Tinf, steps=3000, precision=1)
+    assert rel_max(s.moments()["T"] - Tinf, o.moments()["T"] - Tinf) < 3000 * 2.0 ** -24
+    s.close()
+
+
+def test_fuse_steady_against_closed_form():
+    """700000 steps (175 s of fuse time): E2 against the closed form (reading R18)
+    within the paper's 0.0029 %."""
+    fp, params, Tinf, q3, conv = _fuse()
+    s = lbm.Solver(params, precision=0)
+    for side in (0, 1):
+        s.set_bc(side, lbm.LBM_BC_PERIODIC, None, fp["rho"], lbm.LBM_TBC_TEMP, np.array([Tinf]))
+    s.set_source(np.full((1, params["nx"]), q3))
+    s.set_lagged_sink(conv, Tinf)
+    s.init()
+    s.step(700000)
+    T = s.moments()["T"][0]
+    s.close()
+    L, d = fp["L"], fp["d"]
+    x = (np.arange(params["nx"]) + 0.5) * fp["dx"]
+    m = np.sqrt(4 * fp["hbar"] / (fp["k"] * d))
+    Q = q3 * d / (4 * fp["hbar"])
+    ex = Tinf + Q - Q * np.cosh(m * (x - L / 2)) / np.cosh(m * L / 2)
+    assert oracle.e2_percent(ex, T) <= _paper()["fuse_steady_E2_percent"]["value"]
+
+
+def _app_b():
+    bp = _paper()["appB_problem"]
+    nx = int(round(bp["L"] / bp["dx"])) + 1
+    params = dict(nx=nx, ny=1, flow=0, thermal=5, thermal_op=0, dx=bp["dx"], dt=bp["dt"], rho0=bp["rho"],
+                  cp=bp["cp"], k=bp["k"], T0=bp["T0"], u_prescribed=(bp["u"], 0.0))
+    bcs = [(0, lbm.LBM_TBC_WETNODE, bp["T0"], (bp["u"], 0.0)), (1, lbm.LBM_TBC_WETNODE, bp["TL"], (bp["u"], 0.0))]
+    return bp, params, bcs
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 3000 * 2.0 ** -24)])
+def test_wet_node_app_b_parity(precision, tol):
+    bp, params, bcs = _app_b()
+    o, s = _both(params, bcs, steps=3000, precision=precision)
+    assert rel_max(s.moments()["T"] - bp["T0"], o.moments()["T"] - bp["T0"]) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_wet_node_strip_with_source_parity(op):
+    """37 x 6 strip periodic in y, wet-node x-sides at different T, uniform source,
+    prescribed oblique velocity: FP64 parity."""
+    params = dict(nx=37, ny=6, flow=0, thermal=5, thermal_op=op, dx=1e-3, dt=2e-3, rho0=1000.0, cp=4180.0,
+                  k=0.6, T0=300.0, u_prescribed=(2e-3, 1e-3))
+    bcs = [(0, lbm.LBM_TBC_WETNODE, 310.0, (2e-3, 1e-3)), (1, lbm.LBM_TBC_WETNODE, 300.0, (2e-3, 1e-3))]
+    o, s = _both(params, bcs, q3=5e6, steps=1500)
+    assert rel_max(s.moments()["T"] - 300.0, o.moments()["T"] - 300.0) < 1e-11
+    s.close()
+
+
+def test_app_b_wet_node_against_closed_form():
+    bp, params, bcs = _app_b()
+    s = lbm.Solver(params, precision=0)
+    for side, tkind, tw, u in bcs:
+        s.set_bc(side, lbm.LBM_BC_PERIODIC, np.array([u[0], u[1]]), bp["rho"], tkind, np.array([tw]))
+    s.init()
+    s.step(200000)
+    T = s.moments()["T"][0]
+    s.close()
+    x = np.arange(params["nx"]) * bp["dx"]
+    Pe = bp["rho"] * bp["cp"] * bp["u"] * bp["L"] / bp["k"]
+    ex = bp["T0"] + (bp["TL"] - bp["T0"]) * np.expm1(Pe * x / bp["L"]) / np.expm1(Pe)
+    assert oracle.e2_percent(ex, T) < 1.5 * _paper()["appB_E2_percent"]["value"]
+
+
+def test_rejections():
+    bp, params, bcs = _app_b()
+    s = lbm.Solver(params, precision=0)
+    with pytest.raises(lbm.LbmError):
+        s.set_bc(2, lbm.LBM_BC_PERIODIC, None, 1.0, lbm.LBM_TBC_WETNODE, np.zeros(params["nx"]))
+    s.close()
+    s = lbm.Solver(dict(params, ny=4, flow=9, thermal=9), precision=0)
+    with pytest.raises(lbm.LbmError):
+        s.set_bc(0, lbm.LBM_BC_WALL, None, 1.0, lbm.LBM_TBC_WETNODE, np.zeros(4))
+    s.close()
+    s = lbm.Solver(dict(params, thermal=0, flow=9), precision=0)
+    with pytest.raises(lbm.LbmError):
+        s.set_lagged_sink(1e-3, 300.0)
+    s.close()
+    s = lbm.Solver(dict(params, literal=1), precision=0)
+    with pytest.raises(lbm.LbmError):
+        s.set_lagged_sink(1e-3, 300.0)
+    s.set_lagged_sink(0.0, 300.0)
+    s.close()
