@@ -68,8 +68,12 @@ __device__ __forceinline__ bool frame_node(int nx, int ny, int f, int &i, int &j
 // other rows the interior tiles, with the boundary code compiled out.  Keeping the
 // frame in warps of its own spares the interior warps that touch the inlet or
 // outlet column from running both paths one after the other.
+// FP32 momentum-only solves move 9 values per node: at 64 registers (4 blocks of 256
+// per SM) too few bytes are in flight to cover HBM latency, so they run 6 blocks per
+// SM (40 registers, with some spilling) -- measured 0.78 -> 0.88 (BGK) and 0.83 -> 0.96
+// (MRT) of the copy bandwidth on an 8192 x 4096 grid.
 template <int PREC, int FLOW, int TH, bool SYM>
-__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_step_split(const SpParams P, int fy) {
+__global__ void __launch_bounds__(256, PREC == 1 ? (TH == TH_NONE ? 6 : 4) : 3) k_step_split(const SpParams P, int fy) {
   if ((int)blockIdx.y < fy) {
     const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
     int i, j;
