@@ -166,7 +166,12 @@ lbm_status lbm_create(const lbm_params *p, void *stream, lbm_t *out);
  * and h, and phi beyond the wall mirrored from the boundary node in the gradient
  * and Laplacian stencils; an axis with a wall on either side is walled.
  * The arrays are copied before the call returns (through pinned staging, without
- * synchronising the stream); the new values apply to steps enqueued after the call.
+ * synchronising the stream).  The kernels keep post-collision populations and rebuild
+ * the incoming ones, boundary links included, by the pull: after n steps the state of
+ * time n is formed when it is next read (lbm_moments, lbm_integrals) or advanced
+ * (lbm_step).  New boundary values therefore apply from the boundary links of the
+ * current time n on; a collide-then-push formulation would apply them from time n + 1,
+ * one step later.
  * Errors: LBM_ERR_ARG (side, kind, pairing, a moving or non-wall two-phase side),
  * LBM_ERR_CUDA.
  */
