@@ -106,3 +106,27 @@ def test_fuse_transient_against_ftcs():
         T = o.moments()["T"][0]
         Tf = ftcs_fuse(nx, fp["dx"], fp["dt"], alpha, q3 / (fp["rho"] * fp["cp"]), conv, Tinf, steps)
         assert oracle.e2_percent(Tf - Tinf, T - Tinf) < 0.05   # 0.020 % at 1 s, 0.005 % at 10 s measured
+
+
+@pytest.mark.parametrize("thermal,op", [(5, 0), (5, 1), (9, 0), (9, 1)])
+@pytest.mark.parametrize("conv", [0.0, 3.0])
+def test_thermal_collision_adds_dt_qdot(thermal, op, conv):
+    """Each thermal collision (BGK with the (1 - dt/2tau_T) source factor, Eq.
+    forcing_term_g; MRT with a zero rate on the zeroth moment and the source
+    dt (I - dt Lambda/2) M (w qdot)) adds exactly dt qdot to sum_i g_i at every node,
+    qdot = q'''/(rho0 c_p) - conv (T(t - dt) - T_inf).  The GPU's lagged sink rebuilds
+    T(t - dt) from the post-collision populations through this identity."""
+    rng = np.random.default_rng(7)
+    nx, ny, dx, dt = 6, 5, 1e-3, 2e-3
+    rho0, cp, k = 1000.0, 4180.0, 0.6
+    o = oracle.Oracle(dict(nx=nx, ny=ny, flow=9, flow_op=0, thermal=thermal, thermal_op=op, dx=dx, dt=dt,
+                           rho0=rho0, cp=cp, k=k, nu=1e-6, T0=300.0, conv_coef=conv, T_inf=295.0))
+    q3 = 1e6 * rng.standard_normal((ny, nx))
+    o.set_source(q3=q3)
+    T0 = 300.0 + rng.standard_normal((ny, nx))
+    o.init(None, 1e-3 * rng.standard_normal((ny, nx)), 1e-3 * rng.standard_normal((ny, nx)), T0)
+    g0 = o.dist("g")
+    o.step(1)
+    gs = o.dist("g", post=True)
+    qdot = q3 / (rho0 * cp) - conv * (T0 - 295.0)
+    np.testing.assert_allclose(gs.sum(0) - g0.sum(0), dt * qdot, rtol=1e-9, atol=1e-12)
