@@ -7,7 +7,8 @@ T_m the velocity-weighted bulk temperature (reading R22).
 Compared from column 8 on: over the first columns T_w - T_m crosses zero next to the
 fixed-temperature inlet column, where Nu is singular (-617 to 776 in the oracle's).
 Tolerances, relative L2 over x: FP64 1e-8 (50000 steps of rounding on T, amplified by
-T / (T_w - T_m) ~ 100 in Nu); FP32 deviation storage 1e-3."""
+T / (T_w - T_m) ~ 100 in Nu; 1.1e-10 measured); FP32 deviation storage 1e-4 (4.4e-6
+measured)."""
 import json
 import os
 
@@ -39,7 +40,7 @@ def _local_nusselt(T, u, q, k, dx, H):
     return lower, upper
 
 
-@pytest.mark.parametrize("prec,tol", [(lbm.LBM_FP64, 1e-8), (lbm.LBM_FP32DEV, 1e-3)])
+@pytest.mark.parametrize("prec,tol", [(lbm.LBM_FP64, 1e-8), (lbm.LBM_FP32DEV, 1e-4)])
 def test_channel_local_nusselt_against_oracle(prec, tol):
     with open(GOLDEN) as fh:
         g = json.load(fh)
