@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
 SOURCES = ["lbm_api.cu", "step_sp.cu", "step_sp_a.cu", "step_sp_b.cu", "step_sp_c.cu", "step_sp_d.cu", "step_tma.cu",
-           "step_tma_a.cu", "step_tma_b.cu", "step_mp.cu", "noalloc.cu", "batch.cu", "adjoint.cu", "probe.cu", "sink.cu"]
+           "step_tma_a.cu", "step_tma_b.cu", "step_mp.cu", "noalloc.cu", "adjoint.cu", "probe.cu", "sink.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
