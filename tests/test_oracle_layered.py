@@ -77,3 +77,23 @@ def test_walls_conserve_phase():
     assert abs(m["phi"].sum() - s0) / s0 < 1e-12
     # x-invariant inputs stay x-invariant (columns agree to rounding)
     assert np.abs(m["ux"] - m["ux"][:, :1]).max() <= 1e-12 * np.abs(m["ux"]).max()
+
+
+def test_property_table_consistent_with_printed_columns():
+    """The four fluid systems typed into the workloads (rho_g, rho_l, nu_g, nu_l of the
+    table of Sec. 4.3) reproduce the table's own derived columns: zeta = rho nu and the
+    density, viscosity and zeta ratios, to the printed rounding."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")) as fh:
+        table = json.load(fh)["two_phase_property_table"]
+    for name, fl in wl.TWO_PHASE_SYSTEMS.items():
+        row = table[name]
+        zg, zl = fl["rho_g"] * fl["nu_g"] / 1e-5, fl["rho_l"] * fl["nu_l"] / 1e-5
+        # 0.5 %: the printed inputs carry 2 to 5 significant digits (rho_g = 0.023 at
+        # 25 C alone leaves zeta_g uncertain by 2 %; measured 0.3 %)
+        assert abs(zg / row["zeta_g"] - 1) < 5e-3
+        assert abs(zl / row["zeta_l"] - 1) < 5e-3
+        assert abs(fl["rho_l"] / fl["rho_g"] / row["rho_ratio"] - 1) < 5e-3
+        assert abs(fl["nu_g"] / fl["nu_l"] / row["nu_ratio"] - 1) < 5e-3
+        assert abs(zl / zg / row["zeta_ratio"] - 1) < 5e-3
