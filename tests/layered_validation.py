@@ -67,6 +67,8 @@ def main():
             n0 = json.load(open(os.path.join(a.state_dir, tag + ".json")))["steps"]
         runs.append(dict(case=(name, dx, dt, z_op), tag=tag, w=w, s=s, st=st, ref=reference_for(w), n=n0,
                          prev=None, done=False))
+    with open(os.path.join(HERE, "golden", "paper_numbers.json")) as fh:
+        printed = json.load(fh)["layered_poiseuille_E2_percent"]
     out = open(a.out, "a") if a.out else None
     t0 = time.time()
     while not all(r["done"] for r in runs):
@@ -89,6 +91,10 @@ def main():
                 os.makedirs(a.state_dir, exist_ok=True)
                 r["s"].get_state().tofile(os.path.join(a.state_dir, r["tag"] + ".bin"))
                 json.dump(dict(steps=r["n"]), open(os.path.join(a.state_dir, r["tag"] + ".json"), "w"))
+            if abs(dx - 1.25e-6) < 1e-12 and name in printed:
+                rec["paper_E2_pct"] = printed[name]
+            elif name == "sat_water_100C":
+                rec["paper_E2_pct"] = printed["refinement_sat_water_100C"].get(f"dx_{dx:g}_dt_{dt:g}")
             stop = (not ok or (ch is not None and ch < 1e-6) or r["n"] >= a.max_steps
                     or time.time() - t0 > a.max_secs)
             if stop:
