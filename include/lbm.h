@@ -326,7 +326,7 @@ void lbm_destroy(lbm_t h);
  *                    cannot use the legacy default stream).  Errors as lbm_create.
  *  lbm_batch_step    advance every channel n steps; all channels must be initialised and
  *                    in step.  Asynchronous on the batch stream.  Errors: LBM_ERR_STATE,
- *                    LBM_ERR_CUDA.
+ *                    LBM_ERR_ARG (a channel with a lagged sink), LBM_ERR_CUDA.
  *  lbm_batch_autotune time candidate tile shapes (32..256 threads) and grid sizes (1..16
  *                    blocks per SM) on the next step without advancing the solution; keeps
  *                    the fastest; out_cfg (may be NULL) receives {tile_x, tile_y, grid}.

@@ -1026,6 +1026,8 @@ extern "C" lbm_status lbm_batch_step(lbm_batch_t b, long n) {
   if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
   if (n < 0) return bfail(b, LBM_ERR_ARG, "n must be >= 0");
   if (n == 0) return LBM_OK;
+  for (int k = 0; k < b->n; k++)  // the batched launch does not refresh a lagged qdot
+    if (b->ch[k]->sink_conv != 0.0) return bfail(b, LBM_ERR_ARG, "channel %d has a lagged sink", k);
   lbm_status st = batch_tiles(b, b->bx, b->by);
   if (st != LBM_OK) return st;
   int cur, pre;
