@@ -97,3 +97,25 @@ def test_property_table_consistent_with_printed_columns():
         assert abs(fl["rho_l"] / fl["rho_g"] / row["rho_ratio"] - 1) < 5e-3
         assert abs(fl["nu_g"] / fl["nu_l"] / row["nu_ratio"] - 1) < 5e-3
         assert abs(zl / zg / row["zeta_ratio"] - 1) < 5e-3
+
+
+def test_quadrature_reference_sharp_interface_limit():
+    """The quadrature reference itself: as W -> 0 the profile tends to the two-layer
+    closed form (zeta_l below H/2, zeta_g above): zeta u' = -F (y - y*) with
+    y* = [h^2/(2 zeta_l) + (H^2 - h^2)/(2 zeta_g)] / [h/zeta_l + (H - h)/zeta_g], h = H/2,
+    u = F/zeta_l (y* y - y^2/2) below and u(H) = 0 from above."""
+    from _layered import layered_reference
+    H, F, zl, zg = 0.5e-3, 0.36, 8.9e-4, 1.8e-5
+    h = H / 2
+    y = np.linspace(0.0, H, 201)[1:-1]
+    ystar = (h * h / (2 * zl) + (H * H - h * h) / (2 * zg)) / (h / zl + (H - h) / zg)
+    below = F / zl * (ystar * y - y * y / 2)
+    above = F / zg * ((H * H - y * y) / 2 - ystar * (H - y))
+    exact = np.where(y < h, below, above)
+    errs = []
+    for W in (H / 200, H / 2000, H / 20000):
+        u = layered_reference(y, H, W, F, zl, zg, n=2000001)
+        errs.append(np.abs(u - exact).max() / exact.max())
+    # first order in W (the smeared viscosity jump): 3.2e-2, 3.3e-3, 3.3e-4 measured
+    assert errs[2] < 5e-4
+    assert 8.0 < errs[0] / errs[1] < 12.0 and 8.0 < errs[1] / errs[2] < 12.0
