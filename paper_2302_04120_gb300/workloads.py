@@ -195,7 +195,7 @@ def bubble(n=512, R_cells=64.0, W_cells=5.0, steps=100000, dx=5e-6, dt=1e-7, mob
 # ---------------------------------------------------------------------------
 # Workload 3b: layered two-phase Poiseuille flow (Sec. 4.4)
 # ---------------------------------------------------------------------------
-def layered_poiseuille(fluid="air_water_25C", H=0.5e-3, dx=1.25e-6, dt=1.25e-7, nx=10, W=25e-6,
+def layered_poiseuille(fluid="air_water_25C", H=0.5e-3, dx=1.25e-6, dt=1.25e-8, nx=10, W=25e-6,
                        mobility=1e-5, u_c=1e-4, steps=0, z_op=1, literal=0):
     """Channel of height H between resting walls (y sides), periodic in x, liquid in
     the lower half and gas in the upper half.
@@ -204,8 +204,10 @@ def layered_poiseuille(fluid="air_water_25C", H=0.5e-3, dx=1.25e-6, dt=1.25e-7, 
     liquid below), so zeta = phi zeta_l + (1 - phi) zeta_g is the profile of
     Eq. viscosity_prof; nu = zeta/rho (nu_rule 1); body force F_x = u_c (zeta_l +
     zeta_g)/H^2; u = 0 and p = 0 at t = 0.  The paper uses 10 columns, W = 25 um,
-    M = 1e-5 m^2/s, dx = 1.25 um and dt = 1.25e-7 s (1.25e-8 s in its refinement
-    study), D2Q5 h with BGK and MRT for the momentum (z) equation.
+    M = 1e-5 m^2/s and dx = 1.25 um, D2Q5 h with BGK and MRT for the momentum (z)
+    equation.  It states dt = 1.25e-7 s, and 1.25e-8 s at the same dx in its refinement
+    study; at the real surface tension 1.25e-7 s diverges within ~100 steps, so the
+    default is 1.25e-8 s.
     """
     fl = TWO_PHASE_SYSTEMS[fluid] if isinstance(fluid, str) else fluid
     ny = int(round(H / dx))
