@@ -235,8 +235,9 @@ lbm_status lbm_step(lbm_t h, long n);
 lbm_status lbm_autotune(lbm_t h, int out_block[2]);
 
 /*
- * FMA-rate probe (no counterpart in the paper: the arithmetic roofline of the FP64
- * and FP32 forms on the current device).  Runs eight independent chains of fused
+ * DIAGNOSTIC, not part of the solver: FMA-rate probe used by the benchmark to state
+ * the arithmetic roofline of the FP64 and FP32 forms on the current device (no
+ * counterpart in the paper).  Runs eight independent chains of fused
  * multiply-adds per thread on every SM and returns the rate in GFLOP/s (2 flops per
  * FMA) in *gflops.  Synchronous; allocates and frees its own scratch.
  * precision: LBM_FP64 or LBM_FP32DEV.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA (text in
@@ -280,11 +281,15 @@ long lbm_steps_done(lbm_t h);
 lbm_status lbm_moments(lbm_t h, unsigned mask, double *out, int on_device);
 
 /*
- * Integrals with deterministic FP64 reductions (fixed tree order):
- *  out[0] = sum rho dx^2 (mass per unit depth, kg/m), out[1] = sum phi (two-phase,
- *  else 0), out[2] = max |u| [m/s], out[3] = number of cells with a non-finite value
- *  or |u| >= c.  out is host memory of 4 doubles; the call synchronises the stream.
- * Errors: LBM_ERR_STATE, LBM_ERR_CUDA.
+ * Integrals with deterministic FP64 reductions (fixed tree order).  A bad cell is one
+ * with a non-finite rho, u, T (thermal) or p (two-phase), or with |u| >= c; it is
+ * counted in out[3] and adds nothing to out[0..2]:
+ *  out[0] = sum of rho dx^2 over the healthy cells (mass per unit depth, kg/m),
+ *  out[1] = sum of phi over the healthy cells (two-phase, else 0),
+ *  out[2] = max |u| over the healthy cells [m/s], out[3] = number of bad cells.
+ * out is host memory of 4 doubles; the call synchronises the stream.
+ * Errors: LBM_ERR_STATE, LBM_ERR_CUDA, LBM_ERR_TIMEOUT (a TMA-staged step gave up
+ * waiting for a staged copy since the last call; out is still written).
  */
 lbm_status lbm_integrals(lbm_t h, double out[4]);
 
@@ -372,11 +377,15 @@ lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const double *T_targ
  * whole device, under a framework allocator that forbids foreign allocations, or
  * where an allocation's implicit device synchronisation is not allowed).
  *
- * Computes the same four values as lbm_integrals, with the same deterministic
- * two-stage FP64 reduction:
- *   out4[0] = sum rho dx^2, out4[1] = sum phi (0 when phi is NULL),
- *   out4[2] = max |u| over finite cells, out4[3] = number of cells with a
- *   non-finite value or |u| >= c.
+ * Computes the four quantities of lbm_integrals from the given fields, with a
+ * deterministic two-stage FP64 reduction (fixed order, so repeated calls agree bit
+ * for bit; the summation order differs from lbm_integrals', so the two agree to
+ * rounding).  A bad cell has a non-finite rho, u or phi, or |u| >= c (there is no
+ * temperature field here, so a non-finite T is not seen); it is counted and adds
+ * nothing to the sums or the maximum:
+ *   out4[0] = sum of rho dx^2 over the healthy cells, out4[1] = sum of phi over the
+ *   healthy cells (0 when phi is NULL), out4[2] = max |u| over the healthy cells,
+ *   out4[3] = number of bad cells.
  * rho, ux, uy (and phi, or NULL): device arrays of nx*ny doubles, row-major;
  * out4: device array of 4 doubles written by the call; dx [m]; c = dx/dt [m/s];
  * stream: a cudaStream_t or NULL.  Asynchronous on that stream; it allocates
@@ -390,7 +399,8 @@ lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const double *T_targ
  * current; make that first call before any stream capture.  All calls share the
  * array and each call rewrites every entry it reads, so calls that overlap on the
  * GPU (different streams, or different host threads on one device) race: order
- * them on one stream.
+ * them on one stream.  The looked-up address is kept for the life of the process:
+ * do not call this after a cudaDeviceReset of a device it has already run on.
  * Errors: LBM_ERR_ARG (NULL pointer, sizes), LBM_ERR_CUDA.
  */
 #define LBM_NOALLOC_MAX_BLOCKS 4096

@@ -50,8 +50,10 @@ __global__ void __launch_bounds__(kThreads) k_field_partials(const double *rho, 
       const double umag = sqrt(u * u + w * w);
       const double ph = phi ? phi[i] : 0.0;
       const bool bad = !isfinite(r) || !isfinite(umag) || !isfinite(ph) || umag >= ulim;
-      v[0] += r * area;
-      v[1] += ph;
+      // a bad cell is counted and adds nothing to the sums or the maximum (as in
+      // lbm_integrals)
+      v[0] += bad ? 0.0 : r * area;
+      v[1] += bad ? 0.0 : ph;
       v[2] = fmax(v[2], bad ? 0.0 : umag);
       v[3] += bad ? 1.0 : 0.0;
     }

@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(256) k_moments(const SpParams P, unsigned mask
 // FP64 from the working-precision moments (no square root per node), and a health
 // flag; warp sums in a fixed shuffle tree; per-block FP64 partials (sum of
 // rho - rho0, 0, max |u|^2, bad-node count); a one-block final pass in a fixed order
-// adds N rho0 and takes the one square root.
+// adds (N - bad) rho0 and takes the one square root.  Bad nodes (a non-finite value or
+// |u| >= c) add nothing to the mass or to max |u|: they are only counted.
 __device__ __forceinline__ void block_partials(double drho, double u2, int bad, double *out) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -213,10 +214,10 @@ __device__ __forceinline__ void block_partials(double drho, double u2, int bad, 
 }
 
 // Fixed-order sum of the nb per-block partials by one 256-thread block: thread t sums
-// partials t, t + 256, ... in order, then a fixed tree.  mass = (N rho0 + sum (rho -
-// rho0)) dx^2, max |u| = sqrt(max |u|^2).
-__device__ __forceinline__ void final_reduce(const double *partials, int nb, double n_rho0, double area,
-                                             double *out4) {
+// partials t, t + 256, ... in order, then a fixed tree.  mass = ((N - bad) rho0 +
+// sum over healthy nodes of (rho - rho0)) dx^2, max |u| = sqrt(max |u|^2).
+__device__ __forceinline__ void final_reduce(const double *partials, int nb, double n_rho0, double rho0,
+                                             double area, double *out4) {
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
   double a = 0, b = 0, mx = 0, cnt = 0;
   for (int k = t; k < nb; k += 256) {
@@ -238,7 +239,7 @@ __device__ __forceinline__ void final_reduce(const double *partials, int nb, dou
     __syncthreads();
   }
   if (t == 0) {
-    out4[0] = (n_rho0 + sh[0][0]) * area;
+    out4[0] = (n_rho0 - sh[3][0] * rho0 + sh[0][0]) * area;
     out4[1] = sh[1][0];
     out4[2] = sqrt(sh[2][0]);
     out4[3] = sh[3][0];
@@ -250,6 +251,7 @@ __device__ __forceinline__ void final_reduce(const double *partials, int nb, dou
 template <int PREC, int FLOW, int TH, bool SYM>
 __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *partials, double n_rho0, double area,
                                                    double *out4, unsigned *counter) {
+  // n_rho0 = N rho0 of the whole grid; final_reduce removes rho0 per bad node
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
   __syncthreads();
   if (last) {
     __threadfence();
-    final_reduce(partials, (int)nb, n_rho0, area, out4);
+    final_reduce(partials, (int)nb, n_rho0, P.rho0, area, out4);
     if (threadIdx.x == 0 && threadIdx.y == 0) *counter = 0u;
   }
 }

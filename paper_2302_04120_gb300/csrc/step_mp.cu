@@ -390,8 +390,9 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
       const double ux = (double)m.ux, uy = (double)m.uy, rho = (double)m.rho, p = (double)m.p;
       const double umag = sqrt(ux * ux + uy * uy);
       const bool bad = !isfinite(rho) || !isfinite(umag) || !isfinite(p) || umag >= P.c;
-      red[0] = rho * P.dx * P.dx;
-      red[1] = (double)m.phi;
+      // a bad node (non-finite, or |u| >= c) is counted and adds nothing else
+      red[0] = bad ? 0.0 : rho * P.dx * P.dx;
+      red[1] = bad ? 0.0 : (double)m.phi;
       red[2] = bad ? 0.0 : umag;
       red[3] = bad ? 1.0 : 0.0;
     }

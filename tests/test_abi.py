@@ -94,3 +94,28 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(lbm, "_lib", None)
     with pytest.raises(RuntimeError):
         lbm.lib()
+
+
+def test_noalloc_binding_checks_arguments_without_gpu():
+    """The binding of lbm_field_integrals_noalloc refuses tensors the kernel would read
+    past (wrong dtype, strided, too short, out4 too short) or that are not on a CUDA
+    device, before any C call: these run on a CPU-only host."""
+    torch = pytest.importorskip("torch")
+    from paper_2302_04120_gb300 import lbm
+    nx, ny = 6, 5
+    good = torch.zeros(nx * ny, dtype=torch.float64)
+    out = torch.zeros(4, dtype=torch.float64)
+    cases = [
+        ((good.float(), good, good, None, out), "float64"),
+        ((good, torch.zeros(2 * nx * ny, dtype=torch.float64)[::2], good, None, out), "contiguous"),
+        ((good, good, good[:-1], None, out), "values"),
+        ((good, good, good, good[:3], out), "values"),
+        ((good, good, good, None, out[:3]), "values"),
+        ((good, good, good, None, [0.0] * 4), "torch tensor"),
+        ((good, good, good, None, out), "CUDA"),
+    ]
+    for (rho, ux, uy, phi, o), msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            lbm.lbm_field_integrals_noalloc(rho, ux, uy, phi, nx, ny, 1e-6, 1.0, o)
+    with pytest.raises(ValueError):
+        lbm.lbm_field_integrals_noalloc(good, good, good, None, 0, ny, 1e-6, 1.0, out)

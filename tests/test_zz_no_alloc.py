@@ -84,3 +84,37 @@ def test_noalloc_rejects_oversize_grid():
     st = lbm.lib().lbm_field_integrals_noalloc(fake, fake, fake, None, big_nx, big_ny, 1.0, 1.0, fake, None)
     assert st == lbm.LBM_ERR_ARG
     assert "static scratch limit" in lbm.lbm_last_error(None)
+
+
+@pytest.mark.parametrize("two_phase", [False, True])
+def test_bad_cell_excluded_everywhere(two_phase):
+    """One non-finite population planted through lbm_set_state: lbm_integrals counts
+    the cell and leaves it out of the mass and the phase sum; the allocation-free call
+    on the moments of the same state gives the same four values (to rounding), and the
+    mass equals the sum over the healthy cells of the moments."""
+    import torch
+    if two_phase:
+        w = wl.bubble(n=48, ny=40, R_cells=10.0, W_cells=4.0, steps=20)
+    else:
+        w = wl.channel(nx=64, ny=24, steps=20, Re=100 * 24 / 256)
+    nx, ny = w["params"]["nx"], w["params"]["ny"]
+    s = run_gpu(w, 0)
+    st = s.get_state().view(np.float64).copy()
+    st[5 * nx * ny + 3 * nx + 7] = np.nan          # plane 5, node (7, 3)
+    s.set_state(st.view(np.uint8))
+    ref = s.integrals()
+    assert ref[3] == 1 and np.all(np.isfinite(ref[:3]))
+    m = torch.empty((4, ny, nx), dtype=torch.float64, device="cuda")
+    lbm.lbm_moments(s.h, lbm.LBM_RHO | lbm.LBM_UX | lbm.LBM_UY | lbm.LBM_PHI, m)
+    host = m.cpu().numpy()
+    healthy = np.isfinite(host[0]) & np.isfinite(host[1]) & np.isfinite(host[2])
+    assert healthy.sum() == nx * ny - 1
+    dx = w["params"]["dx"]
+    assert abs(ref[0] - host[0][healthy].sum() * dx * dx) <= 1e-12 * ref[0]
+    if two_phase:
+        assert abs(ref[1] - host[3][healthy].sum()) <= 1e-12 * ref[1]
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    phi = m[3] if two_phase else None
+    assert lbm.lbm_field_integrals_noalloc(m[0], m[1], m[2], phi, nx, ny, dx, s.constants()["c"], out) == 0
+    torch.cuda.synchronize()
+    _check_pair(ref, out.cpu().numpy().tolist())
