@@ -21,6 +21,13 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the same source built with -DORACLE_EXTENDED: every step in long double (80-bit
+# extended on x86-64, binary128 on AArch64), to measure the FP64 rounding floor
+_LIB_EXT = os.path.join(_HERE, "liboracle_ext.so")
+# the same source built as C++ with -DORACLE_DUAL: every step in forward-mode dual
+# numbers (oracle/dual.h), giving exact directional derivatives of the forward map
+_LIB_DUAL = os.path.join(_HERE, "liboracle_dual.so")
+_DUAL_H = os.path.join(_HERE, "dual.h")
 
 BC_PERIODIC, BC_WALL, BC_VELOCITY, BC_PRESSURE, BC_SYMMETRY = 0, 1, 2, 3, 4
 TBC_NONE, TBC_FLUX, TBC_TEMP, TBC_OUTFLOW, TBC_SYMMETRY, TBC_WETNODE = 0, 1, 2, 3, 4, 5
@@ -43,39 +50,50 @@ class OrcParams(C.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP over cells)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
-               _SRC, "-o", _LIB + ".tmp", "-lm"]
+def build(force: bool = False, extended: bool = False, dual: bool = False) -> str:
+    """Compile the oracle (no FMA contraction, OpenMP over cells): FP64 with gcc, long
+    double with ``extended``, or forward-mode dual numbers (g++) with ``dual``."""
+    out = _LIB_DUAL if dual else _LIB_EXT if extended else _LIB
+    src_time = max(os.path.getmtime(_SRC), os.path.getmtime(_DUAL_H))
+    if force or not os.path.exists(out) or os.path.getmtime(out) < src_time:
+        if dual:
+            cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+                   "-x", "c++", "-DORACLE_DUAL", "-I", _HERE, _SRC, "-o", out + ".tmp", "-lm"]
+        else:
+            cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+                   *(["-DORACLE_EXTENDED"] if extended else []), _SRC, "-o", out + ".tmp", "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+        os.replace(out + ".tmp", out)
+    return out
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = C.CDLL(build())
+def lib(extended: bool = False, dual: bool = False):
+    key = "dual" if dual else "ext" if extended else "fp64"
+    if key not in _libs:
+        L = C.CDLL(build(extended=extended, dual=dual))
         d = C.POINTER(C.c_double)
-        _lib.orc_create.restype = C.c_void_p
-        _lib.orc_create.argtypes = [C.POINTER(OrcParams)]
-        _lib.orc_destroy.argtypes = [C.c_void_p]
-        _lib.orc_constants.argtypes = [C.c_void_p, d]
-        _lib.orc_matrix.argtypes = [C.c_void_p, C.c_int, d]
-        _lib.orc_set_bc.argtypes = [C.c_void_p, C.c_int, C.c_int, d, C.c_double, C.c_int, d]
-        _lib.orc_set_source.argtypes = [C.c_void_p, d, d]
-        _lib.orc_init.argtypes = [C.c_void_p, d, d, d, d]
-        _lib.orc_step.argtypes = [C.c_void_p, C.c_long]
-        _lib.orc_moments.argtypes = [C.c_void_p, d, d, d, d, d, d]
-        _lib.orc_get_dist.argtypes = [C.c_void_p, C.c_int, C.c_int, d]
-        _lib.orc_set_dist.argtypes = [C.c_void_p, C.c_int, d]
-        _lib.orc_steps.restype = C.c_long
-        _lib.orc_steps.argtypes = [C.c_void_p]
-    return _lib
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(OrcParams)]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_constants.argtypes = [C.c_void_p, d]
+        L.orc_matrix.argtypes = [C.c_void_p, C.c_int, d]
+        L.orc_set_bc.argtypes = [C.c_void_p, C.c_int, C.c_int, d, C.c_double, C.c_int, d]
+        L.orc_set_source.argtypes = [C.c_void_p, d, d]
+        L.orc_init.argtypes = [C.c_void_p, d, d, d, d]
+        L.orc_step.argtypes = [C.c_void_p, C.c_long]
+        L.orc_moments.argtypes = [C.c_void_p, d, d, d, d, d, d]
+        L.orc_get_dist.argtypes = [C.c_void_p, C.c_int, C.c_int, d]
+        L.orc_set_dist.argtypes = [C.c_void_p, C.c_int, d]
+        L.orc_steps.restype = C.c_long
+        L.orc_steps.argtypes = [C.c_void_p]
+        if dual:
+            L.orc_seed.argtypes = [C.c_void_p, C.c_double, d, d]
+            L.orc_tangent.argtypes = [C.c_void_p, d, d, d]
+        _libs[key] = L
+    return _libs[key]
 
 
 def _ptr(a):
@@ -101,14 +119,19 @@ _DEFAULTS = dict(flow=9, flow_op=0, thermal=0, thermal_op=0, phase=0, z_op=1, nu
                  conv_coef=0.0, T_inf=0.0, gravity=(0.0, 0.0), beta_exp=0.0, T_ref=0.0, rho_ref=0.0)
 
 
+
 class Oracle:
     """One oracle solve.  ``params`` is a dict of SI quantities (see ``OrcParams``).
 
     Grid fields are numpy arrays of shape (ny, nx) (row j = y index).
-    Distributions come back as (q, ny, nx).
+    Distributions come back as (q, ny, nx).  ``extended=True`` runs the same steps
+    in long double; ``dual=True`` in forward-mode dual numbers (``seed`` and
+    ``tangent``); inputs and outputs stay FP64 in every build.
     """
 
-    def __init__(self, params: dict):
+    def __init__(self, params: dict, extended: bool = False, dual: bool = False):
+        self._L = lib(extended, dual)
+        self.extended, self.dual = extended, dual
         full = dict(_DEFAULTS)
         full.update({k: v for k, v in params.items() if k in _PARAM_KEYS})
         self.p = full
@@ -122,13 +145,13 @@ class Oracle:
                 setattr(s, k, v)
         self._s = s
         self.nx, self.ny = int(full["nx"]), int(full["ny"])
-        self.h = lib().orc_create(C.byref(s))
+        self.h = self._L.orc_create(C.byref(s))
         if not self.h:
             raise MemoryError("oracle allocation failed")
 
     def close(self):
         if self.h:
-            lib().orc_destroy(self.h)
+            self._L.orc_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -140,13 +163,13 @@ class Oracle:
     # --- set-up -----------------------------------------------------------
     def constants(self):
         out = np.zeros(5)
-        lib().orc_constants(self.h, _ptr(out))
+        self._L.orc_constants(self.h, _ptr(out))
         return dict(c=out[0], cs2=out[1], tau=out[2], tauT=out[3], tauphi=out[4])
 
     def matrix(self, which: int):
         n = 81 if which in (0, 1, 4) else 25
         out = np.zeros(n)
-        lib().orc_matrix(self.h, which, _ptr(out))
+        self._L.orc_matrix(self.h, which, _ptr(out))
         m = int(round(np.sqrt(n)))
         return out.reshape(m, m)
 
@@ -155,45 +178,63 @@ class Oracle:
         uw = _arr(uw, 2 * ln)
         tw = _arr(tw, ln)
         rw = self.p["rho0"] if rho_w is None else rho_w
-        lib().orc_set_bc(self.h, side, kind, _ptr(uw), float(rw), tkind, _ptr(tw))
+        self._L.orc_set_bc(self.h, side, kind, _ptr(uw), float(rw), tkind, _ptr(tw))
 
     def set_source(self, q3=None, force=None):
         n = self.nx * self.ny
         self._q3 = _arr(q3, n)
         self._force = _arr(force, 2 * n)
-        lib().orc_set_source(self.h, _ptr(self._q3), _ptr(self._force))
+        self._L.orc_set_source(self.h, _ptr(self._q3), _ptr(self._force))
 
     def init(self, a=None, ux=None, uy=None, b=None):
         n = self.nx * self.ny
-        lib().orc_init(self.h, _ptr(_arr(a, n)), _ptr(_arr(ux, n)), _ptr(_arr(uy, n)),
+        self._L.orc_init(self.h, _ptr(_arr(a, n)), _ptr(_arr(ux, n)), _ptr(_arr(uy, n)),
                        _ptr(_arr(b, n)))
 
     # --- stepping and output ----------------------------------------------
     def step(self, n: int):
-        lib().orc_step(self.h, int(n))
+        self._L.orc_step(self.h, int(n))
 
     @property
     def steps(self):
-        return lib().orc_steps(self.h)
+        return self._L.orc_steps(self.h)
 
     def moments(self):
         shp = (self.ny, self.nx)
         out = {k: np.zeros(shp) for k in ("rho", "ux", "uy", "T", "p", "phi")}
-        lib().orc_moments(self.h, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "T", "p", "phi")])
+        self._L.orc_moments(self.h, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "T", "p", "phi")])
         return out
 
     def dist(self, which: str, post: bool = False):
         w = {"f": 0, "g": 1, "h": 2, "z": 3}[which]
         q = 9 if w in (0, 3) or (w == 1 and int(self.p["thermal"]) == 9) else 5
         out = np.zeros((q, self.ny, self.nx))
-        lib().orc_get_dist(self.h, w, int(post), _ptr(out))
+        self._L.orc_get_dist(self.h, w, int(post), _ptr(out))
+        return out
+
+    def seed(self, dnu=0.0, dq3=None, dqwall=None):
+        """Direction of one derivative (dual build): d nu, a direction of the heat-source
+        field (ny, nx) and one of the wall flux (2, nx) for the y- and y+ sides.  Call
+        after set_bc / set_source and before step."""
+        assert self.dual
+        n = self.nx * self.ny
+        self._dq3 = _arr(dq3, n)
+        self._dqw = _arr(dqwall, 2 * self.nx)
+        self._L.orc_seed(self.h, float(dnu), _ptr(self._dq3), _ptr(self._dqw))
+
+    def tangent(self):
+        """Derivatives of u_x, u_y and T along the seeded direction (dual build)."""
+        assert self.dual
+        shp = (self.ny, self.nx)
+        out = {k: np.zeros(shp) for k in ("ux", "uy", "T")}
+        self._L.orc_tangent(self.h, *[_ptr(out[k]) for k in ("ux", "uy", "T")])
         return out
 
     def set_dist(self, which: str, arr):
         w = {"f": 0, "g": 1, "h": 2, "z": 3}[which]
         q = 9 if w in (0, 3) or (w == 1 and int(self.p["thermal"]) == 9) else 5
         a = _arr(arr, q * self.nx * self.ny)
-        lib().orc_set_dist(self.h, w, _ptr(a))
+        self._L.orc_set_dist(self.h, w, _ptr(a))
 
 
 def e2_percent(ref, num):

@@ -48,9 +48,32 @@
  * both): c = {0, +x, +y, -x, -y}, w = {1/3, 1/6, 1/6, 1/6, 1/6}, c_s^2 = c^2/3.
  * Its MRT matrix rows are (1, c_x, c_y, 5|c|^2-4c^2, c_x^2-c_y^2), scaled by c^n.
  */
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+
+/* Working precision.  The oracle is FP64 (real = double).  Built with
+   -DORACLE_EXTENDED it runs the same steps in long double (80-bit extended on
+   x86-64, IEEE binary128 on AArch64): the tests use that build to measure the
+   FP64 rounding floor of long runs.  Built as C++ with -DORACLE_DUAL it runs them
+   in forward-mode dual numbers, which give exact directional derivatives of the
+   discrete forward map (the reference for the adjoint gradients).  Inputs and
+   outputs stay double in every build. */
+#ifdef __cplusplus
+#define ORC_API extern "C"
+#else
+#define ORC_API
+#endif
+
+#if defined(ORACLE_DUAL)
+/* C++ build: forward-mode dual numbers (dual.h), for reference derivatives */
+#include "dual.h"
+typedef dual real;
+#elif defined(ORACLE_EXTENDED)
+typedef long double real;
+#else
+typedef double real;
+#endif
 
 /* ------------------------------------------------------------------------- */
 /* Public parameter block (mirrored field by field by the ctypes wrapper).    */
@@ -86,15 +109,15 @@ enum { TBC_NONE = 0, TBC_FLUX = 1, TBC_TEMP = 2, TBC_OUTFLOW = 3, TBC_SYMMETRY =
 /* D2Q9, Eqs. velocity_D2Q9 / weights_D2Q9 */
 static const int CX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+static const real W9[9] = {(real)4 / 9, (real)1 / 9, (real)1 / 9, (real)1 / 9, (real)1 / 9,
+                             (real)1 / 36, (real)1 / 36, (real)1 / 36, (real)1 / 36};
 /* D2Q5 (extension) */
 static const int CX5[5] = {0, 1, 0, -1, 0};
 static const int CY5[5] = {0, 0, 1, 0, -1};
-static const double W5[5] = {1.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+static const real W5[5] = {(real)1 / 3, (real)1 / 6, (real)1 / 6, (real)1 / 6, (real)1 / 6};
 
 /* Lattice transformation matrix, Eq. M_matrix (rows rho,e,eps,jx,qx,jy,qy,pxx,pxy) */
-static const double M9_LATTICE[9][9] = {
+static const real M9_LATTICE[9][9] = {
     {1, 1, 1, 1, 1, 1, 1, 1, 1},
     {-4, -1, -1, -1, -1, 2, 2, 2, 2},
     {4, -2, -2, -2, -2, 1, 1, 1, 1},
@@ -111,19 +134,19 @@ static const int ORDER9[9] = {0, 2, 4, 1, 3, 1, 3, 2, 2};
    Eq. Minv_matrix_dim divides column k by c^(order k).  One printed entry is
    corrected: row i = 2, column q_y is printed +1/6 but M M^-1 = I needs -1/6
    (reading R27; the test-suite checks both facts). */
-static const double MINV9_LATTICE[9][9] = {
-    {1.0 / 9, -1.0 / 9, 1.0 / 9, 0, 0, 0, 0, 0, 0},
-    {1.0 / 9, -1.0 / 36, -1.0 / 18, 1.0 / 6, -1.0 / 6, 0, 0, 1.0 / 4, 0},
-    {1.0 / 9, -1.0 / 36, -1.0 / 18, 0, 0, 1.0 / 6, -1.0 / 6, -1.0 / 4, 0},
-    {1.0 / 9, -1.0 / 36, -1.0 / 18, -1.0 / 6, 1.0 / 6, 0, 0, 1.0 / 4, 0},
-    {1.0 / 9, -1.0 / 36, -1.0 / 18, 0, 0, -1.0 / 6, 1.0 / 6, -1.0 / 4, 0},
-    {1.0 / 9, 1.0 / 18, 1.0 / 36, 1.0 / 6, 1.0 / 12, 1.0 / 6, 1.0 / 12, 0, 1.0 / 4},
-    {1.0 / 9, 1.0 / 18, 1.0 / 36, -1.0 / 6, -1.0 / 12, 1.0 / 6, 1.0 / 12, 0, -1.0 / 4},
-    {1.0 / 9, 1.0 / 18, 1.0 / 36, -1.0 / 6, -1.0 / 12, -1.0 / 6, -1.0 / 12, 0, 1.0 / 4},
-    {1.0 / 9, 1.0 / 18, 1.0 / 36, 1.0 / 6, 1.0 / 12, -1.0 / 6, -1.0 / 12, 0, -1.0 / 4}};
+static const real MINV9_LATTICE[9][9] = {
+    {(real)1 / 9, -(real)1 / 9, (real)1 / 9, 0, 0, 0, 0, 0, 0},
+    {(real)1 / 9, -(real)1 / 36, -(real)1 / 18, (real)1 / 6, -(real)1 / 6, 0, 0, (real)1 / 4, 0},
+    {(real)1 / 9, -(real)1 / 36, -(real)1 / 18, 0, 0, (real)1 / 6, -(real)1 / 6, -(real)1 / 4, 0},
+    {(real)1 / 9, -(real)1 / 36, -(real)1 / 18, -(real)1 / 6, (real)1 / 6, 0, 0, (real)1 / 4, 0},
+    {(real)1 / 9, -(real)1 / 36, -(real)1 / 18, 0, 0, -(real)1 / 6, (real)1 / 6, -(real)1 / 4, 0},
+    {(real)1 / 9, (real)1 / 18, (real)1 / 36, (real)1 / 6, (real)1 / 12, (real)1 / 6, (real)1 / 12, 0, (real)1 / 4},
+    {(real)1 / 9, (real)1 / 18, (real)1 / 36, -(real)1 / 6, -(real)1 / 12, (real)1 / 6, (real)1 / 12, 0, -(real)1 / 4},
+    {(real)1 / 9, (real)1 / 18, (real)1 / 36, -(real)1 / 6, -(real)1 / 12, -(real)1 / 6, -(real)1 / 12, 0, (real)1 / 4},
+    {(real)1 / 9, (real)1 / 18, (real)1 / 36, (real)1 / 6, (real)1 / 12, -(real)1 / 6, -(real)1 / 12, 0, -(real)1 / 4}};
 
 /* D2Q5 moments (1, c_x, c_y, 5|c|^2 - 4, c_x^2 - c_y^2) in lattice units */
-static const double M5_LATTICE[5][5] = {
+static const real M5_LATTICE[5][5] = {
     {1, 1, 1, 1, 1},
     {0, 1, 0, -1, 0},
     {0, 0, 1, 0, -1},
@@ -137,21 +160,21 @@ static const int ORDER5[5] = {0, 1, 1, 2, 2};
 typedef struct {
   orc_params p;
   int N;
-  double c, cs2;                 /* lattice speed dx/dt and c_s^2 = c^2/3          */
-  double tau, tauT, tauphi;      /* relaxation times in seconds                    */
-  double Md[81], Mdinv[81];      /* dimensional D2Q9 M and inverse                 */
-  double M5d[25], M5dinv[25];    /* dimensional D2Q5 M and inverse                 */
-  double *f, *fn, *fpost;
-  double *g, *gn, *gpost;
-  double *h, *hn, *hpost;
-  double *z, *zn, *zpost;
-  double *rho, *ux, *uy, *T, *pr, *phi, *Tprev, *phiux_prev, *phiuy_prev;
-  double *q3;                    /* q''' field in W m^-3, or NULL                   */
-  double *force;                 /* per-cell force: F_x plane then F_y plane (2N), N m^-3, or NULL */
+  real c, cs2;                 /* lattice speed dx/dt and c_s^2 = c^2/3          */
+  real tau, tauT, tauphi;      /* relaxation times in seconds                    */
+  real Md[81], Mdinv[81];      /* dimensional D2Q9 M and inverse                 */
+  real M5d[25], M5dinv[25];    /* dimensional D2Q5 M and inverse                 */
+  real *f, *fn, *fpost;
+  real *g, *gn, *gpost;
+  real *h, *hn, *hpost;
+  real *z, *zn, *zpost;
+  real *rho, *ux, *uy, *T, *pr, *phi, *Tprev, *phiux_prev, *phiuy_prev;
+  real *q3;                    /* q''' field in W m^-3, or NULL                   */
+  real *force;                 /* per-cell force: F_x plane then F_y plane (2N), N m^-3, or NULL */
   int bc[4], tbc[4];
-  double rho_w[4];
-  double *bcu[4];                /* per side: 2*len (u_x then u_y)                 */
-  double *bct[4];                /* per side: len (q'' in W m^-2 or T_w in K)      */
+  real rho_w[4];
+  real *bcu[4];                /* per side: 2*len (u_x then u_y)                 */
+  real *bct[4];                /* per side: len (q'' in W m^-2 or T_w in K)      */
   long steps;
 } orc_t;
 
@@ -159,9 +182,9 @@ static int side_len(const orc_t *o, int side) { return side < 2 ? o->p.ny : o->p
 static int idx(const orc_t *o, int i, int j) { return j * o->p.nx + i; }
 
 /* Gauss-Jordan inverse with partial pivoting of an n x n matrix (row-major). */
-static int invert(int n, const double *a_in, double *inv) {
-  double a[81];
-  memcpy(a, a_in, sizeof(double) * n * n);
+static int invert(int n, const real *a_in, real *inv) {
+  real a[81];
+  memcpy(a, a_in, sizeof(real) * n * n);
   for (int r = 0; r < n; r++)
     for (int s = 0; s < n; s++) inv[r * n + s] = (r == s) ? 1.0 : 0.0;
   for (int col = 0; col < n; col++) {
@@ -170,14 +193,14 @@ static int invert(int n, const double *a_in, double *inv) {
       if (fabs(a[r * n + col]) > fabs(a[piv * n + col])) piv = r;
     if (a[piv * n + col] == 0.0) return -1;
     for (int s = 0; s < n; s++) {
-      double t = a[col * n + s]; a[col * n + s] = a[piv * n + s]; a[piv * n + s] = t;
+      real t = a[col * n + s]; a[col * n + s] = a[piv * n + s]; a[piv * n + s] = t;
       t = inv[col * n + s]; inv[col * n + s] = inv[piv * n + s]; inv[piv * n + s] = t;
     }
-    double d = a[col * n + col];
+    real d = a[col * n + col];
     for (int s = 0; s < n; s++) { a[col * n + s] /= d; inv[col * n + s] /= d; }
     for (int r = 0; r < n; r++) {
       if (r == col) continue;
-      double m = a[r * n + col];
+      real m = a[r * n + col];
       if (m == 0.0) continue;
       for (int s = 0; s < n; s++) {
         a[r * n + s] -= m * a[col * n + s];
@@ -189,9 +212,9 @@ static int invert(int n, const double *a_in, double *inv) {
 }
 
 /* y = A x for an n x n row-major matrix */
-static void matvec(int n, const double *A, const double *x, double *y) {
+static void matvec(int n, const real *A, const real *x, real *y) {
   for (int r = 0; r < n; r++) {
-    double s = 0.0;
+    real s = 0.0;
     for (int k = 0; k < n; k++) s += A[r * n + k] * x[k];
     y[r] = s;
   }
@@ -200,17 +223,17 @@ static void matvec(int n, const double *A, const double *x, double *y) {
 /* ------------------------------------------------------------------------- */
 /* Creation                                                                  */
 /* ------------------------------------------------------------------------- */
-void *orc_create(const orc_params *prm) {
+ORC_API void *orc_create(const orc_params *prm) {
   orc_t *o = (orc_t *)calloc(1, sizeof(orc_t));
   if (!o) return NULL;
   o->p = *prm;
   int N = o->N = prm->nx * prm->ny;
-  o->c = prm->dx / prm->dt;                  /* c = dx/dt, Sec. 2.1 */
+  o->c = (real)prm->dx / prm->dt;            /* c = dx/dt, Sec. 2.1 */
   o->cs2 = o->c * o->c / 3.0;                /* c_s = c/sqrt(3)     */
   /* tau from nu = (tau - dt/2) c_s^2, Eq. eq_kinematic_viscosity */
   o->tau = prm->nu / o->cs2 + 0.5 * prm->dt;
   /* tau_T from alpha = (tau_T - dt/2) c_s^2, alpha = k/(rho c_p), Sec. 2.2 */
-  if (prm->thermal) o->tauT = (prm->k / (prm->rho0 * prm->cp)) / o->cs2 + 0.5 * prm->dt;
+  if (prm->thermal) o->tauT = ((real)prm->k / ((real)prm->rho0 * prm->cp)) / o->cs2 + 0.5 * prm->dt;
   /* tau_phi from M = (tau_phi - dt/2) c_s^2, Sec. 2.3 */
   if (prm->phase) o->tauphi = prm->mobility / o->cs2 + 0.5 * prm->dt;
 
@@ -226,7 +249,7 @@ void *orc_create(const orc_params *prm) {
   for (int r = 0; r < 5; r++)
     for (int s = 0; s < 5; s++) o->M5d[r * 5 + s] = M5_LATTICE[r][s] * pow(o->c, ORDER5[r]);
   {
-    double lat[25], latinv[25];
+    real lat[25], latinv[25];
     for (int r = 0; r < 5; r++)
       for (int s = 0; s < 5; s++) lat[r * 5 + s] = M5_LATTICE[r][s];
     invert(5, lat, latinv);
@@ -234,31 +257,31 @@ void *orc_create(const orc_params *prm) {
       for (int s = 0; s < 5; s++) o->M5dinv[r * 5 + s] = latinv[r * 5 + s] / pow(o->c, ORDER5[s]);
   }
 
-  o->f = calloc(9 * N, sizeof(double)); o->fn = calloc(9 * N, sizeof(double));
-  o->fpost = calloc(9 * N, sizeof(double));
-  o->g = calloc(9 * N, sizeof(double)); o->gn = calloc(9 * N, sizeof(double));
-  o->gpost = calloc(9 * N, sizeof(double));
-  o->h = calloc(5 * N, sizeof(double)); o->hn = calloc(5 * N, sizeof(double));
-  o->hpost = calloc(5 * N, sizeof(double));
-  o->z = calloc(9 * N, sizeof(double)); o->zn = calloc(9 * N, sizeof(double));
-  o->zpost = calloc(9 * N, sizeof(double));
-  o->rho = calloc(N, sizeof(double)); o->ux = calloc(N, sizeof(double));
-  o->uy = calloc(N, sizeof(double)); o->T = calloc(N, sizeof(double));
-  o->pr = calloc(N, sizeof(double)); o->phi = calloc(N, sizeof(double));
-  o->Tprev = calloc(N, sizeof(double));
-  o->phiux_prev = calloc(N, sizeof(double)); o->phiuy_prev = calloc(N, sizeof(double));
+  o->f = (real *)calloc(9 * N, sizeof(real)); o->fn = (real *)calloc(9 * N, sizeof(real));
+  o->fpost = (real *)calloc(9 * N, sizeof(real));
+  o->g = (real *)calloc(9 * N, sizeof(real)); o->gn = (real *)calloc(9 * N, sizeof(real));
+  o->gpost = (real *)calloc(9 * N, sizeof(real));
+  o->h = (real *)calloc(5 * N, sizeof(real)); o->hn = (real *)calloc(5 * N, sizeof(real));
+  o->hpost = (real *)calloc(5 * N, sizeof(real));
+  o->z = (real *)calloc(9 * N, sizeof(real)); o->zn = (real *)calloc(9 * N, sizeof(real));
+  o->zpost = (real *)calloc(9 * N, sizeof(real));
+  o->rho = (real *)calloc(N, sizeof(real)); o->ux = (real *)calloc(N, sizeof(real));
+  o->uy = (real *)calloc(N, sizeof(real)); o->T = (real *)calloc(N, sizeof(real));
+  o->pr = (real *)calloc(N, sizeof(real)); o->phi = (real *)calloc(N, sizeof(real));
+  o->Tprev = (real *)calloc(N, sizeof(real));
+  o->phiux_prev = (real *)calloc(N, sizeof(real)); o->phiuy_prev = (real *)calloc(N, sizeof(real));
   for (int s = 0; s < 4; s++) {
     o->bc[s] = BC_PERIODIC; o->tbc[s] = TBC_NONE; o->rho_w[s] = prm->rho0;
-    o->bcu[s] = calloc(2 * side_len(o, s), sizeof(double));
-    o->bct[s] = calloc(side_len(o, s), sizeof(double));
+    o->bcu[s] = (real *)calloc(2 * side_len(o, s), sizeof(real));
+    o->bct[s] = (real *)calloc(side_len(o, s), sizeof(real));
   }
   return o;
 }
 
-void orc_destroy(void *handle) {
+ORC_API void orc_destroy(void *handle) {
   orc_t *o = (orc_t *)handle;
   if (!o) return;
-  double *bufs[] = {o->f, o->fn, o->fpost, o->g, o->gn, o->gpost, o->h, o->hn, o->hpost,
+  real *bufs[] = {o->f, o->fn, o->fpost, o->g, o->gn, o->gpost, o->h, o->hn, o->hpost,
                     o->z, o->zn, o->zpost, o->rho, o->ux, o->uy, o->T, o->pr, o->phi,
                     o->Tprev, o->phiux_prev, o->phiuy_prev, o->q3, o->force};
   for (unsigned b = 0; b < sizeof(bufs) / sizeof(bufs[0]); b++) free(bufs[b]);
@@ -267,38 +290,45 @@ void orc_destroy(void *handle) {
 }
 
 /* Derived quantities for the tests: c, c_s^2, tau, tau_T, tau_phi */
-void orc_constants(void *handle, double *out5) {
+ORC_API void orc_constants(void *handle, double *out5) {
   orc_t *o = (orc_t *)handle;
-  out5[0] = o->c; out5[1] = o->cs2; out5[2] = o->tau; out5[3] = o->tauT; out5[4] = o->tauphi;
+  out5[0] = (double)o->c; out5[1] = (double)o->cs2; out5[2] = (double)o->tau;
+  out5[3] = (double)o->tauT; out5[4] = (double)o->tauphi;
 }
 
 /* The dimensional matrices, for the App. A pins. which: 0 M9, 1 M9^-1 (App. A),
    2 M5, 3 M5^-1, 4 Gauss-Jordan inverse of M9 (checks the inversion routine) */
-void orc_matrix(void *handle, int which, double *out) {
+ORC_API void orc_matrix(void *handle, int which, double *out) {
   orc_t *o = (orc_t *)handle;
-  if (which == 4) { invert(9, o->Md, out); return; }
-  const double *src = which == 0 ? o->Md : which == 1 ? o->Mdinv : which == 2 ? o->M5d : o->M5dinv;
-  memcpy(out, src, sizeof(double) * (which < 2 ? 81 : 25));
+  if (which == 4) {
+    real inv[81];
+    invert(9, o->Md, inv);
+    for (int k = 0; k < 81; k++) out[k] = (double)inv[k];
+    return;
+  }
+  const real *src = which == 0 ? o->Md : which == 1 ? o->Mdinv : which == 2 ? o->M5d : o->M5dinv;
+  for (int k = 0; k < (which < 2 ? 81 : 25); k++) out[k] = (double)src[k];
 }
 
-void orc_set_bc(void *handle, int side, int kind, const double *uw, double rho_w, int tkind,
+ORC_API void orc_set_bc(void *handle, int side, int kind, const double *uw, double rho_w, int tkind,
                 const double *tw) {
   orc_t *o = (orc_t *)handle;
   int len = side_len(o, side);
   o->bc[side] = kind; o->tbc[side] = tkind; o->rho_w[side] = rho_w;
-  if (uw) memcpy(o->bcu[side], uw, sizeof(double) * 2 * len);
-  else memset(o->bcu[side], 0, sizeof(double) * 2 * len);
-  if (tw) memcpy(o->bct[side], tw, sizeof(double) * len);
-  else memset(o->bct[side], 0, sizeof(double) * len);
+  for (int k = 0; k < 2 * len; k++) o->bcu[side][k] = uw ? uw[k] : 0;
+  for (int k = 0; k < len; k++) o->bct[side][k] = tw ? tw[k] : 0;
 }
 
-void orc_set_source(void *handle, const double *q3, const double *force) {
+ORC_API void orc_set_source(void *handle, const double *q3, const double *force) {
   orc_t *o = (orc_t *)handle;
   free(o->q3); o->q3 = NULL; free(o->force); o->force = NULL;
-  if (q3) { o->q3 = malloc(sizeof(double) * o->N); memcpy(o->q3, q3, sizeof(double) * o->N); }
+  if (q3) {
+    o->q3 = (real *)malloc(sizeof(real) * o->N);
+    for (int n = 0; n < o->N; n++) o->q3[n] = q3[n];
+  }
   if (force) {
-    o->force = malloc(sizeof(double) * 2 * o->N);
-    memcpy(o->force, force, sizeof(double) * 2 * o->N);
+    o->force = (real *)malloc(sizeof(real) * 2 * o->N);
+    for (int n = 0; n < 2 * o->N; n++) o->force[n] = force[n];
   }
 }
 
@@ -306,39 +336,39 @@ void orc_set_source(void *handle, const double *q3, const double *force) {
 /* Equilibria and source terms                                               */
 /* ------------------------------------------------------------------------- */
 /* f_eq, Eq. feq_geral */
-static double feq9(const orc_t *o, int i, double rho, double ux, double uy) {
-  double cu = o->c * (CX9[i] * ux + CY9[i] * uy);
-  double uu = ux * ux + uy * uy;
+static real feq9(const orc_t *o, int i, real rho, real ux, real uy) {
+  real cu = o->c * (CX9[i] * ux + CY9[i] * uy);
+  real uu = ux * ux + uy * uy;
   return W9[i] * rho * (1.0 + cu / o->cs2 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
 }
 /* Guo forcing term F_hat_i, Eq. forcing_term */
-static double fhat9(const orc_t *o, int i, double ux, double uy, double Fx, double Fy) {
-  double cx = o->c * CX9[i], cy = o->c * CY9[i];
-  double cu = cx * ux + cy * uy;
-  double ax = (cx - ux) / o->cs2 + cu * cx / (o->cs2 * o->cs2);
-  double ay = (cy - uy) / o->cs2 + cu * cy / (o->cs2 * o->cs2);
+static real fhat9(const orc_t *o, int i, real ux, real uy, real Fx, real Fy) {
+  real cx = o->c * CX9[i], cy = o->c * CY9[i];
+  real cu = cx * ux + cy * uy;
+  real ax = (cx - ux) / o->cs2 + cu * cx / (o->cs2 * o->cs2);
+  real ay = (cy - uy) / o->cs2 + cu * cy / (o->cs2 * o->cs2);
   return W9[i] * (ax * Fx + ay * Fy);
 }
 /* linear g_eq, Eq. geq_geral (D2Q5) */
-static double geq5(const orc_t *o, int i, double T, double ux, double uy) __attribute__((unused));
-static double geq5(const orc_t *o, int i, double T, double ux, double uy) {
-  double cu = o->c * (CX5[i] * ux + CY5[i] * uy);
+static real geq5(const orc_t *o, int i, real T, real ux, real uy) __attribute__((unused));
+static real geq5(const orc_t *o, int i, real T, real ux, real uy) {
+  real cu = o->c * (CX5[i] * ux + CY5[i] * uy);
   return W5[i] * T * (1.0 + cu / o->cs2);
 }
 /* The thermal lattice: D2Q5 (thermal = 5) or the paper's D2Q9 (thermal = 9). */
 static int QG(const orc_t *o) { return o->p.thermal == 9 ? 9 : 5; }
 static int cxg(const orc_t *o, int i) { return o->p.thermal == 9 ? CX9[i] : CX5[i]; }
 static int cyg(const orc_t *o, int i) { return o->p.thermal == 9 ? CY9[i] : CY5[i]; }
-static double wg(const orc_t *o, int i) { return o->p.thermal == 9 ? W9[i] : W5[i]; }
+static real wg(const orc_t *o, int i) { return o->p.thermal == 9 ? W9[i] : W5[i]; }
 /* linear g_eq, Eq. geq_geral, on the thermal lattice */
-static double geqT(const orc_t *o, int i, double T, double ux, double uy) {
-  double cu = o->c * (cxg(o, i) * ux + cyg(o, i) * uy);
+static real geqT(const orc_t *o, int i, real T, real ux, real uy) {
+  real cu = o->c * (cxg(o, i) * ux + cyg(o, i) * uy);
   return wg(o, i) * T * (1.0 + cu / o->cs2);
 }
 /* s_i(u), Eq. s_i_Liang (D2Q9) */
-static double s9(const orc_t *o, int i, double ux, double uy) {
-  double cu = o->c * (CX9[i] * ux + CY9[i] * uy);
-  double uu = ux * ux + uy * uy;
+static real s9(const orc_t *o, int i, real ux, real uy) {
+  real cu = o->c * (CX9[i] * ux + CY9[i] * uy);
+  real uu = ux * ux + uy * uy;
   return W9[i] * (cu / o->cs2 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
 }
 
@@ -379,13 +409,13 @@ static int along(int side, int x, int y) { return side < 2 ? y : x; }
 /* ------------------------------------------------------------------------- */
 /* Force on node n: uniform body force + per-cell field + Boussinesq buoyancy of
    Eq. buoyancy_force, F_b = -rho_ref beta_exp (T - T_ref) g, with T of this step. */
-static void force_at(const orc_t *o, int n, double *Fx, double *Fy) {
+static void force_at(const orc_t *o, int n, real *Fx, real *Fy) {
   const orc_params *p = &o->p;
   int N = o->N;
   *Fx = p->Fb[0] + (o->force ? o->force[n] : 0.0);
   *Fy = p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
   if (p->thermal && p->beta_exp != 0.0) {
-    double b = -p->rho_ref * p->beta_exp * (o->T[n] - p->T_ref);
+    real b = -p->rho_ref * p->beta_exp * (o->T[n] - p->T_ref);
     *Fx += b * p->gravity[0];
     *Fy += b * p->gravity[1];
   }
@@ -397,20 +427,20 @@ static void moments_single(orc_t *o) {
 #pragma omp parallel for schedule(static)
   for (int n = 0; n < N; n++) {
     if (p->thermal) {
-      double qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;   /* qdot = q'''/(rho c_p) */
+      real qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;   /* qdot = q'''/(rho c_p) */
       /* lagged convective sink of the fuse problem: uses T of the previous step (R24) */
       if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->Tprev[n] - p->T_inf);
-      double s = 0;
+      real s = 0;
       for (int i = 0; i < QG(o); i++) s += o->g[i * N + n];
       o->T[n] = s + 0.5 * p->dt * qd;                          /* Eq. zero_moment_g */
     }
     if (p->flow) {
       /* Eqs. zero_moment_f, first_moment_f (force includes buoyancy of T(t)) */
-      double Fx, Fy;
+      real Fx, Fy;
       force_at(o, n, &Fx, &Fy);
-      double rho = 0, jx = 0, jy = 0;
+      real rho = 0, jx = 0, jy = 0;
       for (int i = 0; i < 9; i++) {
-        double fi = o->f[i * N + n];
+        real fi = o->f[i * N + n];
         rho += fi;
         jx += o->c * CX9[i] * fi;
         jy += o->c * CY9[i] * fi;
@@ -422,8 +452,8 @@ static void moments_single(orc_t *o) {
   }
 }
 
-static double qdot_at(const orc_t *o, int n) {
-  double qd = o->q3 ? o->q3[n] / (o->p.rho0 * o->p.cp) : 0.0;
+static real qdot_at(const orc_t *o, int n) {
+  real qd = o->q3 ? o->q3[n] / (o->p.rho0 * o->p.cp) : 0.0;
   if (o->p.conv_coef != 0.0) qd -= o->p.conv_coef * (o->Tprev[n] - o->p.T_inf);
   return qd;
 }
@@ -431,30 +461,30 @@ static double qdot_at(const orc_t *o, int n) {
 static void collide_single(orc_t *o) {
   const orc_params *p = &o->p;
   int N = o->N;
-  double dt = p->dt;
+  real dt = p->dt;
   /* momentum MRT rates, Sec. 2.1 and Sec. 3: omega_nu = 1/tau,
      omega_q = (3/dt)(2/dt - omega_nu)/(3/dt - omega_nu), free rates in [1/dt, 2/dt] */
-  double wnu = 1.0 / o->tau;
-  double wq = (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu);
-  double Lam[9] = {0.0, p->omega_e_dt / dt, p->omega_eps_dt / dt, 0.0, wq, 0.0, wq, wnu, wnu};
+  real wnu = 1.0 / o->tau;
+  real wq = (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu);
+  real Lam[9] = {0.0, p->omega_e_dt / dt, p->omega_eps_dt / dt, 0.0, wq, 0.0, wq, wnu, wnu};
   /* thermal D2Q5 MRT rates, analogue of [Lambda_T]_dim (reading R4) */
-  double wT = 1.0 / o->tauT;
-  double LamT[5] = {0.0, wT, wT, 1.0 / dt, 1.0 / dt};
+  real wT = 1.0 / o->tauT;
+  real LamT[5] = {0.0, wT, wT, 1.0 / dt, 1.0 / dt};
   /* thermal D2Q9 MRT, Sec. 2.2: [Lambda_T] = diag(0, 1, 1, omega_T, 1, omega_T, 1, 1, 1)
      with omega_T = 1/tau_T and the unit rates read as 1/dt (reading R3), on the
      momentum transformation matrices */
-  double LamT9[9] = {0.0, 1.0 / dt, 1.0 / dt, wT, 1.0 / dt, wT, 1.0 / dt, 1.0 / dt, 1.0 / dt};
+  real LamT9[9] = {0.0, 1.0 / dt, 1.0 / dt, wT, 1.0 / dt, wT, 1.0 / dt, 1.0 / dt, 1.0 / dt};
   const int qg = QG(o);
   /* S_g prefactor uses tau_T (reading R1); literal print uses tau */
-  double tau_sg = (p->literal & 1) ? o->tau : o->tauT;
+  real tau_sg = (p->literal & 1) ? o->tau : o->tauT;
 #pragma omp parallel for schedule(static)
   for (int n = 0; n < N; n++) {
-    double ux = o->ux[n], uy = o->uy[n];
+    real ux = o->ux[n], uy = o->uy[n];
     if (p->flow) {
-      double rho = o->rho[n];
-      double Fx, Fy;
+      real rho = o->rho[n];
+      real Fx, Fy;
       force_at(o, n, &Fx, &Fy);
-      double fv[9], fe[9], fh[9];
+      real fv[9], fe[9], fh[9];
       for (int i = 0; i < 9; i++) {
         fv[i] = o->f[i * N + n];
         fe[i] = feq9(o, i, rho, ux, uy);
@@ -466,7 +496,7 @@ static void collide_single(orc_t *o) {
           o->fpost[i * N + n] = fv[i] - dt / o->tau * (fv[i] - fe[i]) + dt * (1.0 - dt / (2.0 * o->tau)) * fh[i];
       } else {
         /* MRT in moment space, Eq. colisao_MRT with [M]_dim */
-        double m[9], me[9], Fm[9], ms[9], fs[9];
+        real m[9], me[9], Fm[9], ms[9], fs[9];
         matvec(9, o->Md, fv, m);
         matvec(9, o->Md, fe, me);
         matvec(9, o->Md, fh, Fm);
@@ -477,9 +507,9 @@ static void collide_single(orc_t *o) {
       }
     }
     if (p->thermal) {
-      double T = o->T[n];
-      double qd = qdot_at(o, n);
-      double gv[9], ge[9];
+      real T = o->T[n];
+      real qd = qdot_at(o, n);
+      real gv[9], ge[9];
       for (int i = 0; i < qg; i++) { gv[i] = o->g[i * N + n]; ge[i] = geqT(o, i, T, ux, uy); }
       if (p->thermal_op == 0) {
         /* Eqs. eq_lattice_boltzmann_BGK_T and forcing_term_g */
@@ -487,7 +517,7 @@ static void collide_single(orc_t *o) {
           o->gpost[i * N + n] = gv[i] - dt / o->tauT * (gv[i] - ge[i]) + dt * (1.0 - dt / (2.0 * tau_sg)) * wg(o, i) * qd;
       } else if (qg == 9) {
         /* Eq. colisao_MRT for g with [Lambda_T] and the source Delta t (I - dt Lambda/2) M (w qdot) */
-        double sv[9], m[9], me[9], Sm[9], ms[9], gs[9];
+        real sv[9], m[9], me[9], Sm[9], ms[9], gs[9];
         for (int i = 0; i < 9; i++) sv[i] = W9[i] * qd;
         matvec(9, o->Md, gv, m);
         matvec(9, o->Md, ge, me);
@@ -498,7 +528,7 @@ static void collide_single(orc_t *o) {
         for (int i = 0; i < 9; i++) o->gpost[i * N + n] = gs[i];
       } else {
         /* D2Q5 MRT analogue of Eq. colisao_MRT with source w_i qdot (reading R4) */
-        double sv[5], m[5], me[5], Sm[5], ms[5], gs[5];
+        real sv[5], m[5], me[5], Sm[5], ms[5], gs[5];
         for (int i = 0; i < 5; i++) sv[i] = W5[i] * qd;
         matvec(5, o->M5d, gv, m);
         matvec(5, o->M5d, ge, me);
@@ -513,19 +543,19 @@ static void collide_single(orc_t *o) {
 }
 
 /* Momentum: value entering node (x,y) opposite to outgoing direction i through `side`. */
-static double flow_boundary_value(const orc_t *o, int side, int x, int y, int i) {
+static real flow_boundary_value(const orc_t *o, int side, int x, int y, int i) {
   int n = idx(o, x, y);
   int N = o->N;
-  double fs = o->fpost[i * N + n];
+  real fs = o->fpost[i * N + n];
   int a = along(side, x, y);
   int len = side_len(o, side);
-  double cix = o->c * CX9[i], ciy = o->c * CY9[i];
-  double rw = o->rho_w[side];
+  real cix = o->c * CX9[i], ciy = o->c * CY9[i];
+  real rw = o->rho_w[side];
   switch (o->bc[side]) {
     case BC_WALL:
     case BC_VELOCITY: {
       /* Eq. BB_vel; the wall / inlet velocity is taken at the node's row or column */
-      double uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
+      real uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
       return fs - 2.0 * W9[i] * rw * (cix * uwx + ciy * uwy) / o->cs2;
     }
     case BC_PRESSURE: {
@@ -537,10 +567,10 @@ static double flow_boundary_value(const orc_t *o, int side, int x, int y, int i)
       else if (side == 2) ny_in = y + 1;
       else ny_in = y - 1;
       int m = idx(o, nx_in, ny_in);
-      double uwx = o->ux[n] + 0.5 * (o->ux[n] - o->ux[m]);
-      double uwy = o->uy[n] + 0.5 * (o->uy[n] - o->uy[m]);
-      double cu = cix * uwx + ciy * uwy;
-      double uu = uwx * uwx + uwy * uwy;
+      real uwx = o->ux[n] + 0.5 * (o->ux[n] - o->ux[m]);
+      real uwy = o->uy[n] + 0.5 * (o->uy[n] - o->uy[m]);
+      real cu = cix * uwx + ciy * uwy;
+      real uu = uwx * uwx + uwy * uwy;
       return -fs + 2.0 * W9[i] * rw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
     }
     default:
@@ -550,26 +580,26 @@ static double flow_boundary_value(const orc_t *o, int side, int x, int y, int i)
 
 /* Thermal: value entering node opposite to outgoing i through `side`;
    OUTFLOW, SYMMETRY and WETNODE are resolved after streaming. */
-static double thermal_boundary_value(const orc_t *o, int side, int x, int y, int i) {
+static real thermal_boundary_value(const orc_t *o, int side, int x, int y, int i) {
   int n = idx(o, x, y);
   int N = o->N;
-  double gs = o->gpost[i * N + n];
+  real gs = o->gpost[i * N + n];
   int a = along(side, x, y);
   int len = side_len(o, side);
   switch (o->tbc[side]) {
     case TBC_FLUX: {
       /* Eq. BB_T, rho = rho0; lambda_i = 2 w_i / (c_s^2 / c^2) = 6 w_i on D2Q9 (4/6 axial,
          1/6 diagonal), 1 for the single unknown of D2Q5 (reading R5) */
-      double qflux = o->bct[side][a];
-      double lam = QG(o) == 9 ? 6.0 * W9[i] : 1.0;
+      real qflux = o->bct[side][a];
+      real lam = QG(o) == 9 ? 6.0 * W9[i] : 1.0;
       return gs + lam * (o->p.dt / o->p.dx) * qflux / (o->p.rho0 * o->p.cp);
     }
     case TBC_TEMP: {
       /* Eq. anti_BB_T with the side's velocity (zero at a wall) */
-      double Tw = o->bct[side][a];
-      double uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
-      double cu = o->c * (cxg(o, i) * uwx + cyg(o, i) * uwy);
-      double uu = uwx * uwx + uwy * uwy;
+      real Tw = o->bct[side][a];
+      real uwx = o->bcu[side][a], uwy = o->bcu[side][len + a];
+      real cu = o->c * (cxg(o, i) * uwx + cyg(o, i) * uwy);
+      real uu = uwx * uwx + uwy * uwy;
       return -gs + 2.0 * wg(o, i) * Tw * (1.0 + cu * cu / (2.0 * o->cs2 * o->cs2) - uu / (2.0 * o->cs2));
     }
     default:
@@ -590,11 +620,11 @@ static void symmetry_gather(orc_t *o, int thermal) {
   int N = o->N, nx = p->nx, ny = p->ny;
   int q9 = thermal ? QG(o) == 9 : 1;
   int nq = q9 ? 9 : 5;
-  double *dst = thermal ? o->gn : o->fn;
-  const double *post = thermal ? o->gpost : o->fpost;
+  real *dst = thermal ? o->gn : o->fn;
+  const real *post = thermal ? o->gpost : o->fpost;
   for (int side = 0; side < 4; side++) {
     int kind = thermal ? o->tbc[side] : o->bc[side];
-    if (kind != (thermal ? TBC_SYMMETRY : BC_SYMMETRY)) continue;
+    if (kind != (thermal ? (int)TBC_SYMMETRY : (int)BC_SYMMETRY)) continue;
     int len = side_len(o, side);
     /* the tangential axis wraps where that axis is periodic for this lattice */
     int tper = side < 2 ? (thermal ? (o->tbc[2] == TBC_NONE && o->tbc[3] == TBC_NONE)
@@ -683,9 +713,9 @@ static void stream_single(orc_t *o) {
       int x = side == 0 ? 0 : nx - 1, q = side == 0 ? 1 : 3;
       for (int y = 0; y < ny; y++) {
         int n = idx(o, x, y);
-        double qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;
+        real qd = o->q3 ? o->q3[n] / (p->rho0 * p->cp) : 0.0;
         if (p->conv_coef != 0.0) qd -= p->conv_coef * (o->T[n] - p->T_inf);
-        double others = 0.0;
+        real others = 0.0;
         for (int i = 0; i < 5; i++)
           if (i != q) others += o->gn[i * N + n];
         o->gn[q * N + n] = o->bct[side][y] - 0.5 * p->dt * qd - others;
@@ -697,12 +727,12 @@ static void stream_single(orc_t *o) {
 /* ------------------------------------------------------------------------- */
 /* Two-phase step (Liang et al. model as written in Sec. 2.3)                */
 /* ------------------------------------------------------------------------- */
-static void moments_two_phase(orc_t *o, double *gx, double *gy, double *lap) {
+static void moments_two_phase(orc_t *o, real *gx, real *gy, real *lap) {
   const orc_params *p = &o->p;
   int N = o->N, nx = p->nx, ny = p->ny;
   /* phi = sum h_i, Eq. zero_moment_h */
   for (int n = 0; n < N; n++) {
-    double s = 0;
+    real s = 0;
     for (int i = 0; i < 5; i++) s += o->h[i * N + n];
     o->phi[n] = s;
   }
@@ -714,12 +744,12 @@ static void moments_two_phase(orc_t *o, double *gx, double *gy, double *lap) {
   for (int y = 0; y < ny; y++)
     for (int x = 0; x < nx; x++) {
       int n = idx(o, x, y);
-      double sx = 0, sy = 0, sl = 0;
+      real sx = 0, sy = 0, sl = 0;
       for (int i = 1; i < 9; i++) {
         int tx = x + CX9[i], ty = y + CY9[i];
         if (tx < 0 || tx >= nx) tx = xwall ? (tx < 0 ? 0 : nx - 1) : (tx + nx) % nx;
         if (ty < 0 || ty >= ny) ty = ywall ? (ty < 0 ? 0 : ny - 1) : (ty + ny) % ny;
-        double pn = o->phi[idx(o, tx, ty)];
+        real pn = o->phi[idx(o, tx, ty)];
         sx += W9[i] * o->c * CX9[i] * pn;
         sy += W9[i] * o->c * CY9[i] * pn;
         sl += 2.0 * W9[i] * (pn - o->phi[n]);
@@ -733,66 +763,66 @@ static void moments_two_phase(orc_t *o, double *gx, double *gy, double *lap) {
 static void step_two_phase(orc_t *o) {
   const orc_params *p = &o->p;
   int N = o->N, nx = p->nx, ny = p->ny;
-  double dt = p->dt, cs2 = o->cs2;
-  double *gx = malloc(sizeof(double) * N), *gy = malloc(sizeof(double) * N);
-  double *lap = malloc(sizeof(double) * N);
+  real dt = p->dt, cs2 = o->cs2;
+  real *gx = (real *)malloc(sizeof(real) * N), *gy = (real *)malloc(sizeof(real) * N);
+  real *lap = (real *)malloc(sizeof(real) * N);
   moments_two_phase(o, gx, gy, lap);
-  double kappa = 1.5 * p->sigma * p->W;   /* kappa = 3 sigma W / 2 */
-  double beta = 12.0 * p->sigma / p->W;   /* beta = 12 sigma / W  */
-  double tphi = o->tauphi;
+  real kappa = 1.5 * p->sigma * p->W;   /* kappa = 3 sigma W / 2 */
+  real beta = 12.0 * p->sigma / p->W;   /* beta = 12 sigma / W  */
+  real tphi = o->tauphi;
 #pragma omp parallel for schedule(static)
   for (int n = 0; n < N; n++) {
-    double phi = o->phi[n];
+    real phi = o->phi[n];
     /* chemical potential, Eq. chemical_potential */
-    double mu = 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) - kappa * lap[n];
+    real mu = 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) - kappa * lap[n];
     /* normal, guarded where |grad phi| = 0 */
-    double gnorm = sqrt(gx[n] * gx[n] + gy[n] * gy[n]);
-    double nxv = 0.0, nyv = 0.0;
+    real gnorm = sqrt(gx[n] * gx[n] + gy[n] * gy[n]);
+    real nxv = 0.0, nyv = 0.0;
     if (gnorm != 0.0) { nxv = gx[n] / gnorm; nyv = gy[n] / gnorm; }
     /* rho and nu linear in phi; grad rho = (rho_l - rho_g) grad phi */
-    double rho = p->rho_g + phi * (p->rho_l - p->rho_g);
-    double nu;
+    real rho = p->rho_g + phi * (p->rho_l - p->rho_g);
+    real nu;
     if (p->nu_rule == 0) nu = p->nu_g + phi * (p->nu_l - p->nu_g);
     else {
-      double zeta = p->rho_g * p->nu_g + phi * (p->rho_l * p->nu_l - p->rho_g * p->nu_g);
+      real zeta = p->rho_g * p->nu_g + phi * (p->rho_l * p->nu_l - p->rho_g * p->nu_g);
       nu = zeta / rho;
     }
-    double tau = nu / cs2 + 0.5 * dt;
-    double drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
-    double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[n] : 0.0);
-    double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
+    real tau = nu / cs2 + 0.5 * dt;
+    real drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
+    real Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[n] : 0.0);
+    real Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
     /* u from Eq. u_Liang, then p from Eq. p_Liang */
-    double jx = 0, jy = 0, zs = 0;
+    real jx = 0, jy = 0, zs = 0;
     for (int i = 0; i < 9; i++) {
-      double zi = o->z[i * N + n];
+      real zi = o->z[i * N + n];
       jx += o->c * CX9[i] * zi;
       jy += o->c * CY9[i] * zi;
       if (i >= 1) zs += zi;
     }
-    double ux = (jx + 0.5 * dt * Fx) / rho;
-    double uy = (jy + 0.5 * dt * Fy) / rho;
-    double pr = cs2 / (1.0 - W9[0]) * (zs + 0.5 * dt * (ux * drx + uy * dry) + rho * s9(o, 0, ux, uy));
+    real ux = (jx + 0.5 * dt * Fx) / rho;
+    real uy = (jy + 0.5 * dt * Fy) / rho;
+    real pr = cs2 / (1.0 - W9[0]) * (zs + 0.5 * dt * (ux * drx + uy * dry) + rho * s9(o, 0, ux, uy));
     o->rho[n] = rho; o->ux[n] = ux; o->uy[n] = uy; o->pr[n] = pr;
     /* d_t(phi u) by explicit Euler against the stored previous value */
-    double dtpux = (phi * ux - o->phiux_prev[n]) / dt;
-    double dtpuy = (phi * uy - o->phiuy_prev[n]) / dt;
+    real dtpux = (phi * ux - o->phiux_prev[n]) / dt;
+    real dtpuy = (phi * uy - o->phiuy_prev[n]) / dt;
     /* h collision (BGK), Eqs. eq_lattice_boltzmann_interface, heq_liang, source_term_interface */
-    double ax = dtpux + cs2 * 4.0 * phi * (1.0 - phi) / p->W * nxv;
-    double ay = dtpuy + cs2 * 4.0 * phi * (1.0 - phi) / p->W * nyv;
+    real ax = dtpux + cs2 * 4.0 * phi * (1.0 - phi) / p->W * nxv;
+    real ay = dtpuy + cs2 * 4.0 * phi * (1.0 - phi) / p->W * nyv;
     for (int i = 0; i < 5; i++) {
-      double cx = o->c * CX5[i], cy = o->c * CY5[i];
-      double heq = phi * W5[i] * (1.0 + (cx * ux + cy * uy) / cs2);
-      double Sh = (1.0 - dt / (2.0 * tphi)) * W5[i] * (cx * ax + cy * ay) / cs2;
-      double hi = o->h[i * N + n];
+      real cx = o->c * CX5[i], cy = o->c * CY5[i];
+      real heq = phi * W5[i] * (1.0 + (cx * ux + cy * uy) / cs2);
+      real Sh = (1.0 - dt / (2.0 * tphi)) * W5[i] * (cx * ax + cy * ay) / cs2;
+      real hi = o->h[i * N + n];
       o->hpost[i * N + n] = hi - dt / tphi * (hi - heq) + dt * Sh;
     }
     /* z collision: equilibrium Eq. zeq_liang, forcing Eq. forcing_term_pressure_evolution */
-    double zv[9], ze[9], zf[9];
+    real zv[9], ze[9], zf[9];
     for (int i = 0; i < 9; i++) {
-      double cx = o->c * CX9[i], cy = o->c * CY9[i];
+      real cx = o->c * CX9[i], cy = o->c * CY9[i];
       zv[i] = o->z[i * N + n];
       ze[i] = (i == 0 ? pr / cs2 * (W9[0] - 1.0) : pr / cs2 * W9[i]) + rho * s9(o, i, ux, uy);
-      double cu = cx * ux + cy * uy, cdr = cx * drx + cy * dry;
+      real cu = cx * ux + cy * uy, cdr = cx * drx + cy * dry;
       zf[i] = W9[i] * ((cx * Fx + cy * Fy) / cs2 + cu * cdr / cs2);
     }
     if (p->z_op == 0) {
@@ -801,11 +831,11 @@ static void step_two_phase(orc_t *o) {
     } else {
       /* MRT with the multiphase [Lambda]_dim of Sec. 3; q_y uses omega_q2 like q_x
          (reading R2), literal flag relaxes q_y at 1/dt as printed */
-      double wnu = 1.0 / tau;
-      double wq2 = (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu);
-      double Lam[9] = {1.0 / dt, 1.0 / dt, 1.0 / dt, 1.0 / dt, wq2, 1.0 / dt,
+      real wnu = 1.0 / tau;
+      real wq2 = (3.0 / dt) * (2.0 / dt - wnu) / (3.0 / dt - wnu);
+      real Lam[9] = {1.0 / dt, 1.0 / dt, 1.0 / dt, 1.0 / dt, wq2, 1.0 / dt,
                        (p->literal & 2) ? 1.0 / dt : wq2, wnu, wnu};
-      double m[9], me[9], Fm[9], ms[9], zs2[9];
+      real m[9], me[9], Fm[9], ms[9], zs2[9];
       matvec(9, o->Md, zv, m);
       matvec(9, o->Md, ze, me);
       matvec(9, o->Md, zf, Fm);
@@ -839,7 +869,7 @@ static void step_two_phase(orc_t *o) {
         else o->zn[i * N + idx(o, (tx + nx) % nx, (ty + ny) % ny)] = o->zpost[i * N + n];
       }
     }
-  double *t;
+  real *t;
   t = o->h; o->h = o->hn; o->hn = t;
   t = o->z; o->z = o->zn; o->zn = t;
   free(gx); free(gy); free(lap);
@@ -850,20 +880,20 @@ static void step_two_phase(orc_t *o) {
 /* ------------------------------------------------------------------------- */
 /* Fields (NULL = defaults): a = rho (single phase) or phi (two-phase);
    ux, uy; b = T (thermal) or p (two-phase).  Defaults: rho0, 0, 0, T0, 0. */
-void orc_init(void *handle, const double *a, const double *ux, const double *uy, const double *b) {
+ORC_API void orc_init(void *handle, const double *a, const double *ux, const double *uy, const double *b) {
   orc_t *o = (orc_t *)handle;
   const orc_params *p = &o->p;
   int N = o->N;
   for (int n = 0; n < N; n++) {
-    double u0 = ux ? ux[n] : (p->flow ? 0.0 : p->u_prescribed[0]);
-    double v0 = uy ? uy[n] : (p->flow ? 0.0 : p->u_prescribed[1]);
+    real u0 = ux ? ux[n] : (p->flow ? 0.0 : p->u_prescribed[0]);
+    real v0 = uy ? uy[n] : (p->flow ? 0.0 : p->u_prescribed[1]);
     o->ux[n] = u0; o->uy[n] = v0;
     if (p->phase) {
-      double phi = a ? a[n] : 1.0;
-      double pr = b ? b[n] : 0.0;
-      double rho = p->rho_g + phi * (p->rho_l - p->rho_g);
+      real phi = a ? a[n] : 1.0;
+      real pr = b ? b[n] : 0.0;
+      real rho = p->rho_g + phi * (p->rho_l - p->rho_g);
       for (int i = 0; i < 5; i++) {
-        double cu = o->c * (CX5[i] * u0 + CY5[i] * v0);
+        real cu = o->c * (CX5[i] * u0 + CY5[i] * v0);
         o->h[i * N + n] = phi * W5[i] * (1.0 + cu / o->cs2);
       }
       for (int i = 0; i < 9; i++)
@@ -873,12 +903,12 @@ void orc_init(void *handle, const double *a, const double *ux, const double *uy,
       o->phi[n] = phi; o->rho[n] = rho; o->pr[n] = pr;
       continue;
     }
-    double rho = a ? a[n] : p->rho0;
+    real rho = a ? a[n] : p->rho0;
     o->rho[n] = rho;
     if (p->flow)
       for (int i = 0; i < 9; i++) o->f[i * N + n] = feq9(o, i, rho, u0, v0);
     if (p->thermal) {
-      double T = b ? b[n] : p->T0;
+      real T = b ? b[n] : p->T0;
       o->T[n] = T; o->Tprev[n] = T;
       for (int i = 0; i < QG(o); i++) o->g[i * N + n] = geqT(o, i, T, u0, v0);
     }
@@ -886,7 +916,7 @@ void orc_init(void *handle, const double *a, const double *ux, const double *uy,
   o->steps = 0;
 }
 
-void orc_step(void *handle, long nsteps) {
+ORC_API void orc_step(void *handle, long nsteps) {
   orc_t *o = (orc_t *)handle;
   for (long s = 0; s < nsteps; s++) {
     if (o->p.phase) {
@@ -895,10 +925,10 @@ void orc_step(void *handle, long nsteps) {
       moments_single(o);
       collide_single(o);
       stream_single(o);
-      double *t;
+      real *t;
       t = o->f; o->f = o->fn; o->fn = t;
       t = o->g; o->g = o->gn; o->gn = t;
-      if (o->p.thermal && o->p.conv_coef != 0.0) memcpy(o->Tprev, o->T, sizeof(double) * o->N);
+      if (o->p.thermal && o->p.conv_coef != 0.0) memcpy(o->Tprev, o->T, sizeof(real) * o->N);
     }
     o->steps++;
   }
@@ -906,37 +936,37 @@ void orc_step(void *handle, long nsteps) {
 
 /* Macroscopic fields of the CURRENT pre-collision state (time t = steps*dt).
    Any output pointer may be NULL. */
-void orc_moments(void *handle, double *rho, double *ux, double *uy, double *T, double *pr,
+ORC_API void orc_moments(void *handle, double *rho, double *ux, double *uy, double *T, double *pr,
                  double *phi) {
   orc_t *o = (orc_t *)handle;
   int N = o->N;
   if (o->p.phase) {
     const orc_params *p = &o->p;
-    double *gx = malloc(sizeof(double) * N), *gy = malloc(sizeof(double) * N);
-    double *lap = malloc(sizeof(double) * N);
+    real *gx = (real *)malloc(sizeof(real) * N), *gy = (real *)malloc(sizeof(real) * N);
+    real *lap = (real *)malloc(sizeof(real) * N);
     moments_two_phase(o, gx, gy, lap);
-    double kappa = 1.5 * p->sigma * p->W, beta = 12.0 * p->sigma / p->W;
+    real kappa = 1.5 * p->sigma * p->W, beta = 12.0 * p->sigma / p->W;
     for (int n = 0; n < N; n++) {
-      double ph = o->phi[n];
-      double mu = 4.0 * beta * ph * (ph - 1.0) * (ph - 0.5) - kappa * lap[n];
-      double r = p->rho_g + ph * (p->rho_l - p->rho_g);
-      double drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
-      double Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[n] : 0.0);
-      double Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
-      double jx = 0, jy = 0, zs = 0;
+      real ph = o->phi[n];
+      real mu = 4.0 * beta * ph * (ph - 1.0) * (ph - 0.5) - kappa * lap[n];
+      real r = p->rho_g + ph * (p->rho_l - p->rho_g);
+      real drx = (p->rho_l - p->rho_g) * gx[n], dry = (p->rho_l - p->rho_g) * gy[n];
+      real Fx = mu * gx[n] + p->Fb[0] + (o->force ? o->force[n] : 0.0);
+      real Fy = mu * gy[n] + p->Fb[1] + (o->force ? o->force[N + n] : 0.0);
+      real jx = 0, jy = 0, zs = 0;
       for (int i = 0; i < 9; i++) {
-        double zi = o->z[i * N + n];
+        real zi = o->z[i * N + n];
         jx += o->c * CX9[i] * zi;
         jy += o->c * CY9[i] * zi;
         if (i >= 1) zs += zi;
       }
-      double u = (jx + 0.5 * p->dt * Fx) / r, v = (jy + 0.5 * p->dt * Fy) / r;
-      double pp = o->cs2 / (1.0 - W9[0]) * (zs + 0.5 * p->dt * (u * drx + v * dry) + r * s9(o, 0, u, v));
-      if (rho) rho[n] = r;
-      if (ux) ux[n] = u;
-      if (uy) uy[n] = v;
-      if (pr) pr[n] = pp;
-      if (phi) phi[n] = ph;
+      real u = (jx + 0.5 * p->dt * Fx) / r, v = (jy + 0.5 * p->dt * Fy) / r;
+      real pp = o->cs2 / (1.0 - W9[0]) * (zs + 0.5 * p->dt * (u * drx + v * dry) + r * s9(o, 0, u, v));
+      if (rho) rho[n] = (double)r;
+      if (ux) ux[n] = (double)u;
+      if (uy) uy[n] = (double)v;
+      if (pr) pr[n] = (double)pp;
+      if (phi) phi[n] = (double)ph;
       if (T) T[n] = 0.0;
     }
     free(gx); free(gy); free(lap);
@@ -946,35 +976,71 @@ void orc_moments(void *handle, double *rho, double *ux, double *uy, double *T, d
      recomputes the same values, so overwriting the work arrays is harmless) */
   moments_single(o);
   for (int n = 0; n < N; n++) {
-    if (rho) rho[n] = o->p.flow ? o->rho[n] : o->p.rho0;
-    if (ux) ux[n] = o->ux[n];
-    if (uy) uy[n] = o->uy[n];
-    if (T) T[n] = o->p.thermal ? o->T[n] : 0.0;
+    if (rho) rho[n] = o->p.flow ? (double)o->rho[n] : o->p.rho0;
+    if (ux) ux[n] = (double)o->ux[n];
+    if (uy) uy[n] = (double)o->uy[n];
+    if (T) T[n] = o->p.thermal ? (double)o->T[n] : 0.0;
     /* single-phase pressure deviation p - p0 = c_s^2 (rho - rho0) */
-    if (pr) pr[n] = o->p.flow ? o->cs2 * (o->rho[n] - o->p.rho0) : 0.0;
+    if (pr) pr[n] = o->p.flow ? (double)(o->cs2 * (o->rho[n] - o->p.rho0)) : 0.0;
     if (phi) phi[n] = 0.0;
   }
 }
 
 /* Distributions: which 0 f, 1 g, 2 h, 3 z; post = 0 current pre-collision state,
    1 post-collision values of the last step (valid after >= 1 step). */
-void orc_get_dist(void *handle, int which, int post, double *out) {
+ORC_API void orc_get_dist(void *handle, int which, int post, double *out) {
   orc_t *o = (orc_t *)handle;
   int q = (which == 0 || which == 3 || (which == 1 && o->p.thermal == 9)) ? 9 : 5;
-  double *src;
+  real *src;
   if (which == 0) src = post ? o->fpost : o->f;
   else if (which == 1) src = post ? o->gpost : o->g;
   else if (which == 2) src = post ? o->hpost : o->h;
   else src = post ? o->zpost : o->z;
-  memcpy(out, src, sizeof(double) * q * o->N);
+  for (long k = 0; k < (long)q * o->N; k++) out[k] = (double)src[k];
 }
 
 /* Overwrite the current pre-collision distributions (for planted-mistake tests). */
-void orc_set_dist(void *handle, int which, const double *in) {
+ORC_API void orc_set_dist(void *handle, int which, const double *in) {
   orc_t *o = (orc_t *)handle;
   int q = (which == 0 || which == 3 || (which == 1 && o->p.thermal == 9)) ? 9 : 5;
-  double *dst = which == 0 ? o->f : which == 1 ? o->g : which == 2 ? o->h : o->z;
-  memcpy(dst, in, sizeof(double) * q * o->N);
+  real *dst = which == 0 ? o->f : which == 1 ? o->g : which == 2 ? o->h : o->z;
+  for (long k = 0; k < (long)q * o->N; k++) dst[k] = in[k];
 }
 
-long orc_steps(void *handle) { return ((orc_t *)handle)->steps; }
+ORC_API long orc_steps(void *handle) { return ((orc_t *)handle)->steps; }
+
+#ifdef ORACLE_DUAL
+/* ------------------------------------------------------------------------- */
+/* Forward-mode derivatives (C++ dual-number build only)                      */
+/* ------------------------------------------------------------------------- */
+/* Seeds one directional derivative: the change of the kinematic viscosity dnu
+   (m^2 s^-1, entering through tau, Eq. eq_kinematic_viscosity), a direction of the
+   heat-source field dq3 (nx*ny values, W m^-3, or NULL; Eq. forcing_term_g through
+   qdot = q'''/(rho c_p)) and a direction of the wall heat flux dqwall (nx values for
+   the y- side then nx for the y+ side, W m^-2, or NULL; Eq. BB_T).  Call after
+   orc_set_bc and orc_set_source (which reset the derivative parts) and before
+   orc_step. */
+ORC_API void orc_seed(void *handle, double dnu, const double *dq3, const double *dqwall) {
+  orc_t *o = (orc_t *)handle;
+  o->tau = dual(o->p.nu, dnu) / o->cs2 + 0.5 * o->p.dt;
+  if (dq3) {
+    if (!o->q3) o->q3 = (real *)calloc(o->N, sizeof(real));
+    for (int n = 0; n < o->N; n++) o->q3[n].d = dq3[n];
+  }
+  if (dqwall)
+    for (int side = 2; side < 4; side++)
+      if (o->tbc[side] == TBC_FLUX)
+        for (int a = 0; a < o->p.nx; a++) o->bct[side][a].d = dqwall[(side - 2) * o->p.nx + a];
+}
+
+/* Derivative parts of the current macroscopic fields (single phase): u_x, u_y, T. */
+ORC_API void orc_tangent(void *handle, double *dux, double *duy, double *dT) {
+  orc_t *o = (orc_t *)handle;
+  moments_single(o);
+  for (int n = 0; n < o->N; n++) {
+    if (dux) dux[n] = o->ux[n].d;
+    if (duy) duy[n] = o->uy[n].d;
+    if (dT) dT[n] = o->p.thermal ? o->T[n].d : 0.0;
+  }
+}
+#endif

@@ -295,15 +295,40 @@ def lbm_adjoint(h, steps, ckpt_every, T_target, nx, ny, want_q3=True, want_qwall
     return loss.value, g3, gw, (gn.value if want_nu else None)
 
 
+def _noalloc_arg(name, t, n):
+    """Check one tensor argument of lbm_field_integrals_noalloc before its address goes
+    to the kernel, which reads n doubles from it (or writes them, for out4)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} values, the call needs {n}")
+    return t
+
+
 def lbm_field_integrals_noalloc(rho, ux, uy, phi, nx, ny, dx, c, out4, stream=None):
-    """Allocation-free integrals of device fields (torch CUDA float64 tensors or raw
-    device addresses) into the device array out4; returns the status code."""
-    def addr(t):
-        if t is None:
-            return None
-        return C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
-    return lib().lbm_field_integrals_noalloc(addr(rho), addr(ux), addr(uy), addr(phi), int(nx), int(ny),
-                                             float(dx), float(c), addr(out4), stream)
+    """Allocation-free integrals of device fields into the device array out4; returns
+    the status code.  rho, ux, uy (and phi, or None) are contiguous float64 CUDA
+    tensors of at least nx*ny values, out4 one of at least 4, all on one device;
+    anything else raises ValueError before the C call."""
+    nx, ny = int(nx), int(ny)
+    if nx < 1 or ny < 1:
+        raise ValueError("nx and ny must be >= 1")
+    n = nx * ny
+    named = [("rho", rho, n), ("ux", ux, n), ("uy", uy, n), ("phi", phi, n), ("out4", out4, 4)]
+    ts = [None if t is None and k == "phi" else _noalloc_arg(k, t, m) for k, t, m in named]
+    for (k, _, _), t in zip(named, ts):
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"{k} must be a CUDA tensor")
+    if len({t.device for t in ts if t is not None}) != 1:
+        raise ValueError("all tensors must be on one device")
+    ptr = [None if t is None else C.c_void_p(t.data_ptr()) for t in ts]
+    return lib().lbm_field_integrals_noalloc(ptr[0], ptr[1], ptr[2], ptr[3], nx, ny, float(dx), float(c), ptr[4],
+                                             stream)
 
 
 # --- convenience wrapper -----------------------------------------------------
@@ -412,9 +437,11 @@ class Solver:
     def set_state(self, buf):
         lbm_set_state(self.h, buf)
 
-    def state_arrays(self):
-        """Post-collision populations (q, ny, nx) as float64, deviations added back
-        (f = stored + w_i rho0, g = stored + w_i T0) for single-phase solves."""
+    def state_arrays(self, deviations=False):
+        """Post-collision populations (q, ny, nx) as float64.  Single-phase solves store
+        deviations from the rest equilibrium; they are returned as stored with
+        ``deviations=True`` (f - w_i rho0, g - w_i T0), else with w_i rho0 and w_i T0
+        added back."""
         raw = self.get_state()
         dt = np.float64 if self.precision == LBM_FP64 else np.float32
         a = raw.view(dt).astype(np.float64).reshape(-1, self.ny, self.nx)
@@ -423,16 +450,17 @@ class Solver:
             return dict(z=a[0:9], h=a[9:14], phiu=a[14:16])
         out = {}
         k = 0
+        keep = 0.0 if deviations else 1.0
         if p.get("flow", 9):
             w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
-            out["f"] = a[0:9] + w9[:, None, None] * p.get("rho0", 1000.0)
+            out["f"] = a[0:9] + keep * w9[:, None, None] * p.get("rho0", 1000.0)
             k = 9
         if p.get("thermal", 0) == 9:
             w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
-            out["g"] = a[k:k + 9] + w9[:, None, None] * p.get("T0", 300.0)
+            out["g"] = a[k:k + 9] + keep * w9[:, None, None] * p.get("T0", 300.0)
         elif p.get("thermal", 0):
             w5 = np.array([1 / 3] + [1 / 6] * 4)
-            out["g"] = a[k:k + 5] + w5[:, None, None] * p.get("T0", 300.0)
+            out["g"] = a[k:k + 5] + keep * w5[:, None, None] * p.get("T0", 300.0)
         return out
 
 

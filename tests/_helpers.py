@@ -11,8 +11,11 @@ W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 W5 = np.array([1 / 3] + [1 / 6] * 4)
 
 
-def run_oracle(w, steps=None, q3=None, force=None):
-    o = oracle.Oracle(w["params"])
+def run_oracle(w, steps=None, q3=None, force=None, extended=False):
+    """The oracle on workload w; ``extended`` runs it in long double, whose rounding
+    is far below the 1e-12 bar (the FP64 oracle's own floor on populations, T - T_in
+    and long runs is at or above it)."""
+    o = oracle.Oracle(w["params"], extended=extended)
     for bc in w["bcs"]:
         o.set_bc(*bc)
     if q3 is not None or force is not None or w.get("q3") is not None:
@@ -47,3 +50,8 @@ def rel_l2(a, b, ref=None):
     ref = b if ref is None else ref
     den = np.sqrt(np.sum(np.asarray(ref) ** 2))
     return np.sqrt(np.sum((np.asarray(a) - np.asarray(b)) ** 2)) / (den if den > 0 else 1.0)
+
+
+def deviations(a, w9_or_w5, ref_value):
+    """Populations minus the rest equilibrium w_i * ref (rho0 for f, T0 for g)."""
+    return np.asarray(a) - np.asarray(w9_or_w5)[:, None, None] * ref_value
