@@ -165,7 +165,8 @@ def test_autograd_function_matches_adjoint():
     L = channel_loss(q3, qwall, nu, w, steps, 25, target)
     (3.0 * L).backward()
     loss, g3, gw, gnu = _adjoint(w, steps, 25, target)
-    assert float(L.detach()) == loss
+    # forward runs lbm_step, the adjoint its own checkpointed forward: equal to rounding
+    assert abs(float(L.detach()) - loss) <= 1e-12 * loss
     np.testing.assert_array_equal(q3.grad.numpy(), 3.0 * g3)
     np.testing.assert_array_equal(qwall.grad.numpy(), 3.0 * gw)
     assert float(nu.grad) == 3.0 * gnu
