@@ -218,10 +218,37 @@ lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux, const dou
 /*
  * Advance n >= 0 time steps: fused pull-stream + boundary links + moments + collision
  * (Eqs. eq_lattice_boltzmann_geral, colisao_MRT, ...), one kernel launch per step,
- * asynchronous on the stream.
- * Errors: LBM_ERR_STATE (not initialised), LBM_ERR_CUDA.
+ * asynchronous on the stream.  With a health-check interval K > 0
+ * (lbm_set_check_interval) the call also runs the integrals of lbm_integrals each time
+ * the step count reaches a multiple of K (one stream synchronisation per check) and
+ * stops there if a cell is bad (non-finite, or |u| >= c).
+ * Errors: LBM_ERR_STATE (not initialised), LBM_ERR_CUDA, LBM_ERR_DIVERGED (a check
+ * found bad cells: the state is that of the failing step, lbm_last_good_step gives
+ * the step count of the last check that passed), LBM_ERR_TIMEOUT (see lbm_set_launch).
  */
 lbm_status lbm_step(lbm_t h, long n);
+
+/*
+ * Health check inside lbm_step (no counterpart in the paper: a run-time guard for
+ * long runs).  every = K > 0 checks at each multiple of K steps; 0 (the default)
+ * turns the checks off, keeping lbm_step fully asynchronous.  lbm_last_good_step
+ * returns the step count of the last passed check since lbm_init_fields (-1: none).
+ * Errors: LBM_ERR_ARG (every < 0).
+ */
+lbm_status lbm_set_check_interval(lbm_t h, long every);
+long lbm_last_good_step(lbm_t h);
+
+/*
+ * Wall-time limit of each wait of the TMA-staged step for its staged copies (no
+ * counterpart in the paper; default 1 s, allowed (0, 10] s).  A wait that runs out
+ * marks the handle, lets the block's copies in flight land and ends the block; the
+ * next lbm_integrals / lbm_check reports LBM_ERR_TIMEOUT once and clears the mark.
+ * The results of a step whose waits ran out are not valid: restore a state saved with
+ * lbm_get_state.  expire_next = 1 is a self-test of that failure path: in the next
+ * TMA-staged step every block first waits, with this limit, on a barrier that nothing
+ * completes, so its wait runs out.  Errors: LBM_ERR_ARG.
+ */
+lbm_status lbm_set_wait_limit(lbm_t h, double seconds, int expire_next);
 
 /*
  * Pick the launch of the single-solve step kernel by timing candidates (grid launches
@@ -250,18 +277,23 @@ lbm_status lbm_probe_fma_rate(int precision, double *gflops);
  * choice of memory pipeline for the same arithmetic).  cfg[4]:
  *  {LBM_LAUNCH_GRID, block_x, block_y, 0}: one thread per node, block_x a multiple
  *     of 32, block_x * block_y <= 256 (the default, 64 x 4);
+ *  {LBM_LAUNCH_GRID2, block_x, block_y, 0}: the same with two interior nodes per
+ *     thread along x (each block covers 2 block_x columns): one paired 8-byte (FP32)
+ *     or 16-byte (FP64) load and store per population plane for both nodes, the
+ *     x-shifted value of the pull exchanged between neighbouring lanes;
  *  {LBM_LAUNCH_TMA, tile_height (4 or 8), stages (1..4), CTAs per SM}: persistent
  *     CTAs of 32 x tile_height threads; per tile, the pulled values of every
  *     population plane arrive as tensor-memory-accelerator boxes in shared memory,
  *     `stages` tiles ahead (the first step after lbm_init_fields always uses the
  *     grid launch).  A wait for a box that runs out (about 1 s) marks the handle;
  *     the next lbm_integrals / lbm_check then fails with LBM_ERR_TIMEOUT.
- * lbm_autotune chooses among both kinds; lbm_launch_config reads the current one.
+ * lbm_autotune chooses among all three kinds; lbm_launch_config reads the current one.
  * Errors: LBM_ERR_ARG (two-phase handle, out-of-range value, more CTAs per SM than
  * fit), LBM_ERR_CUDA (the driver refused the tensor maps).
  */
 #define LBM_LAUNCH_GRID 0
 #define LBM_LAUNCH_TMA 1
+#define LBM_LAUNCH_GRID2 2
 lbm_status lbm_set_launch(lbm_t h, const int cfg[4]);
 lbm_status lbm_launch_config(lbm_t h, int cfg[4]);
 
@@ -293,7 +325,7 @@ lbm_status lbm_moments(lbm_t h, unsigned mask, double *out, int on_device);
  */
 lbm_status lbm_integrals(lbm_t h, double out[4]);
 
-/* lbm_integrals + status: LBM_ERR_DIVERGED when out[3] > 0. */
+/* lbm_integrals + status: LBM_ERR_DIVERGED when out[3] > 0 (or LBM_ERR_TIMEOUT). */
 lbm_status lbm_check(lbm_t h);
 
 /*

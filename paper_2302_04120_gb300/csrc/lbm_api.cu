@@ -3,6 +3,8 @@
 // upload, launches and status reporting.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -52,6 +54,11 @@ struct lbm_s {
   // LBM_LAUNCH_TMA (persistent CTAs of 32 x tma_ty threads, boxes staged by TMA)
   int launch_kind;
   int tma_ty, tma_stages, tma_ctas;  // tma_ctas: CTAs per SM
+  unsigned long long tma_wait_ns;    // wall-time limit of each staged-copy wait
+  int tma_expire_next;               // self-test: the next TMA-staged step's waits run out
+  // health check inside lbm_step: every `check_every` steps (0 = off); the step count
+  // of the last check that found every cell healthy (-1: none since init)
+  long check_every, last_good;
   int nsm;
   CUtensorMap tmap[2];  // one per state buffer, boxes 36 x tmap_ty
   int tmap_ty;          // 0 until encoded
@@ -68,7 +75,7 @@ struct lbm_s {
 // Everything a run of grid-launched steps depends on besides device memory contents:
 // the kernel choice and the parameter blocks of both buffer parities.
 struct StepKey {
-  int two_phase, prec, flow, th;
+  int two_phase, prec, flow, th, kind;
   dim3 block;
   double sink_conv, sink_Tinf;
   lbmk::MpParams mp[2];
@@ -343,7 +350,9 @@ extern "C" lbm_status lbm_create(const lbm_params *pin, void *stream, lbm_t *out
   h->tma_ty = 8;
   h->tma_stages = 3;
   h->tma_ctas = 2;
+  h->tma_wait_ns = 1000000000ull;
   h->tmap_ty = 0;
+  h->last_good = -1;
   if (!p.phase && (p.flow || p.thermal)) {
     int fk = p.flow ? (p.flow_op == LBM_MRT ? lbmk::FLOW_MRT : lbmk::FLOW_BGK) : lbmk::FLOW_NONE;
     int tk = th_kind(p);
@@ -576,6 +585,7 @@ extern "C" lbm_status lbm_init_fields(lbm_t h, const double *a, const double *ux
   h->cur = 0;
   h->pre = 1;  // buffer 0 holds f(0) itself; the first step collides it in place
   h->steps = 0;
+  h->last_good = -1;
   h->initialised = 1;
   if (!on_device) CU(h, cudaStreamSynchronize(h->stream));
   return LBM_OK;
@@ -603,6 +613,7 @@ static cudaError_t launch_grid_step(const lbm_t h, int from, int flow, int th, c
   if (two_phase(h)) return lbmk::mp_step(mp_params(h, from), h->p.precision, st);
   const cudaError_t e = sink_refresh(h, from, 0, st);
   if (e != cudaSuccess) return e;
+  if (h->launch_kind == LBM_LAUNCH_GRID2) return lbmk::sp_step2(sp_params(h, from), h->p.precision, flow, th, h->block, st);
   return lbmk::sp_step(sp_params(h, from), h->p.precision, flow, th, h->block, st);
 }
 
@@ -612,6 +623,7 @@ static void step_key(const lbm_t h, int flow, int th, StepKey *k) {
   k->prec = h->p.precision;
   k->flow = flow;
   k->th = th;
+  k->kind = h->launch_kind;
   k->block = h->block;
   k->sink_conv = h->sink_conv;
   k->sink_Tinf = h->sink_Tinf;
@@ -653,10 +665,7 @@ static cudaGraphExec_t step_graph(lbm_t h, int flow, int th) {
   return x;
 }
 
-extern "C" lbm_status lbm_step(lbm_t h, long n) {
-  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
-  if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
-  if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_init_fields has not been called");
+static lbm_status advance(lbm_t h, long n) {
   int flow, th;
   sp_kinds(h, &flow, &th);
   for (long s = 0; s < n;) {
@@ -682,10 +691,12 @@ extern "C" lbm_status lbm_step(lbm_t h, long n) {
     } else if (h->launch_kind == LBM_LAUNCH_TMA && !h->pre) {
       SpParams P = sp_params(h, h->cur);
       e = lbmk::sp_step_tma(P, h->tmap[h->cur], h->p.precision, flow, th, h->tma_ty, h->tma_stages,
-                            h->nsm * h->tma_ctas, step_flag(h), h->stream);
+                            h->nsm * h->tma_ctas, step_flag(h), h->tma_wait_ns, h->tma_expire_next, h->stream);
+      h->tma_expire_next = 0;
     } else {
       SpParams P = sp_params(h, h->cur);
-      e = lbmk::sp_step(P, h->p.precision, flow, th, h->block, h->stream);
+      e = h->launch_kind == LBM_LAUNCH_GRID2 ? lbmk::sp_step2(P, h->p.precision, flow, th, h->block, h->stream)
+                                             : lbmk::sp_step(P, h->p.precision, flow, th, h->block, h->stream);
     }
     if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     h->cur = 1 - h->cur;
@@ -693,6 +704,47 @@ extern "C" lbm_status lbm_step(lbm_t h, long n) {
     h->steps++;
     s++;
   }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_t h, long n) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  if (n < 0) return fail(h, LBM_ERR_ARG, "n must be >= 0");
+  if (!h->initialised) return fail(h, LBM_ERR_STATE, "lbm_init_fields has not been called");
+  if (h->check_every <= 0) return advance(h, n);
+  // health check at every multiple of check_every of the step count
+  while (n > 0) {
+    const long k = std::min(n, h->check_every - h->steps % h->check_every);
+    lbm_status st = advance(h, k);
+    if (st != LBM_OK) return st;
+    n -= k;
+    if (h->steps % h->check_every == 0) {
+      double v[4];
+      st = lbm_integrals(h, v);
+      if (st != LBM_OK) return st;
+      if (v[3] > 0)
+        return fail(h, LBM_ERR_DIVERGED, "%.0f cells non-finite or |u| >= c at step %ld; last healthy check at step %ld",
+                    v[3], h->steps, h->last_good);
+      h->last_good = h->steps;
+    }
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_check_interval(lbm_t h, long every) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  if (every < 0) return fail(h, LBM_ERR_ARG, "the check interval must be >= 0 (0 = off)");
+  h->check_every = every;
+  return LBM_OK;
+}
+
+extern "C" long lbm_last_good_step(lbm_t h) { return h ? h->last_good : -1; }
+
+extern "C" lbm_status lbm_set_wait_limit(lbm_t h, double seconds, int expire_next) {
+  if (!h) return fail(h, LBM_ERR_ARG, "NULL handle");
+  if (!(seconds > 0) || seconds > 10.0) return fail(h, LBM_ERR_ARG, "wait limit must lie in (0, 10] s");
+  h->tma_wait_ns = (unsigned long long)(seconds * 1e9);
+  h->tma_expire_next = expire_next ? 1 : 0;
   return LBM_OK;
 }
 
@@ -752,7 +804,11 @@ extern "C" lbm_status lbm_integrals(lbm_t h, double out[4]) {
   memcpy(out, h->h_out4, 4 * sizeof(double));
   int flag;
   memcpy(&flag, h->h_out4 + 4, sizeof(int));
-  if (flag) return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged copies (flag %d)", flag);
+  if (flag) {  // reported once: clear it for the steps that follow
+    CU(h, cudaMemsetAsync(step_flag(h), 0, sizeof(int), h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    return fail(h, LBM_ERR_TIMEOUT, "a step kernel gave up waiting for its staged copies (flag %d)", flag);
+  }
   return LBM_OK;
 }
 
@@ -1271,7 +1327,7 @@ static lbm_status ensure_tmaps(lbm_t h, int ty) {
 
 static lbm_status check_launch(lbm_t h, const int cfg[4]) {
   if (two_phase(h)) return fail(h, LBM_ERR_ARG, "two-phase solves use a fixed 32 x 8 tile");
-  if (cfg[0] == LBM_LAUNCH_GRID) {
+  if (cfg[0] == LBM_LAUNCH_GRID || cfg[0] == LBM_LAUNCH_GRID2) {
     if (cfg[1] < 32 || cfg[1] % 32 != 0 || cfg[2] < 1 || cfg[1] * cfg[2] > 256)
       return fail(h, LBM_ERR_ARG, "grid launch: block_x a multiple of 32, block_x * block_y <= 256");
     return LBM_OK;
@@ -1286,12 +1342,12 @@ static lbm_status check_launch(lbm_t h, const int cfg[4]) {
       return fail(h, LBM_ERR_ARG, "TMA launch: 1..%d CTAs per SM fit for this tile and stage count", occ);
     return ensure_tmaps(h, cfg[1]);
   }
-  return fail(h, LBM_ERR_ARG, "launch kind must be LBM_LAUNCH_GRID or LBM_LAUNCH_TMA");
+  return fail(h, LBM_ERR_ARG, "launch kind must be LBM_LAUNCH_GRID, LBM_LAUNCH_GRID2 or LBM_LAUNCH_TMA");
 }
 
 static void apply_launch(lbm_t h, const int cfg[4]) {
   h->launch_kind = cfg[0];
-  if (cfg[0] == LBM_LAUNCH_GRID) {
+  if (cfg[0] != LBM_LAUNCH_TMA) {
     h->block = dim3(cfg[1], cfg[2]);
   } else {
     h->tma_ty = cfg[1];
@@ -1311,7 +1367,7 @@ extern "C" lbm_status lbm_set_launch(lbm_t h, const int cfg[4]) {
 extern "C" lbm_status lbm_launch_config(lbm_t h, int cfg[4]) {
   if (!h || !cfg) return fail(h, LBM_ERR_ARG, "NULL argument");
   cfg[0] = h->launch_kind;
-  if (h->launch_kind == LBM_LAUNCH_GRID) {
+  if (h->launch_kind != LBM_LAUNCH_TMA) {
     cfg[1] = (int)h->block.x;
     cfg[2] = (int)h->block.y;
     cfg[3] = 0;
@@ -1333,10 +1389,11 @@ extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
   int cands[64][4];
   int nc = 0;
   static const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
-  for (const auto &sh : shapes) {
-    cands[nc][0] = LBM_LAUNCH_GRID; cands[nc][1] = sh[0]; cands[nc][2] = sh[1]; cands[nc][3] = 0;
-    nc++;
-  }
+  for (int kind = LBM_LAUNCH_GRID; kind <= LBM_LAUNCH_GRID2; kind += LBM_LAUNCH_GRID2 - LBM_LAUNCH_GRID)
+    for (const auto &sh : shapes) {
+      cands[nc][0] = kind; cands[nc][1] = sh[0]; cands[nc][2] = sh[1]; cands[nc][3] = 0;
+      nc++;
+    }
   for (int ty = 4; ty <= 8; ty += 4)
     for (int stages = 2; stages <= 4; stages++) {
       int occ = lbmk::sp_tma_occupancy(h->p.precision, flow, th, ty, stages);
@@ -1361,8 +1418,9 @@ extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
     if (cf[0] == LBM_LAUNCH_TMA && ensure_tmaps(h, cf[1]) != LBM_OK) continue;  // TMA unavailable: grid only
     auto launch = [&]() -> cudaError_t {
       if (cf[0] == LBM_LAUNCH_GRID) return lbmk::sp_step(P, h->p.precision, flow, th, dim3(cf[1], cf[2]), h->stream);
+      if (cf[0] == LBM_LAUNCH_GRID2) return lbmk::sp_step2(P, h->p.precision, flow, th, dim3(cf[1], cf[2]), h->stream);
       return lbmk::sp_step_tma(P, h->tmap[h->cur], h->p.precision, flow, th, cf[1], cf[2], h->nsm * cf[3],
-                               step_flag(h), h->stream);
+                               step_flag(h), h->tma_wait_ns, 0, h->stream);
     };
     cudaError_t e = launch();  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -1383,8 +1441,8 @@ extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
     apply_launch(h, cands[bestc]);
   }
   if (out_block) {
-    out_block[0] = h->launch_kind == LBM_LAUNCH_GRID ? (int)h->block.x : 32;
-    out_block[1] = h->launch_kind == LBM_LAUNCH_GRID ? (int)h->block.y : h->tma_ty;
+    out_block[0] = h->launch_kind != LBM_LAUNCH_TMA ? (int)h->block.x : 32;
+    out_block[1] = h->launch_kind != LBM_LAUNCH_TMA ? (int)h->block.y : h->tma_ty;
   }
   return LBM_OK;
 }

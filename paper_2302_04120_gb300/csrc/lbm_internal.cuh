@@ -88,6 +88,8 @@ struct ThLat {
 
 // Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
+// The same step with two interior nodes per thread along x (block.x a multiple of 32).
+cudaError_t sp_step2(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
 // qdot of the lagged heat sink for the step reading `src` (csrc/sink.cu): qnext =
 // qbase - conv (T(t - dt) - T_inf), T(t - dt) rebuilt from src and qprev (pre: src
 // holds the initial state itself).  Storage precision fields, one plane each.
@@ -105,13 +107,15 @@ int sp_batch_occupancy(int prec, int flow, int th, int threads);
 // returns 0, or nonzero when the driver refuses it.  sp_tma_prepare raises the
 // dynamic shared-memory limit of the kernels of one (prec, flow, th).  The step
 // runs `grid` CTAs of 32 x ty threads with `stages` (1..4) slots of boxes in
-// flight; flag (device int) receives 1 if a copy wait ran out.  P.local must be 0.
+// flight; flag (device int) receives 1 if a copy wait ran out (each ring wait is
+// limited to wait_ns of wall time; expire_probe makes every block's first wait run
+// out, a self-test of that path).  P.local must be 0.
 int sp_tma_encode(void *base, int pitch, int ny, int nq, int elem, int ty, CUtensorMap *out);
 cudaError_t sp_tma_prepare(int prec, int flow, int th);
 int sp_tma_occupancy(int prec, int flow, int th, int ty, int stages);
 size_t sp_tma_smem(int prec, int flow, int th, int ty, int stages);
 cudaError_t sp_step_tma(const SpParams &P, const CUtensorMap &map, int prec, int flow, int th, int ty, int stages,
-                        int grid, int *flag, cudaStream_t s);
+                        int grid, int *flag, unsigned long long wait_ns, int expire_probe, cudaStream_t s);
 // Equilibrium initialisation (pre-collision state of time 0) from double fields (device).
 cudaError_t sp_init(const SpParams &P, int prec, int flow, int th, const double *a,
                     const double *ux, const double *uy, const double *b, dim3 block,

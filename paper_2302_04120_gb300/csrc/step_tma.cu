@@ -14,7 +14,7 @@ namespace lbmk {
 template <int PREC, int FLOW, int TH>
 struct TmaOps {
   static cudaError_t step(const SpParams &P, const CUtensorMap &map, int ty, int stages, int grid, int *flag,
-                          cudaStream_t s);
+                          unsigned long long wait_ns, int expire_probe, cudaStream_t s);
   static cudaError_t prepare();
   static int occupancy(int ty, int stages);
 };
@@ -47,9 +47,9 @@ int sp_tma_encode(void *base, int pitch, int ny, int nq, int elem, int ty, CUten
 }
 
 cudaError_t sp_step_tma(const SpParams &P, const CUtensorMap &map, int prec, int flow, int th, int ty, int stages,
-                        int grid, int *flag, cudaStream_t s) {
+                        int grid, int *flag, unsigned long long wait_ns, int expire_probe, cudaStream_t s) {
   if (stages < 1 || stages > kMaxStages || grid < 1 || P.local) return cudaErrorInvalidValue;
-#define CALL(A, B, C) return TmaOps<A, B, C>::step(P, map, ty, stages, grid, flag, s)
+#define CALL(A, B, C) return TmaOps<A, B, C>::step(P, map, ty, stages, grid, flag, wait_ns, expire_probe, s)
   LBM_SP_DISPATCH(prec, flow, th, CALL);
 #undef CALL
   return cudaErrorInvalidValue;

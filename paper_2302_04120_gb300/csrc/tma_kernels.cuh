@@ -17,9 +17,9 @@
 //   * interior nodes read their nine (five) pulled values from shared memory;
 //     nodes on the domain edge take the global-memory boundary path of k_step;
 //   * post-collision values are stored straight to global memory, coalesced.
-// Every mbarrier wait is bounded (about one second of wall time); a wait that runs
-// out sets a flag the host reads, lets the block's copies in flight land and
-// returns.
+// Every mbarrier wait is bounded (one second of wall time by default, settable per
+// handle); a wait that runs out sets a flag the host reads, lets the block's copies
+// in flight land (bounded again, one second) and returns.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -35,7 +35,7 @@ namespace lbmk {
 template <int PREC, int FLOW, int TH>
 struct TmaOps {
   static cudaError_t step(const SpParams &P, const CUtensorMap &map, int ty, int stages, int grid, int *flag,
-                          cudaStream_t s);
+                          unsigned long long wait_ns, int expire_probe, cudaStream_t s);
   static cudaError_t prepare();
   static int occupancy(int ty, int stages);
 };
@@ -75,14 +75,18 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Wait for the phase of parity `parity` of barrier b; false after about one second
-// of wall time (or 2^28 tries, whichever comes first).
-static __device__ __noinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity) {
+// Wall-time limit of the wait that lets a block's copies in flight land before it
+// exits after a failed wait (always the full second).
+constexpr uint64_t kDrainWaitNs = 1000000000ull;
+
+// Wait for the phase of parity `parity` of barrier b; false after limit_ns of wall
+// time (or 2^28 tries, whichever comes first).
+static __device__ __noinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 28); ++it) {
     if (mbar_try_wait(b, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > 1000000000ull) return false;
+    if ((it & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -157,8 +161,12 @@ __device__ __forceinline__ void step_node_staged(const SpParams &P, int i, int j
 }
 
 template <int PREC, int FLOW, int TH, int TY>
+// wait_ns: wall-time limit of each ring wait.  expire_probe (self-test of the timeout
+// path): each block first waits, with that limit, on a barrier of its own that nothing
+// completes, so the wait runs out and the block takes the failure path below.
 __global__ void __launch_bounds__(kTileX *TY) k_step_tma(const SpParams P, const __grid_constant__ CUtensorMap map,
-                                                         int ntx, int ntiles, int nstages, int *flag) {
+                                                         int ntx, int ntiles, int nstages, int *flag,
+                                                         unsigned long long wait_ns, int expire_probe) {
   typedef typename Prec<PREC>::S S;
   constexpr int NF = Planes<FLOW, TH>::F;
   constexpr int NQ = Planes<FLOW, TH>::N;
@@ -170,10 +178,12 @@ __global__ void __launch_bounds__(kTileX *TY) k_step_tma(const SpParams P, const
   // slots start 128-byte aligned (the dynamic size carries 128 bytes of slack)
   unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t never;  // expire_probe only: no thread or copy completes it
   const int tid = threadIdx.y * kTileX + threadIdx.x;
   const int G = gridDim.x;
   if (tid == 0) {
     for (int s = 0; s < nstages; s++) mbar_init(&full[s], 1);
+    if (expire_probe) mbar_init(&never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -204,13 +214,15 @@ __global__ void __launch_bounds__(kTileX *TY) k_step_tma(const SpParams P, const
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
     const int s = k % nstages;
-    const bool ok = mbar_wait_bounded(&full[s], (uint32_t)(k / nstages) & 1u);
+    bool ok = true;
+    if (expire_probe && k == 0) ok = mbar_wait_bounded(&never, 0u, wait_ns);
+    if (ok) ok = mbar_wait_bounded(&full[s], (uint32_t)(k / nstages) & 1u, wait_ns);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(flag, 1);
         // let the copies this block still has in flight land before it exits
         for (int kk = k; kk < k + nstages && blockIdx.x + kk * G < ntiles; ++kk)
-          mbar_wait_bounded(&full[kk % nstages], (uint32_t)(kk / nstages) & 1u);
+          mbar_wait_bounded(&full[kk % nstages], (uint32_t)(kk / nstages) & 1u, kDrainWaitNs);
       }
       __syncthreads();
       return;
@@ -234,12 +246,13 @@ size_t smem_bytes(int stages) {
 }
 
 template <int PREC, int FLOW, int TH, int TY>
-cudaError_t launch(const SpParams &P, const CUtensorMap &map, int stages, int grid, int *flag, cudaStream_t s) {
+cudaError_t launch(const SpParams &P, const CUtensorMap &map, int stages, int grid, int *flag,
+                   unsigned long long wait_ns, int expire_probe, cudaStream_t s) {
   const int ntx = (P.nx + kTileX - 1) / kTileX, nty = (P.ny + TY - 1) / TY;
   const int ntiles = ntx * nty;
   if (grid > ntiles) grid = ntiles;
-  k_step_tma<PREC, FLOW, TH, TY>
-      <<<grid, dim3(kTileX, TY), smem_bytes<PREC, FLOW, TH, TY>(stages), s>>>(P, map, ntx, ntiles, stages, flag);
+  k_step_tma<PREC, FLOW, TH, TY><<<grid, dim3(kTileX, TY), smem_bytes<PREC, FLOW, TH, TY>(stages), s>>>(
+      P, map, ntx, ntiles, stages, flag, wait_ns, expire_probe);
   return cudaGetLastError();
 }
 
@@ -262,9 +275,9 @@ int occupancy(int stages) {
 
 template <int PREC, int FLOW, int TH>
 cudaError_t TmaOps<PREC, FLOW, TH>::step(const SpParams &P, const CUtensorMap &map, int ty, int stages, int grid,
-                                         int *flag, cudaStream_t s) {
-  if (ty == 4) return tma::launch<PREC, FLOW, TH, 4>(P, map, stages, grid, flag, s);
-  if (ty == 8) return tma::launch<PREC, FLOW, TH, 8>(P, map, stages, grid, flag, s);
+                                         int *flag, unsigned long long wait_ns, int expire_probe, cudaStream_t s) {
+  if (ty == 4) return tma::launch<PREC, FLOW, TH, 4>(P, map, stages, grid, flag, wait_ns, expire_probe, s);
+  if (ty == 8) return tma::launch<PREC, FLOW, TH, 8>(P, map, stages, grid, flag, wait_ns, expire_probe, s);
   return cudaErrorInvalidValue;
 }
 

@@ -25,7 +25,7 @@ LBM_FP64, LBM_FP32DEV = 0, 1
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE, LBM_BC_SYMMETRY = 0, 1, 2, 3, 4
 LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW, LBM_TBC_SYMMETRY, LBM_TBC_WETNODE = 0, 1, 2, 3, 4, 5
 LBM_RHO, LBM_UX, LBM_UY, LBM_T, LBM_P, LBM_PHI = 1, 2, 4, 8, 16, 32
-LBM_LAUNCH_GRID, LBM_LAUNCH_TMA = 0, 1
+LBM_LAUNCH_GRID, LBM_LAUNCH_TMA, LBM_LAUNCH_GRID2 = 0, 1, 2
 _MOMENT_BITS = [("rho", 1), ("ux", 2), ("uy", 4), ("T", 8), ("p", 16), ("phi", 32)]
 
 
@@ -125,6 +125,12 @@ def _extra_signatures(L):
     L.lbm_launch_config.restype = C.c_int
     L.lbm_adjoint.argtypes = [C.c_void_p, C.c_long, C.c_int, C.c_void_p, _dp, C.c_void_p, C.c_void_p, _dp]
     L.lbm_adjoint.restype = C.c_int
+    L.lbm_set_check_interval.argtypes = [C.c_void_p, C.c_long]
+    L.lbm_set_check_interval.restype = C.c_int
+    L.lbm_last_good_step.argtypes = [C.c_void_p]
+    L.lbm_last_good_step.restype = C.c_long
+    L.lbm_set_wait_limit.argtypes = [C.c_void_p, C.c_double, C.c_int]
+    L.lbm_set_wait_limit.restype = C.c_int
 
 
 def _check(h, st):
@@ -266,6 +272,18 @@ def lbm_probe_fma_rate(precision):
     out = C.c_double(0.0)
     _check(None, lib().lbm_probe_fma_rate(int(precision), C.byref(out)))
     return out.value
+
+
+def lbm_set_check_interval(h, every):
+    _check(h, lib().lbm_set_check_interval(h, int(every)))
+
+
+def lbm_last_good_step(h):
+    return lib().lbm_last_good_step(h)
+
+
+def lbm_set_wait_limit(h, seconds, expire_next=False):
+    _check(h, lib().lbm_set_wait_limit(h, float(seconds), int(bool(expire_next))))
 
 
 def lbm_set_launch(h, cfg):
@@ -419,7 +437,8 @@ class Solver:
         return blk[0], blk[1]
 
     def set_launch(self, kind, a, b, c=0):
-        """(LBM_LAUNCH_GRID, block_x, block_y) or (LBM_LAUNCH_TMA, tile_height, stages, ctas_per_sm)."""
+        """(LBM_LAUNCH_GRID or LBM_LAUNCH_GRID2, block_x, block_y) or (LBM_LAUNCH_TMA, tile_height, stages,
+        ctas_per_sm)."""
         lbm_set_launch(self.h, (kind, a, b, c))
 
     def launch_config(self):
@@ -427,6 +446,16 @@ class Solver:
 
     def check(self):
         return lbm_check(self.h)
+
+    def set_check_interval(self, every):
+        lbm_set_check_interval(self.h, every)
+
+    @property
+    def last_good_step(self):
+        return lbm_last_good_step(self.h)
+
+    def set_wait_limit(self, seconds, expire_next=False):
+        lbm_set_wait_limit(self.h, seconds, expire_next)
 
     def constants(self):
         return lbm_constants(self.h)
