@@ -308,9 +308,16 @@ __device__ __forceinline__ void reduce4_block(double v[4], double *out) {
   }
 }
 
+// Resident 32 x 8 blocks per SM asked of the compiler for the FP32 form: 5 caps it
+// at 48 registers (the unbounded build takes 56, i.e. 4 blocks), more warps to cover
+// the HBM latency of the pulls.
+#ifndef LBM_MP_FP32_BLOCKS_PER_SM
+#define LBM_MP_FP32_BLOCKS_PER_SM 5
+#endif
+
 // pass 2 (and its init / moments / integrals variants)
 template <int PREC, int MODE, int BY>
-__global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const double *A, const double *UX,
+__global__ void __launch_bounds__(BX * BY, (PREC == 1 && BY == 8) ? LBM_MP_FP32_BLOCKS_PER_SM : 0) k_mp_collide(const MpParams P, const double *A, const double *UX,
                                                          const double *UY, const double *B, unsigned mask,
                                                          double *out) {
   typedef typename Prec<PREC>::S S;
@@ -332,6 +339,23 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
   } else {
     pull_h<S, R>(P, src, stencil_node(i, P.nx, P.xwall), stencil_node(j, P.ny, P.ywall), h);
   }
+  // the node's z, (phi u)_prev and force do not depend on the tile: their loads are
+  // issued here, so that they are in flight during the halo pulls and the barrier
+  const long long n = (long long)j * P.pitch + i;
+  R z[9];
+  R prevx = 0, prevy = 0, fex = 0, fey = 0;
+  if (live) {
+    if (P.force) {
+      fex = (R)((const S *)P.force)[n];
+      fey = (R)((const S *)P.force)[P.plane + n];
+    }
+    if (inner) pull_z_at<S, R>(P, src + n, z);
+    else pull_z<S, R>(P, src, i, j, z);
+    if (MODE == MODE_STEP) {
+      prevx = (R)src[14ll * P.plane + n];
+      prevy = (R)src[15ll * P.plane + n];
+    }
+  }
   tile[threadIdx.y + 1][threadIdx.x + 1] = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
   constexpr int kHalo = 2 * (BX + 2) + 2 * BY;
   for (int t = tid; t < kHalo; t += BX * BY) {
@@ -351,18 +375,6 @@ __global__ void __launch_bounds__(BX * BY) k_mp_collide(const MpParams P, const 
   __syncthreads();
   double red[4] = {0.0, 0.0, 0.0, 0.0};
   if (live) {
-    const long long n = (long long)j * P.pitch + i;
-    R z[9];
-    R prevx, prevy;
-    R fex = 0, fey = 0;
-    if (P.force) {
-      fex = (R)((const S *)P.force)[n];
-      fey = (R)((const S *)P.force)[P.plane + n];
-    }
-    if (inner) pull_z_at<S, R>(P, src + n, z);
-    else pull_z<S, R>(P, src, i, j, z);
-    prevx = (R)src[14ll * P.plane + n];
-    prevy = (R)src[15ll * P.plane + n];
     MpMacro<R> m;
     mp_macro<R>(P, tile, threadIdx.x + 1, threadIdx.y + 1, z, fex, fey, m);
     if (MODE == MODE_STEP) {
