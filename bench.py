@@ -384,12 +384,14 @@ def _fp64_alu(cells, avg_s, fma64_gflops):
 
 
 def _kernel_tag(launch):
-    return "k_step_tma" if launch[0] == 1 else "k_step_split"
+    return {1: "k_step_tma", 2: "k_step_split2"}.get(launch[0], "k_step_split")
 
 
 def _kernel_name(launch):
     if launch[0] == 1:
         return f"k_step_tma<1,FLOW_MRT,TH_MRT,{launch[1]}>"
+    if launch[0] == 2:
+        return "k_step_split2<1,FLOW_MRT,TH_MRT>"
     return "k_step_split<1,FLOW_MRT,TH_MRT>"
 
 
@@ -398,7 +400,7 @@ def _parse_launch(text):
     if not text:
         return None
     parts = text.split(",")
-    kind = {"grid": 0, "tma": 1}[parts[0]]
+    kind = {"grid": 0, "tma": 1, "grid2": 2}[parts[0]]
     vals = [int(v) for v in parts[1:]] + [0] * (4 - len(parts))
     return (kind, vals[0], vals[1], vals[2])
 
@@ -406,6 +408,8 @@ def _parse_launch(text):
 def _launch_desc(launch):
     if launch[0] == 1:
         return {"kind": "tma", "tile": [32, launch[1]], "stages": launch[2], "ctas_per_sm": launch[3]}
+    if launch[0] == 2:
+        return {"kind": "grid2", "block": [launch[1], launch[2]], "nodes_per_thread": 2}
     return {"kind": "grid", "block": [launch[1], launch[2]]}
 
 
@@ -443,9 +447,28 @@ def run_ours(args):
     launch = _parse_launch(args.launch)
     from paper_2302_04120_gb300 import lbm
 
+    def wl_adjoint():
+        from paper_2302_04120_gb300 import workloads as wl
+        return wl.adjoint_channel()
+
     def wl_bubble(n):
         from paper_2302_04120_gb300 import workloads as wl
         return wl.bubble(n=n, R_cells=n / 8, W_cells=5.0, steps=0)
+    if args.profile_adjoint:
+        import numpy as np
+        w = wl_adjoint()
+        s2 = lbm.Solver(w["params"], precision=0, stream=stream.cuda_stream)
+        for bc in w["bcs"]:
+            s2.set_bc(*bc)
+        s2.set_source(w["q3"], None)
+        s2.init(**w["init"])
+        ny = w["params"]["ny"]
+        target = np.full(ny, 300.0) + 0.01 * np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
+        loss, _, _, gnu = lbm.lbm_adjoint(s2.h, 40, 20, target, w["params"]["nx"], ny)
+        print(json.dumps({"profile_adjoint": "channel_adjoint_1024x128_40steps", "kernel": "k_adj_step",
+                          "loss": loss, "dL_dnu": gnu}), flush=True)
+        s2.close()
+        return
     if args.profile_two_phase:
         # only a 1024 x 1024 FP32 bubble (134 MB of state, above L2), for profiler captures
         w = wl_bubble(1024)
@@ -603,13 +626,16 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-two-phase", action="store_true")
     ap.add_argument("--launch", default=None,
-                    help="fixed step launch instead of the autotuner: grid,BX,BY or tma,TY,STAGES,CTAS")
+                    help="fixed step launch instead of the autotuner: grid,BX,BY, grid2,BX,BY or tma,TY,STAGES,CTAS")
     ap.add_argument("--profile-step", action="store_true",
                     help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
     ap.add_argument("--profile-prec", type=int, default=1, choices=[0, 1],
                     help="precision of --profile-step: 1 FP32 deviation (default), 0 FP64")
     ap.add_argument("--profile-two-phase", action="store_true",
                     help="run only a 1024x1024 FP32 bubble (for ncu captures of the two-phase kernel)")
+    ap.add_argument("--profile-adjoint", action="store_true",
+                    help="run only a short gradient run on the 1024x128 grid (40 steps, checkpoints every 20; "
+                         "for ncu captures of the reverse-step kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

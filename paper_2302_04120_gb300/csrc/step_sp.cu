@@ -49,6 +49,13 @@ cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, c
   return cudaErrorInvalidValue;
 }
 
+cudaError_t sp_step2(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
+#define CALL(A, B, C) return SpOps<A, B, C>::step2(P, block, s)
+  LBM_SP_DISPATCH(prec, flow, th, CALL);
+#undef CALL
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t sp_batch_step(const SpParams *table, const int4 *tiles, int ntiles, int prec, int flow, int th, dim3 block,
                           int grid, cudaStream_t s) {
 #define CALL(A, B, C) return SpOps<A, B, C>::batch(table, tiles, ntiles, block, grid, s)
