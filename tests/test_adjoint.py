@@ -1,6 +1,8 @@
 """Reverse-time adjoint of the fused step (D2Q9 MRT + D2Q5 MRT, FP64).
 
-Checks: the loss equals the FP64 oracle's; directional derivatives of the loss
+Checks: every element of the gradient fields against the oracle's reference
+gradient (forward-mode dual numbers); the loss equals the FP64 oracle's; directional
+derivatives of the loss
 with respect to the heat-source field, the wall heat flux and the viscosity
 match central finite differences of the ORACLE's loss (relative step 1e-6) to
 1e-4 on a small channel with several checkpoint segments, and central
@@ -111,6 +113,23 @@ def test_adjoint_small_against_oracle_finite_differences():
     Lm = _oracle_loss(_with(w, nu=nu - h), target)
     fd = (Lp - Lm) / (2 * h)
     assert abs(fd - gnu) <= 1e-4 * abs(fd), (fd, gnu)
+
+
+def test_adjoint_small_elementwise_against_oracle_gradient():
+    """Every element of the GPU's gradient with respect to the heat source (40 x 12
+    cells) and the wall flux (2 x 40 wall nodes), and dL/dnu, against the oracle's
+    reference gradient: one forward-mode dual-number run of the oracle per input
+    element, exact up to rounding (pinned in test_oracle_builds.py).  Bound 1e-8
+    relative max-norm; the loss to 1e-7 (it is built from T ~ 300 K)."""
+    import oracle
+    from _helpers import rel_max
+    w, steps, target, qw = _setup_small()
+    loss, g3, gw, gnu = _adjoint(w, steps, 25, target)
+    L, r3, rw, rnu = oracle.outlet_loss_gradient(w, steps, target)
+    assert abs(loss - L) <= 1e-7 * L
+    assert rel_max(g3, r3) < 1e-8
+    assert rel_max(gw, rw) < 1e-8
+    assert abs(gnu - rnu) <= 1e-8 * abs(rnu)
 
 
 def test_adjoint_checkpoint_interval_does_not_change_the_gradient():

@@ -2,8 +2,7 @@
 D2Q5 row (Sec. 4.1 fuse with the lagged convective sink, App. B advection-diffusion
 with wet-node ends), and wet-node sides on a 2D strip.
 
-FP64: T - T_ref to 1e-12 relative max-norm (1e-11 where T_ref is 25x smaller than T
-and 1500 steps accumulate contraction differences: 1500 x 2^-53 x 25 = 4e-12).  FP32
+FP64: T - T_ref to 1e-12 relative max-norm against the oracle's long-double build.  FP32
 deviation storage: each step rounds the stored deviations once, so after N steps the
 bound is N x 2^-24 relative (1.8e-4 at 3000 steps; 5e-5 to 6e-5 measured).  Full runs
 against the closed forms: the fuse's steady state within the paper's E2 = 0.0029 %,
@@ -49,7 +48,8 @@ def _fuse():
 
 
 def _both(params, bcs, q3=None, conv=0.0, Tinf=0.0, steps=0, precision=0, moments_every=None):
-    o = oracle.Oracle(dict(params, conv_coef=conv, T_inf=Tinf))
+    # FP64 runs against the oracle's long-double build (its own rounding far below 1e-12)
+    o = oracle.Oracle(dict(params, conv_coef=conv, T_inf=Tinf), extended=precision == 0)
     s = lbm.Solver(params, precision=precision)
     for side, tkind, tw, u in bcs:
         ln = params["ny"] if side < 2 else params["nx"]
@@ -134,12 +134,16 @@ def test_wet_node_app_b_parity(precision, tol):
 @pytest.mark.parametrize("op", [0, 1])
 def test_wet_node_strip_with_source_parity(op):
     """37 x 6 strip periodic in y, wet-node x-sides at different T, uniform source,
-    prescribed oblique velocity: FP64 parity."""
+    prescribed oblique velocity: FP64 parity.  tau_T / dt = 0.50086 here: the BGK
+    non-equilibrium part changes sign and shrinks by only 0.17 % per step, so each
+    step's rounding persists for ~580 steps and any FP64 run carries ~580x the usual
+    accumulated rounding: 2.7e-12 measured against the long-double oracle (BGK;
+    MRT below 1e-12), bound 1e-11 (reading R39)."""
     params = dict(nx=37, ny=6, flow=0, thermal=5, thermal_op=op, dx=1e-3, dt=2e-3, rho0=1000.0, cp=4180.0,
                   k=0.6, T0=300.0, u_prescribed=(2e-3, 1e-3))
     bcs = [(0, lbm.LBM_TBC_WETNODE, 310.0, (2e-3, 1e-3)), (1, lbm.LBM_TBC_WETNODE, 300.0, (2e-3, 1e-3))]
     o, s = _both(params, bcs, q3=5e6, steps=1500)
-    assert rel_max(s.moments()["T"] - 300.0, o.moments()["T"] - 300.0) < 1e-11
+    assert rel_max(s.moments()["T"] - 300.0, o.moments()["T"] - 300.0) < (1e-11 if op == 0 else 1e-12)
     s.close()
 
 
