@@ -25,6 +25,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "batch_sample_seed4.n
 
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
+    if not os.path.exists(GOLDEN):
+        pytest.skip("oracle fixture not written yet: run its script under tests/golden/")
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")

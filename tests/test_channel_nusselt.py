@@ -27,6 +27,8 @@ FIELDS = os.path.join(os.path.dirname(__file__), "golden", "channel_2048x256_fie
 
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
+    if not os.path.exists(FIELDS):
+        pytest.skip("oracle fixture not written yet: run its script under tests/golden/")
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
