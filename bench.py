@@ -217,40 +217,50 @@ def _batch_run(steps, stream, torch):
 
 
 def _adjoint_run(torch):
-    """The gradient workload: 1024 x 128 channel (FP64), 2000 steps, checkpoints every
-    100; wall time of the forward alone against forward + reverse sweep (lbm_adjoint)."""
+    """The gradient workload: 1024 x 128 channel, 2000 steps, checkpoints every 100; wall
+    time of the forward alone against forward + reverse sweep (lbm_adjoint), in FP64 and
+    in the FP32 deviation form."""
     import numpy as np
     from paper_2302_04120_gb300 import lbm
     from paper_2302_04120_gb300 import workloads as wl
     w = wl.adjoint_channel()
     nx, ny, steps = 1024, 128, 2000
 
-    def fresh():
-        s = lbm.Solver(w["params"], precision=0)
+    def fresh(prec):
+        s = lbm.Solver(w["params"], precision=prec)
         for bc in w["bcs"]:
             s.set_bc(*bc)
         s.set_source(w["q3"], None)
         s.init(**w["init"])
         return s
 
-    s = fresh()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s.step(steps)
-    s.moments(lbm.LBM_T)
-    t_fwd = time.perf_counter() - t0
-    s.close()
     target = np.full(ny, 300.0) + 0.01 * np.sin(np.pi * (np.arange(ny) + 0.5) / ny)
-    s = fresh()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lbm.lbm_adjoint(s.h, steps, 100, target, nx, ny)
-    t_adj = time.perf_counter() - t0
-    s.close()
-    return dict(workload="channel_adjoint_1024x128_2000steps", forward_s=round(t_fwd, 4),
-                gradient_s=round(t_adj, 4), ratio=round(t_adj / t_fwd, 2), checkpoint_every=100,
+    res = {}
+    for prec in (0, 1):
+        s = fresh(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(steps)
+        s.moments(lbm.LBM_T)
+        t_fwd = time.perf_counter() - t0
+        s.close()
+        s = fresh(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = lbm.lbm_adjoint(s.h, steps, 100, target, nx, ny)
+        t_adj = time.perf_counter() - t0
+        s.close()
+        res[prec] = (t_fwd, t_adj, out)
+    (f64, a64, o64), (f32, a32, o32) = res[0], res[1]
+    g64, g32 = o64[1], o32[1]
+    return dict(workload="channel_adjoint_1024x128_2000steps", forward_s=round(f64, 4),
+                gradient_s=round(a64, 4), ratio=round(a64 / f64, 2), checkpoint_every=100,
                 dtype="f64", gradients="heat source per cell, wall heat flux per node, viscosity",
-                note="gradient_s covers the forward with checkpoints, the segment recomputes and the reverse sweep")
+                note="gradient_s covers the forward with checkpoints, the segment recomputes and the reverse sweep",
+                fp32=dict(forward_s=round(f32, 4), gradient_s=round(a32, 4), ratio=round(a32 / f32, 2),
+                          gradient_s_over_fp64=round(a32 / a64, 3),
+                          q3_gradient_rel_l2_vs_fp64=float(np.sqrt(np.sum((g32 - g64) ** 2) / np.sum(g64 ** 2))),
+                          nu_gradient_rel_vs_fp64=float(abs(o32[3] - o64[3]) / abs(o64[3]))))
 
 
 def _two_phase_run(steps, stream, torch):
@@ -384,14 +394,14 @@ def _fp64_alu(cells, avg_s, fma64_gflops):
 
 
 def _kernel_tag(launch):
-    return {1: "k_step_tma", 2: "k_step_split2"}.get(launch[0], "k_step_split")
+    return {1: "k_step_tma", 2: "k_step_split_occ"}.get(launch[0], "k_step_split")
 
 
 def _kernel_name(launch):
     if launch[0] == 1:
         return f"k_step_tma<1,FLOW_MRT,TH_MRT,{launch[1]}>"
     if launch[0] == 2:
-        return "k_step_split2<1,FLOW_MRT,TH_MRT>"
+        return "k_step_split<1,FLOW_MRT,TH_MRT,OCC=true>"
     return "k_step_split<1,FLOW_MRT,TH_MRT>"
 
 
@@ -400,7 +410,7 @@ def _parse_launch(text):
     if not text:
         return None
     parts = text.split(",")
-    kind = {"grid": 0, "tma": 1, "grid2": 2}[parts[0]]
+    kind = {"grid": 0, "tma": 1, "gridocc": 2}[parts[0]]
     vals = [int(v) for v in parts[1:]] + [0] * (4 - len(parts))
     return (kind, vals[0], vals[1], vals[2])
 
@@ -409,7 +419,7 @@ def _launch_desc(launch):
     if launch[0] == 1:
         return {"kind": "tma", "tile": [32, launch[1]], "stages": launch[2], "ctas_per_sm": launch[3]}
     if launch[0] == 2:
-        return {"kind": "grid2", "block": [launch[1], launch[2]], "nodes_per_thread": 2}
+        return {"kind": "grid_occ", "block": [launch[1], launch[2]], "blocks_of_256_per_sm": 6}
     return {"kind": "grid", "block": [launch[1], launch[2]]}
 
 
@@ -626,7 +636,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-two-phase", action="store_true")
     ap.add_argument("--launch", default=None,
-                    help="fixed step launch instead of the autotuner: grid,BX,BY, grid2,BX,BY or tma,TY,STAGES,CTAS")
+                    help="fixed step launch instead of the autotuner: grid,BX,BY, gridocc,BX,BY or tma,TY,STAGES,CTAS")
     ap.add_argument("--profile-step", action="store_true",
                     help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
     ap.add_argument("--profile-prec", type=int, default=1, choices=[0, 1],

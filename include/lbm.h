@@ -277,10 +277,10 @@ lbm_status lbm_probe_fma_rate(int precision, double *gflops);
  * choice of memory pipeline for the same arithmetic).  cfg[4]:
  *  {LBM_LAUNCH_GRID, block_x, block_y, 0}: one thread per node, block_x a multiple
  *     of 32, block_x * block_y <= 256 (the default, 64 x 4);
- *  {LBM_LAUNCH_GRID2, block_x, block_y, 0}: the same with two interior nodes per
- *     thread along x (each block covers 2 block_x columns): one paired 8-byte (FP32)
- *     or 16-byte (FP64) load and store per population plane for both nodes, the
- *     x-shifted value of the pull exchanged between neighbouring lanes;
+ *  {LBM_LAUNCH_GRID_OCC, block_x, block_y, 0}: the same kernel built for more
+ *     resident blocks per SM (FP32 with a thermal lattice: 6 blocks of 256 threads at
+ *     40 registers instead of 4 at 64; faster on large grids, slower on short
+ *     launches; the same kernel for the other kinds);
  *  {LBM_LAUNCH_TMA, tile_height (4 or 8), stages (1..4), CTAs per SM}: persistent
  *     CTAs of 32 x tile_height threads; per tile, the pulled values of every
  *     population plane arrive as tensor-memory-accelerator boxes in shared memory,
@@ -293,7 +293,7 @@ lbm_status lbm_probe_fma_rate(int precision, double *gflops);
  */
 #define LBM_LAUNCH_GRID 0
 #define LBM_LAUNCH_TMA 1
-#define LBM_LAUNCH_GRID2 2
+#define LBM_LAUNCH_GRID_OCC 2
 lbm_status lbm_set_launch(lbm_t h, const int cfg[4]);
 lbm_status lbm_launch_config(lbm_t h, int cfg[4]);
 
@@ -383,7 +383,10 @@ void lbm_batch_destroy(lbm_batch_t b);
 
 /*
  * Reverse-time discrete adjoint of the fused step for single-phase D2Q9 MRT + D2Q5 MRT
- * solves in FP64.  Call right after lbm_init_fields (and lbm_set_bc, lbm_set_source):
+ * solves, in the handle's precision: FP64, or FP32 (the forward in FP32 deviation
+ * storage, the adjoint variables and their arithmetic in FP32, the parameter gradients
+ * accumulated in FP64; its gradient is that of the FP32 forward map, to FP32
+ * rounding).  Call right after lbm_init_fields (and lbm_set_bc, lbm_set_source):
  * it runs the forward `steps` steps itself, keeping a checkpoint every ckpt_every
  * steps, then walks the steps backwards, recomputing each segment's states from its
  * checkpoint.  Device memory: (steps/ckpt_every + ckpt_every + 3) state buffers.  On

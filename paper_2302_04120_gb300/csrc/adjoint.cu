@@ -1,5 +1,7 @@
 // Reverse-time (discrete) adjoint of the single-phase fused step: D2Q9 MRT
-// momentum + D2Q5 MRT thermal, FP64, with the channel boundary rules
+// momentum + D2Q5 MRT thermal, FP64 or FP32 (the adjoint of the FP32 deviation
+// form: states stored as FP32 deviations, adjoint variables and arithmetic in FP32,
+// parameter gradients accumulated in FP64), with the channel boundary rules
 // (BB-velocity inlet and walls, anti-BB pressure outlet with extrapolated
 // velocity, anti-BB temperature inlet, heat-flux walls, thermal outflow).
 //
@@ -27,8 +29,6 @@ namespace lbmk {
 
 namespace {
 
-typedef double R;
-
 __device__ __forceinline__ long long nidx(const SpParams &P, int i, int j) { return (long long)j * P.pitch + i; }
 
 // The link arriving at node (i, j) along q is an ordinary streaming link (its
@@ -38,23 +38,25 @@ __device__ __forceinline__ bool streams_in(const SpParams &P, int i, int j, int 
 }
 
 // d(pre_p)/d(u_w) of the anti-BB outlet rule for outgoing direction o.
+template <typename R>
 __device__ __forceinline__ void dpre_duw(const SpParams &P, int o, R rw, R uwx, R uwy, R &gx, R &gy) {
-  const R c = P.c, ics2 = 1.0 / P.cs2;
-  const R cx = c * cx9(o), cy = c * cy9(o);
+  const R c = K<R>(P).c, ics2 = (R)1 / K<R>(P).cs2;
+  const R cx = c * (R)cx9(o), cy = c * (R)cy9(o);
   const R cu = cx * uwx + cy * uwy;
-  const R k = 2.0 * w9<R>(o) * rw;
+  const R k = (R)2 * w9<R>(o) * rw;
   gx = k * (cu * cx * ics2 * ics2 - uwx * ics2);
   gy = k * (cu * cy * ics2 * ics2 - uwy * ics2);
 }
 
 // G = sum over the outlet's unknown populations p of Lam_pre_p * d(pre_p)/d(u_w) at
 // boundary node (bi, bj) of pressure side s; also returns u_w inputs.
-__device__ void outlet_G(const SpParams &P, const R *Xt, const R *LPn, int s, int bi, int bj, R &Gx, R &Gy) {
+template <typename S, typename R>
+__device__ void outlet_G(const SpParams &P, const S *Xt, const R *LPn, int s, int bi, int bj, R &Gx, R &Gy) {
   const int ii = bi + (s == 0) - (s == 1), jj = bj + (s == 2) - (s == 3);
   R ub, vb, ui, vi;
-  post_velocity<R, R>(P, Xt, bi, bj, ub, vb);
-  post_velocity<R, R>(P, Xt, ii, jj, ui, vi);
-  const R uwx = ub + 0.5 * (ub - ui), uwy = vb + 0.5 * (vb - vi);
+  post_velocity<S, R>(P, Xt, bi, bj, ub, vb);
+  post_velocity<S, R>(P, Xt, ii, jj, ui, vi);
+  const R uwx = ub + (R)0.5 * (ub - ui), uwy = vb + (R)0.5 * (vb - vi);
   Gx = 0;
   Gy = 0;
   const long long nb = nidx(P, bi, bj);
@@ -62,7 +64,7 @@ __device__ void outlet_G(const SpParams &P, const R *Xt, const R *LPn, int s, in
   for (int p = 0; p < 9; p++) {
     if (entry_side(bi, bj, cx9(p), cy9(p), P.nx, P.ny, P.xper, P.yper) != s) continue;
     R gx, gy;
-    dpre_duw(P, opp9(p), (R)P.side[s].rho_w, uwx, uwy, gx, gy);
+    dpre_duw<R>(P, opp9(p), K<R>(P).rho_w[s], uwx, uwy, gx, gy);
     const R lam = LPn[p * P.plane + nb];
     Gx += lam * gx;
     Gy += lam * gy;
@@ -70,42 +72,46 @@ __device__ void outlet_G(const SpParams &P, const R *Xt, const R *LPn, int s, in
 }
 
 // Post-collision density and velocity of X at a node (for d u / d X).
-__device__ __forceinline__ void post_rho_u(const SpParams &P, const R *X, int i, int j, R &rho, R &ux, R &uy) {
+template <typename S, typename R>
+__device__ __forceinline__ void post_rho_u(const SpParams &P, const S *X, int i, int j, R &rho, R &ux, R &uy) {
   const long long n = nidx(P, i, j);
   R s = 0;
 #pragma unroll
-  for (int q = 0; q < 9; q++) s += X[q * P.plane + n];
-  rho = P.rho0 + s;
-  post_velocity<R, R>(P, X, i, j, ux, uy);
+  for (int q = 0; q < 9; q++) s += (R)X[q * P.plane + n];
+  rho = K<R>(P).rho0 + s;
+  post_velocity<S, R>(P, X, i, j, ux, uy);
 }
 
 }  // namespace
 
-// Loss at the outlet column and the seed Lam_pre(N).  One thread per row j.
-__global__ void k_adj_loss(const SpParams P, const double *Ttarget, double *LP, double *grad_qdot, double *loss_rows) {
+// Loss at the outlet column and the seed Lam_pre(N).  One thread per row j.  T - T_target
+// is formed in FP64 in both forms (FP32 would resolve T ~ 300 K only to ~3e-5 K).
+template <typename S, typename R>
+__global__ void k_adj_loss(const SpParams P, const double *Ttarget, R *LP, double *grad_qdot, double *loss_rows) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.ny) return;
   const int i = P.nx - 1;
-  const R *src = (const R *)P.src;
+  const S *src = (const S *)P.src;
   const bool interior = false;
   R g[5];
-  pull_g<R, R>(P, src, i, j, interior, g);
+  pull_g<S, R>(P, src, i, j, interior, g);
   const long long n = nidx(P, i, j);
-  const R qd = P.qdot ? ((const R *)P.qdot)[n] : 0.0;
-  const R T = P.T0 + ((g[0] + g[1]) + (g[2] + g[3]) + g[4]) + 0.5 * P.dt * qd;
-  const R e = T - Ttarget[j];
+  const double qd = P.qdot ? (double)((const S *)P.qdot)[n] : 0.0;
+  const double T = P.T0 + (double)((g[0] + g[1]) + (g[2] + g[3]) + g[4]) + 0.5 * P.dt * qd;
+  const double e = T - Ttarget[j];
   loss_rows[j] = e * e / P.ny;
-  const R dLdT = 2.0 * e / P.ny;
+  const double dLdT = 2.0 * e / P.ny;
   R *LPg = LP + (long long)P.gbase * P.plane;
 #pragma unroll
-  for (int q = 0; q < 5; q++) LPg[q * P.plane + n] = dLdT;
+  for (int q = 0; q < 5; q++) LPg[q * P.plane + n] = (R)dLdT;
   grad_qdot[n] += 0.5 * P.dt * dLdT;
 }
 
 // One reverse step.  P.src = X_{t-1} (P.local = 1 when t = 0), Xt = X_t,
 // LPn = Lam_pre(t+1), LP = Lam_pre(t) (output).
-__global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double *__restrict__ Xt,
-                                                  const double *__restrict__ LPn, double *__restrict__ LP,
+template <typename S, typename R>
+__global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const S *__restrict__ Xt,
+                                                  const R *__restrict__ LPn, R *__restrict__ LP,
                                                   double *grad_qdot, double *grad_flux2, double *grad_flux3,
                                                   double *nu_partials) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double
   R dsnu = 0, dsq = 0;
   if (i < P.nx && j < P.ny) {
     const long long n = nidx(P, i, j);
-    const R c = P.c, ic = 1.0 / c;
+    const R c = K<R>(P).c, ic = (R)1 / c;
     // ---- (1) Lam_X(t) = P^T Lam_pre(t+1) at this node --------------------------
     R lx[9], lg[5];
 #pragma unroll
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double
       // reflection consumer: the incoming p = opp(q) at this node built from X_q here
       const int p = opp9(q);
       const int side = entry_side(i, j, cx9(p), cy9(p), P.nx, P.ny, P.xper, P.yper);
-      if (side >= 0) acc += (P.side[side].kind == BC_PRESSURE ? -1.0 : 1.0) * LPn[p * P.plane + n];
+      if (side >= 0) acc += (P.side[side].kind == BC_PRESSURE ? (R)-1 : (R)1) * LPn[p * P.plane + n];
       lx[q] = acc;
     }
     // outlet velocity extrapolation u_w = 1.5 u(x_b) - 0.5 u(x_b - n)
@@ -141,13 +147,13 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double
                                  (s == 3 && j == P.ny - 2));
       if (!on && !inner) continue;
       R Gx, Gy;
-      if (on) outlet_G(P, Xt, LPn, s, i, j, Gx, Gy);
-      else outlet_G(P, Xt, LPn, s, bi, bj, Gx, Gy);
+      if (on) outlet_G<S, R>(P, Xt, LPn, s, i, j, Gx, Gy);
+      else outlet_G<S, R>(P, Xt, LPn, s, bi, bj, Gx, Gy);
       R rho, ux, uy;
-      post_rho_u(P, Xt, i, j, rho, ux, uy);
-      const R coef = on ? 1.5 : -0.5;
+      post_rho_u<S, R>(P, Xt, i, j, rho, ux, uy);
+      const R coef = on ? (R)1.5 : (R)-0.5;
 #pragma unroll
-      for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * cx9(q) - ux) + Gy * (c * cy9(q) - uy)) / rho;
+      for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * (R)cx9(q) - ux) + Gy * (c * (R)cy9(q) - uy)) / rho;
     }
     const R *LPng = LPn + (long long)P.gbase * P.plane;
 #pragma unroll
@@ -176,75 +182,72 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double
       const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
       if (side >= 2 && P.side[side].tkind == TBC_FLUX) {
         double *gf = side == 2 ? grad_flux2 : grad_flux3;
-        gf[i] += P.flux_coef * LPng[p * P.plane + n];
+        gf[i] += P.flux_coef * (double)LPng[p * P.plane + n];
       }
     }
 
     // ---- (2) pre(t) and the forward intermediates -----------------------------
-    const R *src = (const R *)P.src;
+    const S *src = (const S *)P.src;
     const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
     R f[9], g[5];
-    pull_f<R, R>(P, src, i, j, interior, f);
-    pull_g<R, R>(P, src, i, j, interior, g);
+    pull_f<S, R>(P, src, i, j, interior, f);
+    pull_g<S, R>(P, src, i, j, interior, g);
     Macro<R> m;
-    load_sources<R, R>(P, n, m);
+    load_sources<S, R>(P, n, m);
     moments<R, FLOW_MRT, TH_MRT>(P, f, g, m);
-    const R rho = m.rho, drho = m.drho;
+    const R rho = m.rho;
     const R hx = m.ux * ic, hy = m.uy * ic, usq = hx * hx + hy * hy;
     const R Fx = m.Fx * ic, Fy = m.Fy * ic;
-    const R dt = P.dt;
+    const R dt = K<R>(P).dt;
+    const R two = 2, three = 3, four = 4, six = 6, half = 0.5;
 
     // ---- (3) momentum MRT: transpose ------------------------------------------
     // moments of Lam_X (same integer rows as the moments of f)
     const R s14 = (lx[1] + lx[2]) + (lx[3] + lx[4]), s58 = (lx[5] + lx[6]) + (lx[7] + lx[8]);
     const R d58 = lx[5] - lx[7], d68 = lx[6] - lx[8];
-    const R M_e = -4.0 * lx[0] - s14 + 2.0 * s58;
-    const R M_ep = 4.0 * lx[0] - 2.0 * s14 + s58;
-    const R M_qx = 2.0 * (lx[3] - lx[1]) + d58 - d68;
-    const R M_qy = 2.0 * (lx[4] - lx[2]) + d58 + d68;
+    const R M_e = -four * lx[0] - s14 + two * s58;
+    const R M_ep = four * lx[0] - two * s14 + s58;
+    const R M_qx = two * (lx[3] - lx[1]) + d58 - d68;
+    const R M_qy = two * (lx[4] - lx[2]) + d58 + d68;
     const R M_xx = (lx[1] + lx[3]) - (lx[2] + lx[4]);
     const R M_xy = (lx[5] + lx[7]) - (lx[6] + lx[8]);
     // dL/dd_k = -(M Lam)_k / |row_k|^2
-    const R de = -M_e / 36.0, dep = -M_ep / 36.0, dqx = -M_qx / 12.0, dqy = -M_qy / 12.0;
-    const R dxx = -M_xx / 4.0, dxy = -M_xy / 4.0;
-    const R se = P.s_e, sep = P.s_eps, sq = P.s_q, snu = P.s_nu;
+    const R de = -M_e / (R)36, dep = -M_ep / (R)36, dqx = -M_qx / (R)12, dqy = -M_qy / (R)12;
+    const R dxx = -M_xx / four, dxy = -M_xy / four;
+    const R se = K<R>(P).s_e, sep = K<R>(P).s_eps, sq = K<R>(P).s_q, snu = K<R>(P).s_nu;
     // dL/dm_k = s_k dL/dd_k; dL/deq_k = -s_k dL/dd_k
     const R lme = se * de, lmep = sep * dep, lmqx = sq * dqx, lmqy = sq * dqy, lmxx = snu * dxx, lmxy = snu * dxy;
     // equilibria of the moments
-    const R m_s14 = (f[1] + f[2]) + (f[3] + f[4]), m_s58 = (f[5] + f[6]) + (f[7] + f[8]);
     const R mf58 = f[5] - f[7], mf68 = f[6] - f[8];
-    const R m_qx = 2.0 * (f[3] - f[1]) + mf58 - mf68, m_qy = 2.0 * (f[4] - f[2]) + mf58 + mf68;
+    const R m_qx = two * (f[3] - f[1]) + mf58 - mf68, m_qy = two * (f[4] - f[2]) + mf58 + mf68;
     const R m_xx = (f[1] + f[3]) - (f[2] + f[4]), m_xy = (f[5] + f[7]) - (f[6] + f[8]);
-    (void)m_s14;
-    (void)m_s58;
     const R eq_qx = -rho * hx, eq_qy = -rho * hy, eq_xx = rho * (hx * hx - hy * hy), eq_xy = rho * hx * hy;
     // nu enters through s_nu (stress moments) and s_q (third-order moments)
-    dsnu = dxx * ((m_xx - eq_xx) + 0.5 * dt * 2.0 * (hx * Fx - hy * Fy)) + dxy * ((m_xy - eq_xy) + 0.5 * dt * (hx * Fy + hy * Fx));
-    dsq = dqx * ((m_qx - eq_qx) - 0.5 * dt * Fx) + dqy * ((m_qy - eq_qy) - 0.5 * dt * Fy);
+    dsnu = dxx * ((m_xx - eq_xx) + half * dt * two * (hx * Fx - hy * Fy)) + dxy * ((m_xy - eq_xy) + half * dt * (hx * Fy + hy * Fx));
+    dsq = dqx * ((m_qx - eq_qx) - half * dt * Fx) + dqy * ((m_qy - eq_qy) - half * dt * Fy);
     const R le = -se * de, lep = -sep * dep, lqx = -sq * dqx, lqy = -sq * dqy, lxx = -snu * dxx, lxy = -snu * dxy;
-    R l_drho = le * (-2.0 + 3.0 * usq) + lep * (1.0 - 3.0 * usq) + lqx * (-hx) + lqy * (-hy) + lxx * (hx * hx - hy * hy) +
-               lxy * (hx * hy);
-    R l_hx = le * (6.0 * rho * hx) + lep * (-6.0 * rho * hx) + lqx * (-rho) + lxx * (2.0 * rho * hx) + lxy * (rho * hy);
-    R l_hy = le * (6.0 * rho * hy) + lep * (-6.0 * rho * hy) + lqy * (-rho) + lxx * (-2.0 * rho * hy) + lxy * (rho * hx);
+    R l_drho = le * (-two + three * usq) + lep * ((R)1 - three * usq) + lqx * (-hx) + lqy * (-hy) +
+               lxx * (hx * hx - hy * hy) + lxy * (hx * hy);
+    R l_hx = le * (six * rho * hx) + lep * (-six * rho * hx) + lqx * (-rho) + lxx * (two * rho * hx) + lxy * (rho * hy);
+    R l_hy = le * (six * rho * hy) + lep * (-six * rho * hy) + lqy * (-rho) + lxx * (-two * rho * hy) + lxy * (rho * hx);
     // forcing moments that depend on u
-    const R l_uF = -6.0 * (1.0 - 0.5 * se) * dt * de + 6.0 * (1.0 - 0.5 * sep) * dt * dep;
-    const R l_Fxx = -(1.0 - 0.5 * snu) * dt * dxx * 2.0, l_Fxy = -(1.0 - 0.5 * snu) * dt * dxy;
+    const R l_uF = -six * ((R)1 - half * se) * dt * de + six * ((R)1 - half * sep) * dt * dep;
+    const R l_Fxx = -((R)1 - half * snu) * dt * dxx * two, l_Fxy = -((R)1 - half * snu) * dt * dxy;
     l_hx += l_uF * Fx + l_Fxx * Fx + l_Fxy * Fy;
     l_hy += l_uF * Fy - l_Fxx * Fy + l_Fxy * Fx;
-    (void)drho;
 
     // ---- (4) thermal D2Q5 MRT: transpose --------------------------------------
     const R B0 = -((lg[0] + lg[1]) + (lg[2] + lg[3]) + lg[4]);
     const R B1 = -(lg[1] - lg[3]), B2 = -(lg[2] - lg[4]);
-    const R B3 = -(-4.0 * lg[0] + ((lg[1] + lg[2]) + (lg[3] + lg[4])));
+    const R B3 = -(-four * lg[0] + ((lg[1] + lg[2]) + (lg[3] + lg[4])));
     const R B4 = -((lg[1] + lg[3]) - (lg[2] + lg[4]));
-    const R t0 = B0 / 5.0, t1 = B1 / 2.0, t2 = B2 / 2.0, t3 = B3 / 20.0, t4 = B4 / 4.0;
-    const R sT = P.omegaT;
+    const R t0 = B0 / (R)5, t1 = B1 / two, t2 = B2 / two, t3 = B3 / (R)20, t4 = B4 / four;
+    const R sT = K<R>(P).omegaT;
     const R lm1 = sT * t1, lm2 = sT * t2, lm3 = t3, lm4 = t4;
-    const R lT = -sT * hx * t1 - sT * hy * t2 + (2.0 / 3.0) * t3;
+    const R lT = -sT * hx * t1 - sT * hy * t2 + (two / three) * t3;
     l_hx += -sT * m.T * t1;
     l_hy += -sT * m.T * t2;
-    grad_qdot[n] += 0.5 * dt * lT - dt * t0 + (dt / 3.0) * t3;
+    grad_qdot[n] += (double)(half * dt * lT - dt * t0 + (dt / three) * t3);
 
     // ---- (5) back to the pre-collision populations ----------------------------
     R out[14];
@@ -252,12 +255,12 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double
     for (int q = 0; q < 9; q++) {
       const int cxq = cx9(q), cyq = cy9(q);
       // transpose of the moment rows: sum_k M[k][q] lm_k
-      const R e_row = q == 0 ? -4.0 : (q <= 4 ? -1.0 : 2.0);
-      const R ep_row = q == 0 ? 4.0 : (q <= 4 ? -2.0 : 1.0);
-      const R qx_row = q == 0 ? 0.0 : (q <= 4 ? -2.0 * cxq : (R)cxq);
-      const R qy_row = q == 0 ? 0.0 : (q <= 4 ? -2.0 * cyq : (R)cyq);
-      const R xx_row = (q >= 1 && q <= 4) ? (R)(cxq * cxq - cyq * cyq) : 0.0;
-      const R xy_row = q >= 5 ? (R)(cxq * cyq) : 0.0;
+      const R e_row = q == 0 ? -four : (q <= 4 ? (R)-1 : two);
+      const R ep_row = q == 0 ? four : (q <= 4 ? -two : (R)1);
+      const R qx_row = q == 0 ? (R)0 : (q <= 4 ? -two * (R)cxq : (R)cxq);
+      const R qy_row = q == 0 ? (R)0 : (q <= 4 ? -two * (R)cyq : (R)cyq);
+      const R xx_row = (q >= 1 && q <= 4) ? (R)(cxq * cxq - cyq * cyq) : (R)0;
+      const R xy_row = q >= 5 ? (R)(cxq * cyq) : (R)0;
       R v = lx[q] + e_row * lme + ep_row * lmep + qx_row * lmqx + qy_row * lmqy + xx_row * lmxx + xy_row * lmxy;
       v += l_drho + (l_hx * ((R)cxq - hx) + l_hy * ((R)cyq - hy)) / rho;
       out[q] = v;
@@ -265,22 +268,23 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const double
 #pragma unroll
     for (int q = 0; q < 5; q++) {
       const R r1 = (R)cx5(q), r2 = (R)cy5(q);
-      const R r3 = q == 0 ? -4.0 : 1.0;
-      const R r4 = (q == 1 || q == 3) ? 1.0 : (q == 0 ? 0.0 : -1.0);
+      const R r3 = q == 0 ? -four : (R)1;
+      const R r4 = (q == 1 || q == 3) ? (R)1 : (q == 0 ? (R)0 : (R)-1);
       out[9 + q] = lg[q] + r1 * lm1 + r2 * lm2 + r3 * lm3 + r4 * lm4 + lT;
     }
 #pragma unroll
     for (int q = 0; q < 14; q++) LP[q * P.plane + n] = out[q];
   }
-  // per-block, fixed-order sums of the nu-rate sensitivities
+  // per-block, fixed-order sums of the nu-rate sensitivities (FP64)
+  double dn = (double)dsnu, dq = (double)dsq;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    dsnu += __shfl_down_sync(0xffffffffu, dsnu, o);
-    dsq += __shfl_down_sync(0xffffffffu, dsq, o);
+    dn += __shfl_down_sync(0xffffffffu, dn, o);
+    dq += __shfl_down_sync(0xffffffffu, dq, o);
   }
   __shared__ double sh[8][2];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if ((tid & 31) == 0) { sh[tid >> 5][0] = dsnu; sh[tid >> 5][1] = dsq; }
+  if ((tid & 31) == 0) { sh[tid >> 5][0] = dn; sh[tid >> 5][1] = dq; }
   __syncthreads();
   if (tid == 0) {
     double a = 0, b = 0;
@@ -303,18 +307,25 @@ __global__ void k_adj_final(const double *nu_partials, int nb, double *out2) {
   if (lane == 0) { out2[0] = a; out2[1] = b; }
 }
 
-cudaError_t adj_loss(const SpParams &P, const double *Ttarget, double *LP, double *grad_qdot, double *loss_rows,
-                     cudaStream_t s) {
-  k_adj_loss<<<(P.ny + 127) / 128, 128, 0, s>>>(P, Ttarget, LP, grad_qdot, loss_rows);
+cudaError_t adj_loss(const SpParams &P, int prec, const double *Ttarget, void *LP, double *grad_qdot,
+                     double *loss_rows, cudaStream_t s) {
+  const dim3 g((P.ny + 127) / 128), b(128);
+  if (prec == 0) k_adj_loss<double, double><<<g, b, 0, s>>>(P, Ttarget, (double *)LP, grad_qdot, loss_rows);
+  else k_adj_loss<float, float><<<g, b, 0, s>>>(P, Ttarget, (float *)LP, grad_qdot, loss_rows);
   return cudaGetLastError();
 }
 
 dim3 adj_grid(int nx, int ny) { return dim3((nx + 63) / 64, (ny + 3) / 4); }
 
-cudaError_t adj_step(const SpParams &P, const double *Xt, const double *LPn, double *LP, double *grad_qdot,
+cudaError_t adj_step(const SpParams &P, int prec, const void *Xt, const void *LPn, void *LP, double *grad_qdot,
                      double *grad_flux2, double *grad_flux3, double *nu_partials, cudaStream_t s) {
-  k_adj_step<<<adj_grid(P.nx, P.ny), dim3(64, 4), 0, s>>>(P, Xt, LPn, LP, grad_qdot, grad_flux2, grad_flux3,
-                                                          nu_partials);
+  const dim3 g = adj_grid(P.nx, P.ny), b(64, 4);
+  if (prec == 0)
+    k_adj_step<double, double><<<g, b, 0, s>>>(P, (const double *)Xt, (const double *)LPn, (double *)LP, grad_qdot,
+                                               grad_flux2, grad_flux3, nu_partials);
+  else
+    k_adj_step<float, float><<<g, b, 0, s>>>(P, (const float *)Xt, (const float *)LPn, (float *)LP, grad_qdot,
+                                             grad_flux2, grad_flux3, nu_partials);
   return cudaGetLastError();
 }
 

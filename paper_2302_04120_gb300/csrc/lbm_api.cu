@@ -613,7 +613,8 @@ static cudaError_t launch_grid_step(const lbm_t h, int from, int flow, int th, c
   if (two_phase(h)) return lbmk::mp_step(mp_params(h, from), h->p.precision, st);
   const cudaError_t e = sink_refresh(h, from, 0, st);
   if (e != cudaSuccess) return e;
-  if (h->launch_kind == LBM_LAUNCH_GRID2) return lbmk::sp_step2(sp_params(h, from), h->p.precision, flow, th, h->block, st);
+  if (h->launch_kind == LBM_LAUNCH_GRID_OCC)
+    return lbmk::sp_step_occ(sp_params(h, from), h->p.precision, flow, th, h->block, st);
   return lbmk::sp_step(sp_params(h, from), h->p.precision, flow, th, h->block, st);
 }
 
@@ -695,7 +696,7 @@ static lbm_status advance(lbm_t h, long n) {
       h->tma_expire_next = 0;
     } else {
       SpParams P = sp_params(h, h->cur);
-      e = h->launch_kind == LBM_LAUNCH_GRID2 ? lbmk::sp_step2(P, h->p.precision, flow, th, h->block, h->stream)
+      e = h->launch_kind == LBM_LAUNCH_GRID_OCC ? lbmk::sp_step_occ(P, h->p.precision, flow, th, h->block, h->stream)
                                              : lbmk::sp_step(P, h->p.precision, flow, th, h->block, h->stream);
     }
     if (e != cudaSuccess) return fail(h, LBM_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
@@ -1185,7 +1186,6 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
     if (h->bc[s] == LBM_BC_SYMMETRY || h->tbc[s] == LBM_TBC_SYMMETRY || h->tbc[s] == LBM_TBC_WETNODE)
       return fail(h, LBM_ERR_ARG, "the adjoint does not cover symmetry or wet-node sides");
   if (h->sink_conv != 0.0) return fail(h, LBM_ERR_ARG, "the adjoint does not cover the lagged sink");
-  if (p.precision != LBM_FP64) return fail(h, LBM_ERR_ARG, "the adjoint runs in FP64");
   if (p.beta_exp != 0.0) return fail(h, LBM_ERR_ARG, "the adjoint does not cover the buoyancy coupling");
   if (p.nx < 2) return fail(h, LBM_ERR_ARG, "nx must be >= 2 (loss on the x+ column)");
   if (steps < 1 || ckpt_every < 1) return fail(h, LBM_ERR_ARG, "steps and ckpt_every must be >= 1");
@@ -1193,7 +1193,9 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
     return fail(h, LBM_ERR_STATE, "call lbm_adjoint right after lbm_init_fields (it runs the forward itself)");
   const int K = ckpt_every;
   const long M = (steps + K - 1) / K;          // segments
-  const size_t sbytes = (size_t)h->nq * h->plane * sizeof(double);
+  // states and adjoint variables in the storage precision (FP64, or FP32 for the
+  // deviation form); parameter gradients in FP64
+  const size_t sbytes = (size_t)h->nq * h->plane * h->elem;
   const size_t pbytes = (size_t)h->plane * sizeof(double);
   const int nx = p.nx, ny = p.ny;
   dim3 ag = lbmk::adj_grid(nx, ny);
@@ -1226,18 +1228,21 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
     ACU(cudaMemcpyAsync(tt, T_target, sizeof(double) * ny, cudaMemcpyHostToDevice, h->stream));
     // forward with checkpoints: ck[m] = X_{mK-1} (ck[0] = pre-collision initial state)
     ACU(cudaMemcpyAsync(ck, h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice, h->stream));
-    for (long t = 0; t < steps; t++) {
-      st = lbm_step(h, 1);
+    // (whole segments through lbm_step, so that long ones replay the captured step graph)
+    for (long t = 0; t < steps;) {
+      const long k = std::min((long)K - t % K, steps - t);
+      st = lbm_step(h, k);
       if (st != LBM_OK) goto done;
-      if ((t + 1) % K == 0 && (t + 1) / K < M)
-        ACU(cudaMemcpyAsync((char *)ck + sbytes * (size_t)((t + 1) / K), h->buf[h->cur], sbytes,
-                            cudaMemcpyDeviceToDevice, h->stream));
+      t += k;
+      if (t % K == 0 && t / K < M)
+        ACU(cudaMemcpyAsync((char *)ck + sbytes * (size_t)(t / K), h->buf[h->cur], sbytes, cudaMemcpyDeviceToDevice,
+                            h->stream));
     }
     // loss at time N and the seed Lam_pre(N)
     int cur = 0;
     ACU(cudaMemsetAsync(lp, 0, sbytes * 2, h->stream));
     SpParams P = sp_params(h, h->cur);
-    ACU(lbmk::adj_loss(P, tt, lp, gq, lr, h->stream));
+    ACU(lbmk::adj_loss(P, p.precision, tt, lp, gq, lr, h->stream));
     for (long m = M - 1; m >= 0; m--) {
       const long s0 = m * K, s1 = (m + 1) * K < steps ? (m + 1) * K - 1 : steps - 1;
       // recompute X_{s0-1} .. X_{s1} into seg[0 .. s1-s0+1]
@@ -1247,7 +1252,7 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
         Q.local = (m == 0 && k == 1) ? 1 : 0;
         Q.src = (char *)seg + sbytes * (size_t)(k - 1);
         Q.dst = (char *)seg + sbytes * (size_t)k;
-        ACU(lbmk::sp_step(Q, 0, lbmk::FLOW_MRT, lbmk::TH_MRT, h->block, h->stream));
+        ACU(lbmk::sp_step(Q, p.precision, lbmk::FLOW_MRT, lbmk::TH_MRT, h->block, h->stream));
       }
       for (long t = s1; t >= s0; t--) {
         const long k = t - s0 + 1;
@@ -1255,10 +1260,10 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
         Q.local = (t == 0) ? 1 : 0;
         Q.src = (char *)seg + sbytes * (size_t)(k - 1);
         Q.dst = NULL;
-        const double *Xt = (const double *)((char *)seg + sbytes * (size_t)k);
-        double *LPn = (double *)((char *)lp + sbytes * (size_t)cur);
-        double *LPo = (double *)((char *)lp + sbytes * (size_t)(1 - cur));
-        ACU(lbmk::adj_step(Q, Xt, LPn, LPo, gq, gf, gf + nx, nup, h->stream));
+        const void *Xt = (const char *)seg + sbytes * (size_t)k;
+        void *LPn = (char *)lp + sbytes * (size_t)cur;
+        void *LPo = (char *)lp + sbytes * (size_t)(1 - cur);
+        ACU(lbmk::adj_step(Q, p.precision, Xt, LPn, LPo, gq, gf, gf + nx, nup, h->stream));
         cur = 1 - cur;
       }
     }
@@ -1327,7 +1332,7 @@ static lbm_status ensure_tmaps(lbm_t h, int ty) {
 
 static lbm_status check_launch(lbm_t h, const int cfg[4]) {
   if (two_phase(h)) return fail(h, LBM_ERR_ARG, "two-phase solves use a fixed 32 x 8 tile");
-  if (cfg[0] == LBM_LAUNCH_GRID || cfg[0] == LBM_LAUNCH_GRID2) {
+  if (cfg[0] == LBM_LAUNCH_GRID || cfg[0] == LBM_LAUNCH_GRID_OCC) {
     if (cfg[1] < 32 || cfg[1] % 32 != 0 || cfg[2] < 1 || cfg[1] * cfg[2] > 256)
       return fail(h, LBM_ERR_ARG, "grid launch: block_x a multiple of 32, block_x * block_y <= 256");
     return LBM_OK;
@@ -1342,7 +1347,7 @@ static lbm_status check_launch(lbm_t h, const int cfg[4]) {
       return fail(h, LBM_ERR_ARG, "TMA launch: 1..%d CTAs per SM fit for this tile and stage count", occ);
     return ensure_tmaps(h, cfg[1]);
   }
-  return fail(h, LBM_ERR_ARG, "launch kind must be LBM_LAUNCH_GRID, LBM_LAUNCH_GRID2 or LBM_LAUNCH_TMA");
+  return fail(h, LBM_ERR_ARG, "launch kind must be LBM_LAUNCH_GRID, LBM_LAUNCH_GRID_OCC or LBM_LAUNCH_TMA");
 }
 
 static void apply_launch(lbm_t h, const int cfg[4]) {
@@ -1389,7 +1394,7 @@ extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
   int cands[64][4];
   int nc = 0;
   static const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2}, {256, 1}};
-  for (int kind = LBM_LAUNCH_GRID; kind <= LBM_LAUNCH_GRID2; kind += LBM_LAUNCH_GRID2 - LBM_LAUNCH_GRID)
+  for (int kind = LBM_LAUNCH_GRID; kind <= LBM_LAUNCH_GRID_OCC; kind += LBM_LAUNCH_GRID_OCC - LBM_LAUNCH_GRID)
     for (const auto &sh : shapes) {
       cands[nc][0] = kind; cands[nc][1] = sh[0]; cands[nc][2] = sh[1]; cands[nc][3] = 0;
       nc++;
@@ -1418,7 +1423,8 @@ extern "C" lbm_status lbm_autotune(lbm_t h, int out_block[2]) {
     if (cf[0] == LBM_LAUNCH_TMA && ensure_tmaps(h, cf[1]) != LBM_OK) continue;  // TMA unavailable: grid only
     auto launch = [&]() -> cudaError_t {
       if (cf[0] == LBM_LAUNCH_GRID) return lbmk::sp_step(P, h->p.precision, flow, th, dim3(cf[1], cf[2]), h->stream);
-      if (cf[0] == LBM_LAUNCH_GRID2) return lbmk::sp_step2(P, h->p.precision, flow, th, dim3(cf[1], cf[2]), h->stream);
+      if (cf[0] == LBM_LAUNCH_GRID_OCC)
+        return lbmk::sp_step_occ(P, h->p.precision, flow, th, dim3(cf[1], cf[2]), h->stream);
       return lbmk::sp_step_tma(P, h->tmap[h->cur], h->p.precision, flow, th, cf[1], cf[2], h->nsm * cf[3],
                                step_flag(h), h->tma_wait_ns, 0, h->stream);
     };

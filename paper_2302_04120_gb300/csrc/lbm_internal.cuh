@@ -88,8 +88,9 @@ struct ThLat {
 
 // Launchers (step_sp.cu).  prec: 0 FP64, 1 FP32 deviation.  Return cudaGetLastError().
 cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
-// The same step with two interior nodes per thread along x (block.x a multiple of 32).
-cudaError_t sp_step2(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
+// The same step built for more resident blocks per SM (FP32 with a thermal lattice: 6
+// blocks of 256 at 40 registers instead of 4 at 64; other kinds: the same kernel).
+cudaError_t sp_step_occ(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s);
 // qdot of the lagged heat sink for the step reading `src` (csrc/sink.cu): qnext =
 // qbase - conv (T(t - dt) - T_inf), T(t - dt) rebuilt from src and qprev (pre: src
 // holds the initial state itself).  Storage precision fields, one plane each.
@@ -133,9 +134,11 @@ int sp_integral_blocks(int nx, int ny);
 cudaError_t to_storage(const double *in, void *out, int nx, int ny, int pitch, int nplanes,
                        long long plane, int prec, double scale, cudaStream_t s);
 // Adjoint (adjoint.cu): loss at the outlet column + seed, one reverse step, final sum.
-cudaError_t adj_loss(const SpParams &P, const double *Ttarget, double *LP, double *grad_qdot, double *loss_rows,
-                     cudaStream_t s);
-cudaError_t adj_step(const SpParams &P, const double *Xt, const double *LPn, double *LP, double *grad_qdot,
+// prec 0: FP64 states and adjoint variables; 1: FP32 deviation states, FP32 adjoint
+// variables (LP, LPn float); the parameter gradients are FP64 in both.
+cudaError_t adj_loss(const SpParams &P, int prec, const double *Ttarget, void *LP, double *grad_qdot,
+                     double *loss_rows, cudaStream_t s);
+cudaError_t adj_step(const SpParams &P, int prec, const void *Xt, const void *LPn, void *LP, double *grad_qdot,
                      double *grad_flux2, double *grad_flux3, double *nu_partials, cudaStream_t s);
 cudaError_t adj_final(const double *nu_partials, int nb, double *out2, cudaStream_t s);
 dim3 adj_grid(int nx, int ny);

@@ -71,9 +71,18 @@ __device__ __forceinline__ bool frame_node(int nx, int ny, int f, int &i, int &j
 // FP32 momentum-only solves move 9 values per node: at 64 registers (4 blocks of 256
 // per SM) too few bytes are in flight to cover HBM latency, so they run 6 blocks per
 // SM (40 registers, with some spilling) -- measured 0.78 -> 0.88 (BGK) and 0.83 -> 0.96
-// (MRT) of the copy bandwidth on an 8192 x 4096 grid.
-template <int PREC, int FLOW, int TH, bool SYM>
-__global__ void __launch_bounds__(256, PREC == 1 ? (TH == TH_NONE ? 6 : 4) : 3) k_step_split(const SpParams P, int fy) {
+// (MRT) of the copy bandwidth on an 8192 x 4096 grid.  FP32 solves with a thermal
+// lattice have two builds: 4 blocks per SM (64 registers, OCC = false), the faster on
+// short launches such as the 2048 x 256 channel (16.3 against 20.4 us per step), and 6
+// (40 registers, OCC = true), the faster on large grids (8192 x 4096: 549 against
+// 578 us, 1.01 against 0.96 of the measured copy bandwidth); the launch kind picks one.
+template <int PREC, bool OCC, int TH>
+constexpr int split_blocks_per_sm() {
+  return PREC == 1 ? ((TH == TH_NONE || OCC) ? 6 : 4) : 3;
+}
+
+template <int PREC, int FLOW, int TH, bool SYM, bool OCC = false>
+__global__ void __launch_bounds__(256, split_blocks_per_sm<PREC, OCC, TH>()) k_step_split(const SpParams P, int fy) {
   if ((int)blockIdx.y < fy) {
     const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
     int i, j;
@@ -84,132 +93,6 @@ __global__ void __launch_bounds__(256, PREC == 1 ? (TH == TH_NONE ? 6 : 4) : 3) 
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = (blockIdx.y - fy) * blockDim.y + threadIdx.y;
   if (i <= 0 || j <= 0 || i >= P.nx - 1 || j >= P.ny - 1) return;
   step_node<PREC, FLOW, TH, true>(P, i, j);
-}
-
-// ----------------------------------------------------------------------------
-// Two nodes per thread along x: 64-bit (FP32) or 128-bit (FP64) accesses
-// ----------------------------------------------------------------------------
-template <typename S> struct Vec2;
-template <> struct Vec2<float> { typedef float2 T; };
-template <> struct Vec2<double> { typedef double2 T; };
-
-// Pulled values of one population plane (velocity cx, source row r) for the node pair
-// (i0, i0 + 1) of a thread, i0 even: one aligned pair load of (i0, i0 + 1) at row r;
-// for cx = +1 node i0 needs column i0 - 1, the odd half of the neighbouring lane's
-// pair (a lane shuffle; lane 0 loads it), for cx = -1 node i0 + 1 needs column
-// i0 + 2, the even half of the next lane's pair (lane 31 loads it).  ic is i0 clamped
-// into the row, so that lanes past the last column read inside the row.
-template <typename S, typename R>
-__device__ __forceinline__ void pull_pair(const S *plane, long long row, int ic, int pitch, int cx, int lane, R &a,
-                                          R &b) {
-  typedef typename Vec2<S>::T V;
-  const V v = *reinterpret_cast<const V *>(plane + row + ic);
-  if (cx == 0) {
-    a = (R)v.x;
-    b = (R)v.y;
-  } else if (cx > 0) {
-    S left = __shfl_up_sync(0xffffffffu, v.y, 1);
-    if (lane == 0) left = plane[row + (ic > 0 ? ic - 1 : 0)];
-    a = (R)left;
-    b = (R)v.x;
-  } else {
-    S right = __shfl_down_sync(0xffffffffu, v.x, 1);
-    if (lane == 31) right = plane[row + (ic + 2 < pitch ? ic + 2 : pitch - 1)];
-    a = (R)v.y;
-    b = (R)right;
-  }
-}
-
-// Interior nodes (i0, j), (i0 + 1, j) of a non-local step: pull both, then moments,
-// collision and store one after the other; a pair store where both are interior,
-// else a store of the interior one.  All 32 lanes of the warp call this (shuffles).
-template <int PREC, int FLOW, int TH>
-__device__ __forceinline__ void step_pair(const SpParams &P, int i0, int j, int lane) {
-  typedef typename Prec<PREC>::S S;
-  typedef typename Prec<PREC>::R R;
-  typedef typename Vec2<S>::T V;
-  constexpr int QT = ThLat<TH>::Q;
-  const S *src = (const S *)P.src;
-  S *dst = (S *)P.dst;
-  const int ic = i0 < P.pitch - 2 ? i0 : P.pitch - 2;
-  R f0[9], f1[9], g0[9], g1[9];
-  if (FLOW != FLOW_NONE) {
-#pragma unroll
-    for (int q = 0; q < 9; q++)
-      pull_pair<S, R>(src + q * P.plane, (long long)(j - cy9(q)) * P.pitch, ic, P.pitch, cx9(q), lane, f0[q], f1[q]);
-  }
-  if (TH != TH_NONE) {
-    const S *gs = src + (long long)P.gbase * P.plane;
-#pragma unroll
-    for (int q = 0; q < QT; q++)
-      pull_pair<S, R>(gs + q * P.plane, (long long)(j - cyT(QT, q)) * P.pitch, ic, P.pitch, cxT(QT, q), lane, g0[q],
-                      g1[q]);
-  }
-  const bool live0 = i0 >= 1 && i0 <= P.nx - 2, live1 = i0 + 1 <= P.nx - 2;
-  const long long n = (long long)j * P.pitch + ic;
-  Macro<R> m0, m1;
-  load_sources<S, R>(P, n, m0);
-  load_sources<S, R>(P, n + 1, m1);
-  moments<R, FLOW, TH>(P, f0, g0, m0);
-  collide<R, FLOW, TH>(P, m0, f0, g0);
-  moments<R, FLOW, TH>(P, f1, g1, m1);
-  collide<R, FLOW, TH>(P, m1, f1, g1);
-  if (live0 && live1) {
-    if (FLOW != FLOW_NONE) {
-#pragma unroll
-      for (int q = 0; q < 9; q++) {
-        V v;
-        v.x = (S)f0[q];
-        v.y = (S)f1[q];
-        *reinterpret_cast<V *>(dst + q * P.plane + n) = v;
-      }
-    }
-    if (TH != TH_NONE) {
-      S *gd = dst + (long long)P.gbase * P.plane;
-#pragma unroll
-      for (int q = 0; q < QT; q++) {
-        V v;
-        v.x = (S)g0[q];
-        v.y = (S)g1[q];
-        *reinterpret_cast<V *>(gd + q * P.plane + n) = v;
-      }
-    }
-  } else if (live0 || live1) {
-    const long long nn = live0 ? n : n + 1;
-    if (FLOW != FLOW_NONE) {
-#pragma unroll
-      for (int q = 0; q < 9; q++) dst[q * P.plane + nn] = (S)(live0 ? f0[q] : f1[q]);
-    }
-    if (TH != TH_NONE) {
-      S *gd = dst + (long long)P.gbase * P.plane;
-#pragma unroll
-      for (int q = 0; q < QT; q++) gd[q * P.plane + nn] = (S)(live0 ? g0[q] : g1[q]);
-    }
-  }
-}
-
-// k_step_split with two interior nodes per thread along x: gridDim.x covers the row in
-// blocks of 2 blockDim.x nodes (blockDim.x a multiple of 32; the row pitch is a
-// multiple of 32 elements, so every pair starts on an 8-byte (FP32) or 16-byte (FP64)
-// boundary).  The frame blocks take one frame node per thread, as in k_step_split.
-#ifndef LBM_SPLIT2_FP32_BLOCKS_PER_SM
-#define LBM_SPLIT2_FP32_BLOCKS_PER_SM 4
-#endif
-template <int PREC, int FLOW, int TH, bool SYM>
-__global__ void __launch_bounds__(256, PREC == 1 ? LBM_SPLIT2_FP32_BLOCKS_PER_SM : 2) k_step_split2(const SpParams P,
-                                                                                                  int fy) {
-  if ((int)blockIdx.y < fy) {
-    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-    int i, j;
-    if (frame_node(P.nx, P.ny, (blockIdx.y * gridDim.x + blockIdx.x) * nt + tid, i, j))
-      step_node<PREC, FLOW, TH, false, SYM>(P, i, j);
-    return;
-  }
-  const int j = (blockIdx.y - fy) * blockDim.y + threadIdx.y;
-  if (j <= 0 || j >= P.ny - 1) return;  // uniform over the warp: one row per warp
-  const int i0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (__all_sync(0xffffffffu, i0 >= P.nx - 1)) return;  // no interior node in the warp
-  step_pair<PREC, FLOW, TH>(P, i0, j, threadIdx.x & 31);
 }
 
 // Every node in one pass (the first step after initialisation, whose pull is local).
@@ -439,15 +322,14 @@ cudaError_t SpOps<PREC, FLOW, TH>::step(const SpParams &P, dim3 block, cudaStrea
 }
 
 template <int PREC, int FLOW, int TH>
-cudaError_t SpOps<PREC, FLOW, TH>::step2(const SpParams &P, dim3 block, cudaStream_t s) {
-  if (P.local || block.x % 32 != 0) return step(P, block, s);
-  const dim3 grid((P.nx + 2 * block.x - 1) / (2 * block.x), (P.ny + block.y - 1) / block.y);
+cudaError_t SpOps<PREC, FLOW, TH>::step_occ(const SpParams &P, dim3 block, cudaStream_t s) {
+  dim3 grid = grid_for(P.nx, P.ny, block);
   const int nt = block.x * block.y;
   const int nfb = (frame_nodes(P.nx, P.ny) + nt - 1) / nt;  // frame blocks
   const int fy = (nfb + (int)grid.x - 1) / (int)grid.x;      // rows of them
-  if (grid.y + fy > 65535u) return step(P, block, s);
-  if (P.sym) k_step_split2<PREC, FLOW, TH, true><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
-  else k_step_split2<PREC, FLOW, TH, false><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
+  if (P.local || grid.y + fy > 65535u) return step(P, block, s);
+  if (P.sym) k_step_split<PREC, FLOW, TH, true, true><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
+  else k_step_split<PREC, FLOW, TH, false, true><<<dim3(grid.x, grid.y + fy), block, 0, s>>>(P, fy);
   return cudaGetLastError();
 }
 

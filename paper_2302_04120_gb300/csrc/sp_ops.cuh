@@ -17,8 +17,8 @@ constexpr int kTmaMaxStages = 4;
 template <int PREC, int FLOW, int TH>
 struct SpOps {
   static cudaError_t step(const SpParams &P, dim3 block, cudaStream_t s);
-  // the same step with two interior nodes per thread along x (paired loads/stores)
-  static cudaError_t step2(const SpParams &P, dim3 block, cudaStream_t s);
+  // the same step built for more resident blocks per SM (see split_blocks_per_sm)
+  static cudaError_t step_occ(const SpParams &P, dim3 block, cudaStream_t s);
   static cudaError_t batch(const SpParams *table, const int4 *tiles, int ntiles, dim3 block, int grid,
                            cudaStream_t s);
   static int occupancy(int threads);

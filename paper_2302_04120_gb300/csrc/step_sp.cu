@@ -49,8 +49,8 @@ cudaError_t sp_step(const SpParams &P, int prec, int flow, int th, dim3 block, c
   return cudaErrorInvalidValue;
 }
 
-cudaError_t sp_step2(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
-#define CALL(A, B, C) return SpOps<A, B, C>::step2(P, block, s)
+cudaError_t sp_step_occ(const SpParams &P, int prec, int flow, int th, dim3 block, cudaStream_t s) {
+#define CALL(A, B, C) return SpOps<A, B, C>::step_occ(P, block, s)
   LBM_SP_DISPATCH(prec, flow, th, CALL);
 #undef CALL
   return cudaErrorInvalidValue;

@@ -25,7 +25,7 @@ LBM_FP64, LBM_FP32DEV = 0, 1
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_VELOCITY, LBM_BC_PRESSURE, LBM_BC_SYMMETRY = 0, 1, 2, 3, 4
 LBM_TBC_NONE, LBM_TBC_FLUX, LBM_TBC_TEMP, LBM_TBC_OUTFLOW, LBM_TBC_SYMMETRY, LBM_TBC_WETNODE = 0, 1, 2, 3, 4, 5
 LBM_RHO, LBM_UX, LBM_UY, LBM_T, LBM_P, LBM_PHI = 1, 2, 4, 8, 16, 32
-LBM_LAUNCH_GRID, LBM_LAUNCH_TMA, LBM_LAUNCH_GRID2 = 0, 1, 2
+LBM_LAUNCH_GRID, LBM_LAUNCH_TMA, LBM_LAUNCH_GRID_OCC = 0, 1, 2
 _MOMENT_BITS = [("rho", 1), ("ux", 2), ("uy", 4), ("T", 8), ("p", 16), ("phi", 32)]
 
 
@@ -437,7 +437,7 @@ class Solver:
         return blk[0], blk[1]
 
     def set_launch(self, kind, a, b, c=0):
-        """(LBM_LAUNCH_GRID or LBM_LAUNCH_GRID2, block_x, block_y) or (LBM_LAUNCH_TMA, tile_height, stages,
+        """(LBM_LAUNCH_GRID or LBM_LAUNCH_GRID_OCC, block_x, block_y) or (LBM_LAUNCH_TMA, tile_height, stages,
         ctas_per_sm)."""
         lbm_set_launch(self.h, (kind, a, b, c))
 

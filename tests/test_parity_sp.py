@@ -319,17 +319,16 @@ def _run_launch(w, prec, launch, steps):
 @pytest.mark.parametrize("prec", [FP64, FP32])
 @pytest.mark.parametrize("nx,ny,block", [(100, 42, (32, 2)), (97, 13, (64, 1)), (33, 9, (32, 4)), (130, 7, (128, 2)),
                                          (3, 5, (32, 1))])
-def test_paired_launch_equals_grid_launch(prec, nx, ny, block):
-    """LBM_LAUNCH_GRID2 (two interior nodes per thread along x, paired loads and stores,
-    the x-shifted pull values exchanged between lanes) on ragged grids -- odd widths,
-    a pair straddling the last interior column, lanes past the row, a grid with no
-    interior pair -- against the one-node-per-thread launch: the same arithmetic, so
-    equal to rounding (1e-13 of the largest deviation in FP64, 1e-6 in FP32; the two
-    kernels may contract different operations into FMAs), and against the oracle."""
+def test_occupancy_launch_equals_grid_launch(prec, nx, ny, block):
+    """LBM_LAUNCH_GRID_OCC (the step built for 6 resident blocks per SM) on ragged grids,
+    including one without interior nodes, against the default grid launch: the same
+    arithmetic, so equal to rounding (1e-13 of the largest deviation in FP64, 1e-6 in
+    FP32; the two builds may contract different operations into FMAs), and against the
+    oracle."""
     w = wl.channel(nx=nx, ny=ny, steps=0, Re=100 * ny / 256)
     steps = 150
-    a = _run_launch(w, prec, (lbm.LBM_LAUNCH_GRID2, *block), steps)
-    assert a.launch_config()[0] == lbm.LBM_LAUNCH_GRID2
+    a = _run_launch(w, prec, (lbm.LBM_LAUNCH_GRID_OCC, *block), steps)
+    assert a.launch_config()[0] == lbm.LBM_LAUNCH_GRID_OCC
     b = _run_launch(w, prec, (lbm.LBM_LAUNCH_GRID, 64, 4), steps)
     sa, sb = a.state_arrays(deviations=True), b.state_arrays(deviations=True)
     tol = 1e-13 if prec == FP64 else 1e-6
@@ -339,11 +338,11 @@ def test_paired_launch_equals_grid_launch(prec, nx, ny, block):
     _compare_fields(o, a, T_in=w["T_in"], tol=1e-12 if prec == FP64 else 1e-5, prec=prec)
 
 
-def test_paired_launch_full_size_and_graph_replay():
-    """The 2048 x 256 workload with the paired launch, 200 steps (graph-replayed runs of
+def test_occupancy_launch_full_size_and_graph_replay():
+    """The 2048 x 256 workload with the occupancy build, 200 steps (graph-replayed runs of
     64 steps), FP32: equal to the grid launch to 1e-6 of the largest deviation."""
     w = wl.channel(steps=0)
-    a = _run_launch(w, FP32, (lbm.LBM_LAUNCH_GRID2, 32, 2), 200)
+    a = _run_launch(w, FP32, (lbm.LBM_LAUNCH_GRID_OCC, 32, 2), 200)
     b = _run_launch(w, FP32, (lbm.LBM_LAUNCH_GRID, 32, 2), 200)
     sa, sb = a.state_arrays(deviations=True), b.state_arrays(deviations=True)
     for k in sa:
