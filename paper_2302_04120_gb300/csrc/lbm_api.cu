@@ -1146,9 +1146,12 @@ extern "C" lbm_status lbm_batch_autotune(lbm_batch_t b, int out_cfg[3]) {
     st = batch_tiles(b, sh[0], sh[1]);
     if (st != LBM_OK) break;
     const int occ = lbmk::sp_batch_occupancy(b->prec, b->flow, b->th, sh[0] * sh[1]);
-    for (int m : mults) {
+    // grid-stride launches of a few blocks per SM, and one block per entry (the block
+    // scheduler then hands out the tiles)
+    for (int mi = 0; mi <= (int)(sizeof(mults) / sizeof(mults[0])); mi++) {
+      const int m = mi < (int)(sizeof(mults) / sizeof(mults[0])) ? mults[mi] : 0;
       if (m > (occ > 0 ? occ : 1) * 2) continue;
-      const int grid = sms * m;
+      const int grid = m ? sms * m : b->ntiles;
       b->bx = sh[0];
       b->by = sh[1];
       b->grid = grid;

@@ -110,11 +110,16 @@ __global__ void __launch_bounds__(256) k_step(const SpParams P) {
 // blockDim.x x blockDim.y tile of the channel's interior; an entry (channel, f0, 0, 1)
 // is blockDim.x * blockDim.y consecutive nodes of its boundary frame from frame
 // index f0 (the list puts these first), as in k_step_split.
+#ifndef LBM_BATCH_FP32_BLOCKS_PER_SM
+#define LBM_BATCH_FP32_BLOCKS_PER_SM 4
+#endif
 template <int PREC, int FLOW, int TH>
-__global__ void __launch_bounds__(256, PREC == 1 ? 4 : 3) k_batch_step(const SpParams *__restrict__ table, const int4 *__restrict__ tiles,
+__global__ void __launch_bounds__(256, PREC == 1 ? LBM_BATCH_FP32_BLOCKS_PER_SM : 3) k_batch_step(const SpParams *__restrict__ table, const int4 *__restrict__ tiles,
                                                      int ntiles) {
+  int4 next = blockIdx.x < ntiles ? tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int4 tl = tiles[t];
+    const int4 tl = next;
+    if (t + gridDim.x < ntiles) next = tiles[t + gridDim.x];  // the next entry's load overlaps this tile
     const SpParams &P = table[tl.x];
     if (tl.w == 1) {
       int i, j;
