@@ -244,36 +244,41 @@ def e2_percent(ref, num):
     return 100.0 * np.sqrt(np.sum((ref - num) ** 2) / np.sum(ref ** 2))
 
 
+def outlet_loss_jvp(w, steps, T_target, dnu=0.0, dq3=None, dqwall=None):
+    """The outlet-temperature loss L = mean_j (T(nx - 1, j; steps) - T_target[j])^2 of a
+    single-phase thermal solve (workload dict w: params, bcs, init, q3) and its exact
+    directional derivative along (dnu, dq3 (ny, nx), dqwall (2, nx)), from one run of
+    the oracle's forward-mode dual-number build.  Returns (L, dL)."""
+    p = w["params"]
+    ny = int(p["ny"])
+    T_target = np.asarray(T_target, dtype=np.float64)
+    o = Oracle(p, dual=True)
+    for bc in w["bcs"]:
+        o.set_bc(*bc)
+    if w.get("q3") is not None:
+        o.set_source(q3=w["q3"])
+    o.seed(dnu=dnu, dq3=dq3, dqwall=dqwall)
+    o.init(**(w.get("init") or {}))
+    o.step(steps)
+    T = o.moments()["T"][:, -1]
+    dT = o.tangent()["T"][:, -1]
+    o.close()
+    e = T - T_target
+    return float(np.mean(e ** 2)), float((2.0 * e / ny) @ dT)
+
+
 def outlet_loss_gradient(w, steps, T_target, q3=True, qwall=True, nu=True):
     """Reference gradient of the outlet-temperature loss
     L = mean_j (T(nx - 1, j; steps) - T_target[j])^2 of a single-phase thermal solve
     (workload dict w: params, bcs, init, q3), by forward-mode dual numbers: one
     directional derivative of the whole run per input element, each exact to
-    rounding.  Inputs: the heat-source field q''' (Eq. forcing_term_g via
-    qdot = q'''/(rho c_p)), the heat flux of the y- and y+ walls (Eq. BB_T) and the
+    rounding.  Inputs: the heat-source field (Eq. forcing_term_g via
+    qdot = q3/(rho c_p)), the heat flux of the y- and y+ walls (Eq. BB_T) and the
     kinematic viscosity (Eq. eq_kinematic_viscosity).  Returns (L, dL/dq3 (ny, nx),
     dL/dqwall (2, nx), dL/dnu); the parts not asked for are None."""
     p = w["params"]
     nx, ny = int(p["nx"]), int(p["ny"])
-    T_target = np.asarray(T_target, dtype=np.float64)
-
-    def run(**seed):
-        o = Oracle(p, dual=True)
-        for bc in w["bcs"]:
-            o.set_bc(*bc)
-        if w.get("q3") is not None:
-            o.set_source(q3=w["q3"])
-        o.seed(**seed)
-        o.init(**(w.get("init") or {}))
-        o.step(steps)
-        T = o.moments()["T"][:, -1]
-        dT = o.tangent()["T"][:, -1]
-        o.close()
-        return T, dT
-
-    T0, _ = run()
-    r = 2.0 * (T0 - T_target) / ny            # dL/dT_out
-    loss = float(np.mean((T0 - T_target) ** 2))
+    loss, _ = outlet_loss_jvp(w, steps, T_target)
     g3 = gw = gnu = None
     if q3:
         g3 = np.zeros((ny, nx))
@@ -281,14 +286,14 @@ def outlet_loss_gradient(w, steps, T_target, q3=True, qwall=True, nu=True):
             for i in range(nx):
                 e = np.zeros((ny, nx))
                 e[j, i] = 1.0
-                g3[j, i] = r @ run(dq3=e)[1]
+                g3[j, i] = outlet_loss_jvp(w, steps, T_target, dq3=e)[1]
     if qwall:
         gw = np.zeros((2, nx))
         for s in range(2):
             for i in range(nx):
                 e = np.zeros((2, nx))
                 e[s, i] = 1.0
-                gw[s, i] = r @ run(dqwall=e)[1]
+                gw[s, i] = outlet_loss_jvp(w, steps, T_target, dqwall=e)[1]
     if nu:
-        gnu = float(r @ run(dnu=1.0)[1])
+        gnu = outlet_loss_jvp(w, steps, T_target, dnu=1.0)[1]
     return loss, g3, gw, gnu

@@ -8,6 +8,8 @@ match central finite differences of the ORACLE's loss (relative step 1e-6) to
 1e-4 on a small channel with several checkpoint segments, and central
 differences of the GPU forward on the full 1024 x 128 workload; the autograd
 wrapper returns the same gradients."""
+import os
+
 import numpy as np
 import pytest
 
@@ -232,3 +234,40 @@ def test_fp32_adjoint_against_fp64_and_oracle():
     print(f"FP32 adjoint vs oracle: q3 {d3:.2e}, qwall {dw:.2e}, nu {dnu:.2e}, loss {abs(loss - L) / L:.2e}")
     assert abs(loss - L) <= 2e-3 * L
     assert d3 < 1e-3 and dw < 1e-3 and dnu < 1e-3
+
+
+ADJ_REF = os.path.join(os.path.dirname(__file__), "golden", "adjoint_reference_1024x128.json")
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-8), (1, 1e-3)])
+def test_adjoint_full_workload_against_oracle_reference(prec, tol):
+    """The gradient workload at its configuration (1024 x 128, 2000 steps, checkpoints
+    every 100) against exact directional derivatives of the oracle's run of it
+    (forward-mode dual numbers, tests/golden/adjoint_reference_1024x128.json, written by
+    make_adjoint_reference.py, which calls only the oracle): the loss, dL/dnu, dL/dq'''
+    at three sampled cells and along a smooth direction, dL/dq'' at two sampled wall
+    nodes.  FP64 within 1e-8 of each value, FP32 within 1e-3."""
+    import json
+    if not os.path.exists(ADJ_REF):
+        pytest.skip("oracle fixture not written yet: run tests/golden/make_adjoint_reference.py")
+    with open(ADJ_REF) as fh:
+        ref = json.load(fh)
+    w = wl.adjoint_channel()
+    nx, ny = w["params"]["nx"], w["params"]["ny"]
+    assert ref["steps"] == w["steps"] == 2000
+    target = np.array(ref["target"])
+    s = lbm.Solver(w["params"], precision=prec)
+    for bc in w["bcs"]:
+        s.set_bc(*bc)
+    s.set_source(w["q3"], None)
+    s.init(**w["init"])
+    loss, g3, gw, gnu = lbm.lbm_adjoint(s.h, 2000, 100, target, nx, ny)
+    s.close()
+    assert abs(loss - ref["loss"]) <= (1e-7 if prec == 0 else 2e-3) * ref["loss"]
+    assert abs(gnu - ref["dL_dnu"]) <= tol * abs(ref["dL_dnu"])
+    for c in ref["q3_cells"]:
+        assert abs(g3[c["j"], c["i"]] - c["dL"]) <= tol * abs(c["dL"]), c
+    d = wl.smooth_source(nx, ny, seed=ref["q3_direction"]["seed"], scale=1.0)
+    assert abs(np.sum(g3 * d) - ref["q3_direction"]["dL"]) <= tol * abs(ref["q3_direction"]["dL"])
+    for c in ref["qwall_nodes"]:
+        assert abs(gw[c["side"], c["i"]] - c["dL"]) <= tol * abs(c["dL"]), c
