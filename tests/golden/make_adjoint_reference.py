@@ -6,10 +6,12 @@ oracle's forward-mode dual-number build, one oracle run per derivative:
   * the loss L = mean_j (T(nx - 1, j) - T_target[j])^2 with T_target the outlet
     temperature of the same run without heat source plus 0.01 K sin(pi y / H)
     (reading R26), and dL/dnu;
-  * dL/dq''' at three cells drawn with numpy PCG64 seed 0 among the last 256 columns
-    (where the outlet loss is sensitive), and along one smooth direction (the workload's
-    filter applied to seed 7);
-  * dL/dq'' at two wall nodes drawn with the same generator.
+  * dL/dq''' at three cells drawn with numpy PCG64 seed 0 among the last 12 columns
+    (in the 1.25 ms of 2000 steps the flow, u_m = 0.079 m/s, carries heat 40 to 60
+    columns, so the outlet loss barely sees cells further upstream: 93 columns upstream
+    the derivative is below 1e-28), and along one
+    smooth direction (the workload's filter applied to seed 7);
+  * dL/dq'' at two wall nodes drawn with the same generator among the last 12 columns.
 
 Calls only the oracle and the seeded input generators.
 
@@ -52,8 +54,8 @@ def main():
     nx, ny, steps = w["params"]["nx"], w["params"]["ny"], w["steps"]
     target = target_profile(w, steps)
     rng = np.random.default_rng(0)
-    cells = [(int(rng.integers(0, ny)), int(rng.integers(nx - 256, nx))) for _ in range(3)]
-    walls = [(int(rng.integers(0, 2)), int(rng.integers(nx - 256, nx))) for _ in range(2)]
+    cells = [(int(rng.integers(0, ny)), int(rng.integers(nx - 12, nx))) for _ in range(3)]
+    walls = [(int(rng.integers(0, 2)), int(rng.integers(nx - 12, nx))) for _ in range(2)]
     direction = wl.smooth_source(nx, ny, seed=7, scale=1.0)
     L, dnu = oracle.outlet_loss_jvp(w, steps, target, dnu=1.0)
     out = dict(workload="channel_adjoint_1024x128_2000steps", steps=steps, target=[float(v) for v in target],
