@@ -40,7 +40,7 @@ __device__ __forceinline__ bool streams_in(const SpParams &P, int i, int j, int 
 // d(pre_p)/d(u_w) of the anti-BB outlet rule for outgoing direction o.
 template <typename R>
 __device__ __forceinline__ void dpre_duw(const SpParams &P, int o, R rw, R uwx, R uwy, R &gx, R &gy) {
-  const R c = K<R>(P).c, ics2 = (R)1 / K<R>(P).cs2;
+  const R c = K<R>(P).c, ics2 = K<R>(P).inv_cs2;
   const R cx = c * (R)cx9(o), cy = c * (R)cy9(o);
   const R cu = cx * uwx + cy * uwy;
   const R k = (R)2 * w9<R>(o) * rw;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const S *__r
   R dsnu = 0, dsq = 0;
   if (i < P.nx && j < P.ny) {
     const long long n = nidx(P, i, j);
-    const R c = K<R>(P).c, ic = (R)1 / c;
+    const R c = K<R>(P).c, ic = K<R>(P).inv_c;
     // ---- (1) Lam_X(t) = P^T Lam_pre(t+1) at this node --------------------------
     R lx[9], lg[5];
 #pragma unroll

@@ -142,6 +142,8 @@ static int axis_periodic(const lbm_t h, int axis, int thermal) {
 template <typename R>
 static void fill_const(const SpParams &P, lbmk::SpConst<R> &k) {
   k.c = (R)P.c; k.cs2 = (R)P.cs2; k.dt = (R)P.dt; k.rho0 = (R)P.rho0; k.T0 = (R)P.T0;
+  // the same IEEE divisions the kernels would take per thread, taken once here
+  k.inv_c = (R)1 / k.c; k.inv_cs2 = (R)1 / k.cs2; k.three_inv_c2 = (R)3 / (k.c * k.c);
   k.Fx = (R)P.Fx; k.Fy = (R)P.Fy; k.ux_pres = (R)P.ux_pres; k.uy_pres = (R)P.uy_pres;
   k.omega = (R)P.omega; k.s_e = (R)P.s_e; k.s_eps = (R)P.s_eps; k.s_q = (R)P.s_q; k.s_nu = (R)P.s_nu;
   k.omegaT = (R)P.omegaT; k.tsrc_fac = (R)P.tsrc_fac; k.flux_coef = (R)P.flux_coef;

@@ -111,7 +111,7 @@ __device__ __forceinline__ void pull_f(const SpParams &P, const S *src, int i, i
     for (int q = 0; q < 9; q++) f[q] = (R)src[q * P.plane + n];
     return;
   }
-  const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
+  const R c = K<R>(P).c, inv_cs2 = K<R>(P).inv_cs2;
   // 1. gather, branch-free so that all nine loads are in flight together: the
   //    streaming source (periodic wrap included), or for a link entering through a
   //    side the outgoing population o = opp(q) of this node
@@ -208,7 +208,7 @@ __device__ __forceinline__ void pull_g(const SpParams &P, const S *src, int i, i
     for (int q = 0; q < QT; q++) g[q] = (R)gsrc[q * P.plane + n];
     return;
   }
-  const R c = K<R>(P).c, inv_cs2 = (R)1 / K<R>(P).cs2;
+  const R c = K<R>(P).c, inv_cs2 = K<R>(P).inv_cs2;
   // 1. gather (branch-free, all loads in flight together)
   int side[QT], tk[QT];
   R raw[QT];
@@ -359,7 +359,7 @@ __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R
 
 template <typename R>
 __device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &m, R f[9]) {
-  const R c = K<R>(P).c, inv_cs2 = (R)3 / (c * c), inv_cs4 = inv_cs2 * inv_cs2;
+  const R c = K<R>(P).c, inv_cs2 = K<R>(P).three_inv_c2, inv_cs4 = inv_cs2 * inv_cs2;
   const R om = K<R>(P).omega;
   const R fac = ((R)1 - (R)0.5 * om) * K<R>(P).dt;  // (1 - dt/(2 tau)) dt
   const R hu = (R)0.5 * (m.ux * m.ux + m.uy * m.uy) * inv_cs2;  // u^2 / (2 c_s^2)
@@ -386,7 +386,7 @@ __device__ __forceinline__ void collide_bgk9(const SpParams &P, const Macro<R> &
 
 template <typename R>
 __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &m, R f[9]) {
-  const R c = K<R>(P).c, ic = (R)1 / c;
+  const R c = K<R>(P).c, ic = K<R>(P).inv_c;
   const R dt = K<R>(P).dt;
   // lattice-scaled moments of the deviations (rows of Eq. M_matrix)
   const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
@@ -437,7 +437,7 @@ __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &
 // geq_geral) on the thermal lattice QT.
 template <typename R, int QT = 5>
 __device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &m, R *g) {
-  const R c = K<R>(P).c, inv_cs2 = (R)3 / (c * c);
+  const R c = K<R>(P).c, inv_cs2 = K<R>(P).three_inv_c2;
   const R om = K<R>(P).omegaT;
   const R src = K<R>(P).tsrc_fac * K<R>(P).dt * m.qd;
   const R dT = m.T - K<R>(P).T0;
@@ -462,7 +462,7 @@ __device__ __forceinline__ void collide_bgk5(const SpParams &P, const Macro<R> &
 // (T - T0, -2 (T - T0), T - T0, T u_x/c, -T u_x/c, T u_y/c, -T u_y/c, 0, 0).
 template <typename R>
 __device__ __forceinline__ void collide_mrt9T(const SpParams &P, const Macro<R> &m, R g[9]) {
-  const R ic = (R)1 / K<R>(P).c, dt = K<R>(P).dt;
+  const R ic = K<R>(P).inv_c, dt = K<R>(P).dt;
   const R dT = m.T - K<R>(P).T0;
   const R sT = K<R>(P).omegaT;  // dt / tau_T
   const R qd = m.qd;
@@ -509,7 +509,7 @@ template <typename R>
 __device__ __forceinline__ void collide_mrt5(const SpParams &P, const Macro<R> &m, R g[5]) {
   // D2Q5 moments (1, c_x, c_y, 5|c|^2 - 4c^2, c_x^2 - c_y^2) scaled by c^-n; rates
   // (0, 1/tau_T, 1/tau_T, 1/dt, 1/dt); source Delta t (I - dt Lambda/2) M (w qdot).
-  const R ic = (R)1 / K<R>(P).c, dt = K<R>(P).dt;
+  const R ic = K<R>(P).inv_c, dt = K<R>(P).dt;
   const R dT = m.T - K<R>(P).T0;
   const R m1 = g[1] - g[3], m2 = g[2] - g[4];
   const R m3 = -(R)4 * g[0] + ((g[1] + g[2]) + (g[3] + g[4]));
