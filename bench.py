@@ -143,6 +143,31 @@ def _gpu_run(prec, steps, warmup, stream, torch, nx=CELLS_NX, ny=CELLS_NY, launc
     return times_ms, chk, launch
 
 
+def _cold_pick(prec, stream, torch, steps=60):
+    """The launch for the L2-flushed per-step timing.  The library's autotuner times
+    back-to-back steps, which on this 58.7 MB state run from L2 (as a long run does);
+    the timed steps start from a cold L2, so the autotuner's pick and the plain grid
+    shapes are timed again here under the same flush, and the fastest is used."""
+    from paper_2302_04120_gb300 import lbm
+    from paper_2302_04120_gb300 import workloads as wl
+    w = wl.channel(nx=CELLS_NX, ny=CELLS_NY, steps=0)
+    s = lbm.Solver(w["params"], precision=prec, stream=stream.cuda_stream)
+    s.apply_workload(w)
+    s.step(1)
+    s.autotune()
+    tuned = s.launch_config()
+    s.close()
+    cands = [tuned] + [c for c in [(0, 64, 1, 0), (0, 64, 2, 0), (0, 32, 2, 0), (0, 32, 4, 0), (0, 128, 1, 0)]
+                       if tuple(c) != tuple(tuned)]
+    best, best_t = tuned, None
+    for c in cands:
+        t, chk, _ = _gpu_run(prec, steps, 3, stream, torch, launch=tuple(c))
+        m = statistics.mean(t)
+        if chk == 0 and (best_t is None or m < best_t):
+            best, best_t = tuple(c), m
+    return best
+
+
 def _e2e(prec, steps, warmup, stream, torch):
     """End to end through the C ABI: every step uploads both walls' heat-flux
     profiles from pinned host memory (lbm_set_bc), advances one step and reads
@@ -504,13 +529,15 @@ def run_ours(args):
         print(json.dumps({"profile_step": WORKLOAD, "kernel": kname, "launch": _launch_desc(l32),
                           "ms_per_step": round(statistics.mean(t32), 5), "status": int(chk32)}), flush=True)
         return
+    launch32 = launch or _cold_pick(1, stream, torch)
+    launch64 = launch or _cold_pick(0, stream, torch, steps=20)
     # FP64 plain form (same grid), fewer steps: it is ALU-bound on GB300
-    t64, chk64, blk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch, launch=launch)
+    t64, chk64, blk64 = _gpu_run(0, max(args.steps // 4, 50), args.warmup, stream, torch, launch=launch64)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        t32, chk32, blk32 = _gpu_run(1, args.steps, args.warmup, stream, torch, launch=launch)
+        t32, chk32, blk32 = _gpu_run(1, args.steps, args.warmup, stream, torch, launch=launch32)
     torch.cuda.synchronize()
     total_s = _max_over_ranks(sum(t32) / 1e3, "cuda")
     # roofline-size variant: 8192 x 4096 nodes, 3.8 GB of state (>> 129 MB L2)
@@ -556,7 +583,9 @@ def run_ours(args):
                      "frac": round(ach32 / peak, 4), "peak_source": peak_kind,
                      "traffic": _traffic_from_profile(_kernel_tag(blk32) + "_fp32_mrt_mrt_2048x256"),
                      "kernel": _kernel_name(blk32), "algorithmic_bytes_per_launch": BYTES_PER_CELL[1] * cells,
-                     "launch": _launch_desc(blk32)},
+                     "launch": _launch_desc(blk32),
+                     "launch_selection": "fixed by --launch" if launch else
+                     "fastest of the autotuner's pick and 5 grid shapes, each timed over 60 L2-flushed steps"},
         "roofline_scaled": {"workload": "channel_d2q9mrt_d2q5mrt_8192x4096", "bound": "hbm",
                             "value": round(8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e6, 1), "unit_value": "MLUPS",
                             "achieved": round(BYTES_PER_CELL[1] * 8192 * 4096 / (statistics.mean(tsc) / 1e3) / 1e9, 1),
