@@ -315,7 +315,9 @@ lbm_status lbm_moments(lbm_t h, unsigned mask, double *out, int on_device);
 /*
  * Integrals with deterministic FP64 reductions (fixed tree order).  A bad cell is one
  * with a non-finite rho, u, T (thermal) or p (two-phase), or with |u| >= c; it is
- * counted in out[3] and adds nothing to out[0..2]:
+ * counted in out[3] and adds nothing to out[0..2].  Single-phase FP32 solves form
+ * |u|^2, its maximum and the |u| >= c test in FP32 (the precision of their u); the
+ * mass is summed in FP64 in every precision:
  *  out[0] = sum of rho dx^2 over the healthy cells (mass per unit depth, kg/m),
  *  out[1] = sum of phi over the healthy cells (two-phase, else 0),
  *  out[2] = max |u| over the healthy cells [m/s], out[3] = number of bad cells.

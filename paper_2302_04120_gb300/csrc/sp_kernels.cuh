@@ -207,89 +207,186 @@ __global__ void __launch_bounds__(256) k_moments(const SpParams P, unsigned mask
 // rho - rho0, 0, max |u|^2, bad-node count); a one-block final pass in a fixed order
 // adds (N - bad) rho0 and takes the one square root.  Bad nodes (a non-finite value or
 // |u| >= c) add nothing to the mass or to max |u|: they are only counted.
-__device__ __forceinline__ void block_partials(double drho, double u2, int bad, double *out) {
+// Error-free sum of two floats (Knuth's TwoSum): s + e equals a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// A sum of node values: FP64, or for FP32 values a compensated FP32 pair hi + lo
+// (each addition's rounding error carried in lo, so the pair keeps about twice FP32's
+// precision), so that the FP64 pipe, slow on GB300, is not used per node.  A plain
+// aggregate (it also lives in shared memory): clear() before use.
+template <typename R> struct NodeSum;
+template <> struct NodeSum<double> {
+  double v;
+  __device__ void clear() { v = 0.0; }
+  __device__ void add(double x) { v += x; }
+  __device__ void merge(const NodeSum &o) { v += o.v; }
+  __device__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __device__ double value() const { return v; }
+};
+template <> struct NodeSum<float> {
+  float hi, lo;
+  __device__ void clear() { hi = 0.f; lo = 0.f; }
+  __device__ void add(float x) {
+    float e;
+    two_sum(hi, x, hi, e);
+    lo += e;
+  }
+  __device__ void merge(const NodeSum &o) {
+    float e;
+    two_sum(hi, o.hi, hi, e);
+    lo += o.lo + e;
+  }
+  __device__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      NodeSum x;
+      x.hi = __shfl_down_sync(0xffffffffu, hi, o);
+      x.lo = __shfl_down_sync(0xffffffffu, lo, o);
+      merge(x);
+    }
+  }
+  __device__ double value() const { return (double)hi + (double)lo; }
+};
+
+// One block's partials in the working precision: sum of drho, max |u|^2, bad count.
+template <typename R> struct Part {
+  NodeSum<R> s;
+  R u2;
+  int bad;
+  __device__ void clear() { s.clear(); u2 = (R)0; bad = 0; }
+  __device__ void merge(const Part &o) {
+    s.merge(o.s);
+    u2 = u2 > o.u2 ? u2 : o.u2;
+    bad += o.bad;
+  }
+};
+// Partials written by other blocks of the launch: read through L2 (__ldcg).
+__device__ __forceinline__ Part<float> load_part(const Part<float> *p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+  Part<float> r;
+  r.s.hi = v.x; r.s.lo = v.y; r.u2 = v.z; r.bad = __float_as_int(v.w);
+  return r;
+}
+__device__ __forceinline__ Part<double> load_part(const Part<double> *p) {
+  Part<double> r;
+  r.s.v = __ldcg(&p->s.v); r.u2 = __ldcg(&p->u2); r.bad = __ldcg(&p->bad);
+  return r;
+}
+
+// Per-block partials in a fixed order: lane tree, then the warps in order.
+template <typename R>
+__device__ __forceinline__ void block_partials(Part<R> a, Part<R> *out) {
+  a.s.warp_reduce();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    drho += __shfl_down_sync(0xffffffffu, drho, o);
-    u2 = fmax(u2, __shfl_down_sync(0xffffffffu, u2, o));
+    const R u = __shfl_down_sync(0xffffffffu, a.u2, o);
+    a.u2 = a.u2 > u ? a.u2 : u;
+    a.bad += __shfl_down_sync(0xffffffffu, a.bad, o);
   }
-  const int nbad = __popc(__ballot_sync(0xffffffffu, bad));
-  __shared__ double sh[8][3];
+  __shared__ Part<R> sh[8];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-  if (lane == 0) { sh[warp][0] = drho; sh[warp][1] = u2; sh[warp][2] = (double)nbad; }
+  if (lane == 0) sh[warp] = a;
   __syncthreads();
   if (tid == 0) {
-    double a = 0, mx = 0, cnt = 0;
-    for (int w = 0; w < nw; w++) { a += sh[w][0]; mx = fmax(mx, sh[w][1]); cnt += sh[w][2]; }
-    out[0] = a; out[1] = 0.0; out[2] = mx; out[3] = cnt;
+    Part<R> b = sh[0];
+    for (int w = 1; w < nw; w++) b.merge(sh[w]);
+    *out = b;
   }
 }
 
-// Fixed-order sum of the nb per-block partials by one 256-thread block: thread t sums
-// partials t, t + 256, ... in order, then a fixed tree.  mass = ((N - bad) rho0 +
-// sum over healthy nodes of (rho - rho0)) dx^2, max |u| = sqrt(max |u|^2).
-__device__ __forceinline__ void final_reduce(const double *partials, int nb, double n_rho0, double rho0,
-                                             double area, double *out4) {
+// Fixed-order sum of the nb per-block partials by one 256-thread block: thread t
+// merges partials t, t + 256, ... in order, then a fixed tree, in the working
+// precision; one thread forms the FP64 results.  mass = ((N - bad) rho0 + sum over
+// healthy nodes of (rho - rho0)) dx^2, max |u| = sqrt(max |u|^2).
+template <typename R>
+__device__ __forceinline__ void final_reduce(const Part<R> *parts, int nb, double n_rho0, double rho0, double area,
+                                             double *out4) {
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  double a = 0, b = 0, mx = 0, cnt = 0;
-  for (int k = t; k < nb; k += 256) {
-    a += __ldcg(partials + 4 * k + 0);
-    b += __ldcg(partials + 4 * k + 1);
-    mx = fmax(mx, __ldcg(partials + 4 * k + 2));
-    cnt += __ldcg(partials + 4 * k + 3);
-  }
-  __shared__ double sh[4][256];
-  sh[0][t] = a; sh[1][t] = b; sh[2][t] = mx; sh[3][t] = cnt;
+  Part<R> a;
+  a.clear();
+  for (int k = t; k < nb; k += 256) a.merge(load_part(parts + k));
+  __shared__ Part<R> sh[256];
+  sh[t] = a;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if (t < w) {
-      sh[0][t] += sh[0][t + w];
-      sh[1][t] += sh[1][t + w];
-      sh[2][t] = fmax(sh[2][t], sh[2][t + w]);
-      sh[3][t] += sh[3][t + w];
-    }
+    if (t < w) sh[t].merge(sh[t + w]);
     __syncthreads();
   }
   if (t == 0) {
-    out4[0] = (n_rho0 - sh[3][0] * rho0 + sh[0][0]) * area;
-    out4[1] = sh[1][0];
-    out4[2] = sqrt(sh[2][0]);
-    out4[3] = sh[3][0];
+    const double bad = (double)sh[0].bad;
+    out4[0] = (n_rho0 - bad * rho0 + sh[0].s.value()) * area;
+    out4[1] = 0.0;
+    out4[2] = sqrt((double)sh[0].u2);
+    out4[3] = bad;
   }
 }
 
 // Integrals in one launch: every block writes its partials; the block that counts
 // last (a device counter, 0 on entry and reset by that block) makes the final pass.
+// The first fy rows of blocks take the boundary frame, one node per thread (its pull
+// rules are the long path); in the others each thread takes the interior nodes of its
+// column in `steps` groups of rows, with the pull compiled without boundary code.
+// drho is summed exactly enough for FP64 (NodeSum); |u|^2, its maximum and the health
+// test are taken in the working precision.  On GB300 the FP64 pipe bounded the form
+// with every quantity in FP64 (49 us on 2048 x 256, 57 % FP64 pipe).
+template <typename S, typename R, int FLOW, int TH, bool SYM, bool INNER>
+__device__ __forceinline__ void integrate_node(const SpParams &P, int i, int j, R c2, Part<R> &acc) {
+  const S *src = (const S *)P.src;
+  const bool interior = INNER || (!P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1));
+  R f[9], g[9];
+  if (FLOW != FLOW_NONE) pull_f<S, R, SYM && !INNER>(P, src, i, j, interior, f);
+  if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q, SYM && !INNER>(P, src, i, j, interior, g);
+  Macro<R> m;
+  load_sources<S, R>(P, (long long)j * P.pitch + i, m);
+  moments<R, FLOW, TH>(P, f, g, m);
+  const R uu = m.ux * m.ux + m.uy * m.uy;
+  const R Tchk = (TH != TH_NONE) ? m.T : (R)0;
+  if (!isfinite(m.drho) || !isfinite(uu) || !isfinite(Tchk) || uu >= c2) {
+    acc.bad++;
+  } else {
+    acc.s.add(m.drho);
+    acc.u2 = acc.u2 > uu ? acc.u2 : uu;
+  }
+}
+
 template <int PREC, int FLOW, int TH, bool SYM>
-__global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *partials, double n_rho0, double area,
-                                                   double *out4, unsigned *counter) {
+__global__ void __launch_bounds__(256, 3) k_integrals(const SpParams P, int steps, int fy, double *partials,
+                                                      double n_rho0, double area, double *out4, unsigned *counter) {
   // n_rho0 = N rho0 of the whole grid; final_reduce removes rho0 per bad node
   typedef typename Prec<PREC>::S S;
   typedef typename Prec<PREC>::R R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  double drho = 0.0, u2 = 0.0;
-  int bad = 0;
-  if (i < P.nx && j < P.ny) {
-    const long long n = (long long)j * P.pitch + i;
-    const S *src = (const S *)P.src;
-    const bool interior = !P.local && (i > 0) && (i < P.nx - 1) && (j > 0) && (j < P.ny - 1);
-    R f[9], g[9];
-    if (FLOW != FLOW_NONE) pull_f<S, R, SYM>(P, src, i, j, interior, f);
-    if (TH != TH_NONE) pull_g<S, R, ThLat<TH>::Q, SYM>(P, src, i, j, interior, g);
-    Macro<R> m;
-    load_sources<S, R>(P, n, m);
-    moments<R, FLOW, TH>(P, f, g, m);
-    const double ux = (double)m.ux, uy = (double)m.uy;
-    drho = (double)m.drho;
-    u2 = ux * ux + uy * uy;
-    const R Tchk = (TH != TH_NONE) ? m.T : (R)0;
-    bad = !isfinite(drho) || !isfinite(u2) || !isfinite(Tchk) || u2 >= P.c * P.c;
-    if (bad) { drho = 0.0; u2 = 0.0; }
+  const R c2 = K<R>(P).c * K<R>(P).c;
+  Part<R> acc;
+  acc.clear();
+  if ((int)blockIdx.y < fy) {
+    const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    int i, j;
+    if (frame_node(P.nx, P.ny, (blockIdx.y * gridDim.x + blockIdx.x) * nt + tid, i, j))
+      integrate_node<S, R, FLOW, TH, SYM, false>(P, i, j, c2, acc);
+  } else {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > 0 && i < P.nx - 1) {
+#pragma unroll 1
+      for (int r = 0; r < steps; r++) {
+        const int j = ((blockIdx.y - fy) * steps + r) * blockDim.y + threadIdx.y;
+        if (j >= P.ny - 1) break;
+        if (j < 1) continue;
+        if (P.local) integrate_node<S, R, FLOW, TH, SYM, false>(P, i, j, c2, acc);
+        else integrate_node<S, R, FLOW, TH, SYM, true>(P, i, j, c2, acc);
+      }
+    }
   }
-  block_partials(drho, u2, bad, partials + 4ll * (blockIdx.y * gridDim.x + blockIdx.x));
+  Part<R> *parts = reinterpret_cast<Part<R> *>(partials);  // sizeof(Part<R>) <= 4 doubles
+  block_partials<R>(acc, parts + blockIdx.y * gridDim.x + blockIdx.x);
   const unsigned nb = gridDim.x * gridDim.y;
   __shared__ bool last;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -299,7 +396,7 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
   __syncthreads();
   if (last) {
     __threadfence();
-    final_reduce(partials, (int)nb, n_rho0, P.rho0, area, out4);
+    final_reduce<R>(parts, (int)nb, n_rho0, P.rho0, area, out4);
     if (threadIdx.x == 0 && threadIdx.y == 0) *counter = 0u;
   }
 }
@@ -308,7 +405,6 @@ __global__ void __launch_bounds__(256) k_integrals(const SpParams P, double *par
 // Launch entry points
 // ----------------------------------------------------------------------------
 inline dim3 grid_for(int nx, int ny, dim3 b) { return dim3((nx + b.x - 1) / b.x, (ny + b.y - 1) / b.y); }
-constexpr int kRedBX = 64, kRedBY = 4;  // integrals block
 
 template <int PREC, int FLOW, int TH>
 cudaError_t SpOps<PREC, FLOW, TH>::step(const SpParams &P, dim3 block, cudaStream_t s) {
@@ -373,9 +469,12 @@ cudaError_t SpOps<PREC, FLOW, TH>::integrals(const SpParams &P, double *partials
                                              cudaStream_t s) {
   const dim3 block(kRedBX, kRedBY);
   const double n_rho0 = (double)P.nx * P.ny * P.rho0, area = P.dx * P.dx;
-  const dim3 grid = grid_for(P.nx, P.ny, block);
-  if (P.sym) k_integrals<PREC, FLOW, TH, true><<<grid, block, 0, s>>>(P, partials, n_rho0, area, out4, counter);
-  else k_integrals<PREC, FLOW, TH, false><<<grid, block, 0, s>>>(P, partials, n_rho0, area, out4, counter);
+  int steps, fy;
+  const dim3 grid = integral_grid(P.nx, P.ny, &steps, &fy);
+  if (P.sym)
+    k_integrals<PREC, FLOW, TH, true><<<grid, block, 0, s>>>(P, steps, fy, partials, n_rho0, area, out4, counter);
+  else
+    k_integrals<PREC, FLOW, TH, false><<<grid, block, 0, s>>>(P, steps, fy, partials, n_rho0, area, out4, counter);
   return cudaGetLastError();
 }
 

@@ -88,16 +88,16 @@ cudaError_t sp_moments(const SpParams &P, int prec, int flow, int th, unsigned m
   return cudaErrorInvalidValue;
 }
 
-static const dim3 kRedBlock(64, 4);
-
 int sp_integral_blocks(int nx, int ny) {
-  dim3 g = grid_for(nx, ny, kRedBlock);
+  int steps, fy;
+  dim3 g = integral_grid(nx, ny, &steps, &fy);
   return (int)(g.x * g.y);
 }
 
 cudaError_t sp_integrals(const SpParams &P, int prec, int flow, int th, double *partials, int max_blocks,
                          double *out4, unsigned *counter, cudaStream_t s) {
-  dim3 grid = grid_for(P.nx, P.ny, kRedBlock);
+  int steps, fy;
+  dim3 grid = integral_grid(P.nx, P.ny, &steps, &fy);
   if ((int)(grid.x * grid.y) > max_blocks) return cudaErrorInvalidValue;
 #define CALL(A, B, C) return SpOps<A, B, C>::integrals(P, partials, out4, counter, s)
   LBM_SP_DISPATCH(prec, flow, th, CALL);

@@ -26,11 +26,12 @@ def _cuda():
     build.build()
 
 
-def _check_pair(ref, got):
-    # same tolerance as the FP64 parity tests: 1e-12 relative
+def _check_pair(ref, got, umax_tol=1e-12):
+    # same tolerance as the FP64 parity tests: 1e-12 relative; max |u| of a
+    # single-phase FP32 solve is formed from |u|^2 rounded to FP32 (2^-24 relative)
     assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0])
     assert abs(got[1] - ref[1]) <= 1e-12 * max(abs(ref[1]), 1.0)
-    assert abs(got[2] - ref[2]) <= 1e-12 * ref[2]
+    assert abs(got[2] - ref[2]) <= umax_tol * ref[2]
     assert got[3] == ref[3]
 
 
@@ -51,7 +52,7 @@ def test_noalloc_matches_lbm_integrals_single_phase(prec):
                                              w["params"]["dx"], c, out)
         assert st == lbm.LBM_OK, lbm.lbm_last_error(None)
         torch.cuda.synchronize()
-        _check_pair(ref, out.cpu().numpy().tolist())
+        _check_pair(ref, out.cpu().numpy().tolist(), 1e-12 if prec == 0 else 1.2e-7)
 
 
 def test_noalloc_matches_lbm_integrals_two_phase():
