@@ -489,10 +489,10 @@ def run_ours(args):
     def wl_bubble(n):
         from paper_2302_04120_gb300 import workloads as wl
         return wl.bubble(n=n, R_cells=n / 8, W_cells=5.0, steps=0)
-    if args.profile_adjoint:
+    if args.profile_adjoint is not None:
         import numpy as np
         w = wl_adjoint()
-        s2 = lbm.Solver(w["params"], precision=0, stream=stream.cuda_stream)
+        s2 = lbm.Solver(w["params"], precision=args.profile_adjoint, stream=stream.cuda_stream)
         for bc in w["bcs"]:
             s2.set_bc(*bc)
         s2.set_source(w["q3"], None)
@@ -672,9 +672,9 @@ def main():
                     help="precision of --profile-step: 1 FP32 deviation (default), 0 FP64")
     ap.add_argument("--profile-two-phase", action="store_true",
                     help="run only a 1024x1024 FP32 bubble (for ncu captures of the two-phase kernel)")
-    ap.add_argument("--profile-adjoint", action="store_true",
+    ap.add_argument("--profile-adjoint", type=int, nargs="?", const=0, default=None, choices=[0, 1],
                     help="run only a short gradient run on the 1024x128 grid (40 steps, checkpoints every 20; "
-                         "for ncu captures of the reverse-step kernel)")
+                         "for ncu captures of the reverse-step kernel); 0 FP64 (default), 1 FP32")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -109,8 +109,15 @@ __global__ void k_adj_loss(const SpParams P, const double *Ttarget, R *LP, doubl
 
 // One reverse step.  P.src = X_{t-1} (P.local = 1 when t = 0), Xt = X_t,
 // LPn = Lam_pre(t+1), LP = Lam_pre(t) (output).
+// The FP32 reverse step is latency-bound (long-scoreboard stalls, 22 % warps active at
+// 100 registers and 2 blocks per SM): built for 4 resident blocks (64 registers, a few
+// spills) the gradient run of the 1024 x 128 workload takes 99.7 ms instead of 113.6 ms
+// (3 blocks: no gain).  The FP64 step is bound by the FP64 pipe: 2 blocks.
+#ifndef LBM_ADJ_FP32_BLOCKS_PER_SM
+#define LBM_ADJ_FP32_BLOCKS_PER_SM 4
+#endif
 template <typename S, typename R>
-__global__ void __launch_bounds__(256) k_adj_step(const SpParams P, const S *__restrict__ Xt,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_SM : 2) k_adj_step(const SpParams P, const S *__restrict__ Xt,
                                                   const R *__restrict__ LPn, R *__restrict__ LP,
                                                   double *grad_qdot, double *grad_flux2, double *grad_flux3,
                                                   double *nu_partials) {
