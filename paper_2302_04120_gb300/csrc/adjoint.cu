@@ -1,7 +1,8 @@
 // Reverse-time (discrete) adjoint of the single-phase fused step: D2Q9 MRT
 // momentum + D2Q5 MRT thermal, FP64 or FP32 (the adjoint of the FP32 deviation
 // form: states stored as FP32 deviations, adjoint variables and arithmetic in FP32,
-// parameter gradients accumulated in FP64), with the channel boundary rules
+// parameter gradients accumulated to FP64 precision: FP64 sums, or in the FP32 form
+// compensated FP32 pairs), with the channel boundary rules
 // (BB-velocity inlet and walls, anti-BB pressure outlet with extrapolated
 // velocity, anti-BB temperature inlet, heat-flux walls, thermal outflow).
 //
@@ -24,6 +25,7 @@
 #include "lattice.cuh"
 #include "lbm_internal.cuh"
 #include "sp_device.cuh"
+#include "compensated.cuh"
 
 namespace lbmk {
 
@@ -84,6 +86,31 @@ __device__ __forceinline__ void post_rho_u(const SpParams &P, const S *X, int i,
 
 }  // namespace
 
+// Per-node parameter-gradient accumulators (8 bytes per node): an FP64 sum, or in the
+// FP32 form a compensated FP32 pair (hi, lo) in the same 8 bytes, so that the reverse
+// step runs no FP64 instruction per node.  grad_value() gives the FP64 value.
+__device__ __forceinline__ void grad_add(double *g, long long n, double v) { g[n] += v; }
+__device__ __forceinline__ void grad_add(double *g, long long n, float v) {
+  float2 *g2 = reinterpret_cast<float2 *>(g);
+  float2 a = g2[n];
+  float e;
+  two_sum(a.x, v, a.x, e);
+  a.y += e;
+  g2[n] = a;
+}
+// An FP64 value into the accumulator of a form with working precision R.
+template <typename R> __device__ __forceinline__ void grad_add_fp64(double *g, long long n, double v);
+template <> __device__ __forceinline__ void grad_add_fp64<double>(double *g, long long n, double v) { g[n] += v; }
+template <> __device__ __forceinline__ void grad_add_fp64<float>(double *g, long long n, double v) {
+  const float hi = (float)v, lo = (float)(v - (double)hi);  // v = hi + lo to ~2^-48
+  float2 *g2 = reinterpret_cast<float2 *>(g);
+  float2 a = g2[n];
+  float e;
+  two_sum(a.x, hi, a.x, e);
+  a.y += e + lo;
+  g2[n] = a;
+}
+
 // Loss at the outlet column and the seed Lam_pre(N).  One thread per row j.  T - T_target
 // is formed in FP64 in both forms (FP32 would resolve T ~ 300 K only to ~3e-5 K).
 template <typename S, typename R>
@@ -104,7 +131,7 @@ __global__ void k_adj_loss(const SpParams P, const double *Ttarget, R *LP, doubl
   R *LPg = LP + (long long)P.gbase * P.plane;
 #pragma unroll
   for (int q = 0; q < 5; q++) LPg[q * P.plane + n] = (R)dLdT;
-  grad_qdot[n] += 0.5 * P.dt * dLdT;
+  grad_add_fp64<R>(grad_qdot, n, 0.5 * P.dt * dLdT);
 }
 
 // One reverse step.  P.src = X_{t-1} (P.local = 1 when t = 0), Xt = X_t,
@@ -254,7 +281,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
     const R lT = -sT * hx * t1 - sT * hy * t2 + (two / three) * t3;
     l_hx += -sT * m.T * t1;
     l_hy += -sT * m.T * t2;
-    grad_qdot[n] += (double)(half * dt * lT - dt * t0 + (dt / three) * t3);
+    grad_add(grad_qdot, n, (R)(half * dt * lT - dt * t0 + (dt / three) * t3));
 
     // ---- (5) back to the pre-collision populations ----------------------------
     R out[14];
@@ -282,23 +309,25 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
 #pragma unroll
     for (int q = 0; q < 14; q++) LP[q * P.plane + n] = out[q];
   }
-  // per-block, fixed-order sums of the nu-rate sensitivities (FP64)
-  double dn = (double)dsnu, dq = (double)dsq;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dn += __shfl_down_sync(0xffffffffu, dn, o);
-    dq += __shfl_down_sync(0xffffffffu, dq, o);
-  }
-  __shared__ double sh[8][2];
+  // per-block, fixed-order sums of the nu-rate sensitivities (working precision,
+  // compensated in FP32), added to the block's FP64 partials by one thread
+  NodeSum<R> dn, dq;
+  dn.clear();
+  dq.clear();
+  dn.add(dsnu);
+  dq.add(dsq);
+  dn.warp_reduce();
+  dq.warp_reduce();
+  __shared__ NodeSum<R> sh[8][2];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   if ((tid & 31) == 0) { sh[tid >> 5][0] = dn; sh[tid >> 5][1] = dq; }
   __syncthreads();
   if (tid == 0) {
-    double a = 0, b = 0;
-    for (int w = 0; w < (int)(blockDim.x * blockDim.y) / 32; w++) { a += sh[w][0]; b += sh[w][1]; }
+    NodeSum<R> a = sh[0][0], b = sh[0][1];
+    for (int w = 1; w < (int)(blockDim.x * blockDim.y) / 32; w++) { a.merge(sh[w][0]); b.merge(sh[w][1]); }
     double *acc = nu_partials + 2ll * (blockIdx.y * gridDim.x + blockIdx.x);
-    acc[0] += a;
-    acc[1] += b;
+    acc[0] += a.value();
+    acc[1] += b.value();
   }
 }
 

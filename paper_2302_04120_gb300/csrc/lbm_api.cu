@@ -1286,9 +1286,15 @@ extern "C" lbm_status lbm_adjoint(lbm_t h, long steps, int ckpt_every, const dou
       if (!tmp) { free(hl); st = fail(h, LBM_ERR_NOMEM, "host allocation"); goto done; }
       e = cudaMemcpyAsync(tmp, gq, pbytes, cudaMemcpyDeviceToHost, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      // per node an FP64 sum, or in the FP32 form a compensated FP32 pair (hi, lo)
+      const float *pair = (const float *)tmp;
       if (e == cudaSuccess)
         for (int j = 0; j < ny; j++)
-          for (int i = 0; i < nx; i++) g_q3[(size_t)j * nx + i] = tmp[(size_t)j * h->pitch + i] / (p.rho0 * p.cp);
+          for (int i = 0; i < nx; i++) {
+            const size_t k = (size_t)j * h->pitch + i;
+            const double g = h->elem == 4 ? (double)pair[2 * k] + (double)pair[2 * k + 1] : tmp[k];
+            g_q3[(size_t)j * nx + i] = g / (p.rho0 * p.cp);
+          }
       free(tmp);
       if (e != cudaSuccess) { free(hl); st = fail(h, LBM_ERR_CUDA, "gradient copy: %s", cudaGetErrorString(e)); goto done; }
     }
