@@ -144,6 +144,11 @@ static void fill_const(const SpParams &P, lbmk::SpConst<R> &k) {
   k.c = (R)P.c; k.cs2 = (R)P.cs2; k.dt = (R)P.dt; k.rho0 = (R)P.rho0; k.T0 = (R)P.T0;
   // the same IEEE divisions the kernels would take per thread, taken once here
   k.inv_c = (R)1 / k.c; k.inv_cs2 = (R)1 / k.cs2; k.three_inv_c2 = (R)3 / (k.c * k.c);
+  k.hdt = (R)0.5 * k.dt;
+  k.fk_e = ((R)1 - (R)0.5 * (R)P.s_e) * k.dt;
+  k.fk_eps = ((R)1 - (R)0.5 * (R)P.s_eps) * k.dt;
+  k.fk_q = ((R)1 - (R)0.5 * (R)P.s_q) * k.dt;
+  k.fk_nu = ((R)1 - (R)0.5 * (R)P.s_nu) * k.dt;
   k.Fx = (R)P.Fx; k.Fy = (R)P.Fy; k.ux_pres = (R)P.ux_pres; k.uy_pres = (R)P.uy_pres;
   k.omega = (R)P.omega; k.s_e = (R)P.s_e; k.s_eps = (R)P.s_eps; k.s_q = (R)P.s_q; k.s_nu = (R)P.s_nu;
   k.omegaT = (R)P.omegaT; k.tsrc_fac = (R)P.tsrc_fac; k.flux_coef = (R)P.flux_coef;

@@ -23,6 +23,8 @@ template <typename R>
 struct SpConst {
   R c, cs2, dt, rho0, T0, Fx, Fy, ux_pres, uy_pres;
   R inv_c, inv_cs2, three_inv_c2;  // 1/c, 1/cs2, 3/(c c), each rounded once in R
+  R hdt;                            // dt / 2
+  R fk_e, fk_eps, fk_q, fk_nu;      // MRT forcing factors (1 - s_k / 2) dt, s_k = dt Lambda_k
   R omega, s_e, s_eps, s_q, s_nu, omegaT, tsrc_fac, flux_coef, bgx, bgy, T_ref;
   R rho_w[4];
 };

@@ -331,10 +331,10 @@ __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R
     // Eq. zero_moment_g
     if (ThLat<TH>::Q == 9) m.sumg = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
     else m.sumg = (g[0] + g[1]) + (g[2] + g[3]) + g[4];
-    m.T = K<R>(P).T0 + m.sumg + (R)0.5 * K<R>(P).dt * m.qd;
+    m.T = K<R>(P).T0 + m.sumg + K<R>(P).hdt * m.qd;
     if (FLOW != FLOW_NONE && P.buoy) {
       // Boussinesq buoyancy with this step's temperature (Eq. buoyancy_force)
-      const R dT = (K<R>(P).T0 - K<R>(P).T_ref) + m.sumg + (R)0.5 * K<R>(P).dt * m.qd;
+      const R dT = (K<R>(P).T0 - K<R>(P).T_ref) + m.sumg + K<R>(P).hdt * m.qd;
       m.Fx += K<R>(P).bgx * dT;
       m.Fy += K<R>(P).bgy * dT;
     }
@@ -343,7 +343,7 @@ __device__ __forceinline__ void moments(const SpParams &P, const R f[9], const R
     // Eqs. zero_moment_f and first_moment_f
     m.drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     m.rho = K<R>(P).rho0 + m.drho;
-    const R c = K<R>(P).c, hdt = (R)0.5 * K<R>(P).dt;
+    const R c = K<R>(P).c, hdt = K<R>(P).hdt;
     const R jx = c * ((f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]));
     const R jy = c * ((f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]));
     const R inv = (R)1 / m.rho;
@@ -407,13 +407,14 @@ __device__ __forceinline__ void collide_mrt9(const SpParams &P, const Macro<R> &
   const R eq_xx = m.rho * (ux * ux - uy * uy), eq_xy = m.rho * ux * uy;
   const R s_e = K<R>(P).s_e, s_ep = K<R>(P).s_eps, s_q = K<R>(P).s_q, s_nu = K<R>(P).s_nu;
   // Delta m_k = dt Lambda_k (m_k - m_k^eq) - dt (1 - dt Lambda_k / 2) F_k  (Eq. colisao_MRT)
-  const R d_e = s_e * (m_e - eq_e) - ((R)1 - (R)0.5 * s_e) * dt * ((R)6 * uF);
-  const R d_ep = s_ep * (m_ep - eq_ep) + ((R)1 - (R)0.5 * s_ep) * dt * ((R)6 * uF);
+  // (the factors (1 - dt Lambda_k / 2) dt come from the host-filled constants)
+  const R d_e = s_e * (m_e - eq_e) - K<R>(P).fk_e * ((R)6 * uF);
+  const R d_ep = s_ep * (m_ep - eq_ep) + K<R>(P).fk_eps * ((R)6 * uF);
   const R d_jx = -dt * Fx, d_jy = -dt * Fy;
-  const R d_qx = s_q * (m_qx - eq_qx) + ((R)1 - (R)0.5 * s_q) * dt * Fx;
-  const R d_qy = s_q * (m_qy - eq_qy) + ((R)1 - (R)0.5 * s_q) * dt * Fy;
-  const R d_xx = s_nu * (m_xx - eq_xx) - ((R)1 - (R)0.5 * s_nu) * dt * ((R)2 * (ux * Fx - uy * Fy));
-  const R d_xy = s_nu * (m_xy - eq_xy) - ((R)1 - (R)0.5 * s_nu) * dt * (ux * Fy + uy * Fx);
+  const R d_qx = s_q * (m_qx - eq_qx) + K<R>(P).fk_q * Fx;
+  const R d_qy = s_q * (m_qy - eq_qy) + K<R>(P).fk_q * Fy;
+  const R d_xx = s_nu * (m_xx - eq_xx) - K<R>(P).fk_nu * ((R)2 * (ux * Fx - uy * Fy));
+  const R d_xy = s_nu * (m_xy - eq_xy) - K<R>(P).fk_nu * (ux * Fy + uy * Fx);
   // back to populations: M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
   const R a1 = d_e * ((R)1 / (R)36), a2 = d_ep * ((R)1 / (R)36);
   const R a3 = d_jx * ((R)1 / (R)6), a4 = d_qx * ((R)1 / (R)12);
@@ -519,7 +520,7 @@ __device__ __forceinline__ void collide_mrt5(const SpParams &P, const Macro<R> &
   const R d1 = sT * (m1 - m.T * m.ux * ic);
   const R d2 = sT * (m2 - m.T * m.uy * ic);
   // e-moment: rate 1/dt, equilibrium -(2/3) dT, source -(2/3) qdot with factor 1/2
-  const R d3 = (m3 + (R)(2.0 / 3.0) * dT) - (R)0.5 * dt * (-(R)(2.0 / 3.0) * m.qd);
+  const R d3 = (m3 + (R)(2.0 / 3.0) * dT) - K<R>(P).hdt * (-(R)(2.0 / 3.0) * m.qd);
   const R d4 = m4;
   const R a0 = d0 * (R)0.2, a1 = d1 * (R)0.5, a2 = d2 * (R)0.5, a3 = d3 * (R)0.05, a4 = d4 * (R)0.25;
   g[0] -= a0 - (R)4 * a3;
