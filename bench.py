@@ -507,6 +507,33 @@ def run_ours(args):
                           "loss": loss, "dL_dnu": gnu}), flush=True)
         s2.close()
         return
+    if args.profile_batch:
+        # only the first 16 channels of the batched workload (1.35e7 nodes, 1.5 GB of
+        # state, above L2), batched, for profiler captures of the batched step kernel
+        from paper_2302_04120_gb300 import workloads as wl
+        specs = wl.channel_batch_specs()[:16]
+        b = lbm.Batch([wl.channel(nx=sp["nx"], ny=sp["ny"], steps=0, Re=sp["Re"], Pr=sp["Pr"], dx=sp["dx"],
+                                  dt=sp["dt"])["params"] for sp in specs], precision=1, stream=stream.cuda_stream)
+        for ch, sp in zip(b.channels, specs):
+            w = wl.channel_from_spec(sp, steps=0)
+            for bc in w["bcs"]:
+                ch.set_bc(*bc)
+            ch.init(**w["init"])
+        b.step(2)
+        b.autotune()
+        b.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        nodes = sum(sp["nx"] * sp["ny"] for sp in specs)
+        print(json.dumps({"profile_batch": "channel_batch_seed4_first16", "kernel": "k_batch_step<1,FLOW_MRT,TH_MRT>",
+                          "nodes": nodes, "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 5),
+                          "status": int(min(c.check() for c in b.channels))}), flush=True)
+        b.close()
+        return
     if args.profile_two_phase:
         # only a 1024 x 1024 FP32 bubble (134 MB of state, above L2), for profiler captures
         w = wl_bubble(1024)
@@ -673,6 +700,9 @@ def main():
                     help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
     ap.add_argument("--profile-prec", type=int, default=1, choices=[0, 1],
                     help="precision of --profile-step: 1 FP32 deviation (default), 0 FP64")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run only the first 16 channels of the batched workload, batched (for ncu captures of "
+                         "the batched step kernel)")
     ap.add_argument("--profile-two-phase", action="store_true",
                     help="run only a 1024x1024 FP32 bubble (for ncu captures of the two-phase kernel)")
     ap.add_argument("--profile-adjoint", type=int, nargs="?", const=0, default=None, choices=[0, 1],
