@@ -3,11 +3,13 @@ against the oracle's run of the same workload in its long-double build (stored i
 tests/golden/ by make_channel_nusselt.py, which calls only the oracle):
 
   * the fields u_x, u_y and T - T_in element by element: FP64 to 1e-12 relative
-    max-norm (u relative to max |u|), FP32 deviation storage to 1e-5 relative L2;
+    max-norm (u relative to max |u|; measured 3.9e-15, 1.4e-15, 6.6e-14), FP32
+    deviation storage to 1e-5 relative L2 (measured 5.1e-7, 5.3e-8, 8.1e-6);
   * the local Nusselt number along both walls, Nu(x) = q'' D_h / (k (T_w - T_m)) with
     T_w by half-cell extrapolation and T_m the velocity-weighted bulk temperature
-    (reading R22), compared from column 8 on: over the first columns T_w - T_m
-    crosses zero next to the fixed-temperature inlet column, where Nu is singular.
+    (reading R22), compared from column 8 on (over the first columns T_w - T_m
+    crosses zero next to the fixed-temperature inlet column, where Nu is singular):
+    relative L2 1e-12 in FP64 (measured 4.6e-14), 1e-5 in FP32 (measured 4.5e-6).
 """
 import json
 import os
@@ -66,6 +68,6 @@ def test_channel_full_run_against_oracle(prec):
     p = w["params"]
     lower, upper = _local_nusselt(m["T"], m["ux"], w["qflux"], p["k"], p["dx"], w["H"])
     assert np.all(np.isfinite(lower)) and np.all(np.isfinite(upper))
-    tol = 1e-9 if prec == lbm.LBM_FP64 else 2e-5
+    tol = 1e-12 if prec == lbm.LBM_FP64 else 1e-5
     assert rel_l2(lower[8:], np.array(g["Nu_lower"])[8:]) < tol
     assert rel_l2(upper[8:], np.array(g["Nu_upper"])[8:]) < tol
