@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
       else outlet_G<S, R>(P, Xt, LPn, s, bi, bj, Gx, Gy);
       R rho, ux, uy;
       post_rho_u<S, R>(P, Xt, i, j, rho, ux, uy);
-      const R coef = on ? (R)1.5 : (R)-0.5;
+      const R coef = (on ? (R)1.5 : (R)-0.5) / rho;  // one division for the nine links
 #pragma unroll
-      for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * (R)cx9(q) - ux) + Gy * (c * (R)cy9(q) - uy)) / rho;
+      for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * (R)cx9(q) - ux) + Gy * (c * (R)cy9(q) - uy));
     }
     const R *LPng = LPn + (long long)P.gbase * P.plane;
 #pragma unroll
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
     Macro<R> m;
     load_sources<S, R>(P, n, m);
     moments<R, FLOW_MRT, TH_MRT>(P, f, g, m);
-    const R rho = m.rho;
+    const R rho = m.rho, irho = (R)1 / rho;
     const R hx = m.ux * ic, hy = m.uy * ic, usq = hx * hx + hy * hy;
     const R Fx = m.Fx * ic, Fy = m.Fy * ic;
     const R dt = K<R>(P).dt;
@@ -246,8 +246,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
     const R M_xx = (lx[1] + lx[3]) - (lx[2] + lx[4]);
     const R M_xy = (lx[5] + lx[7]) - (lx[6] + lx[8]);
     // dL/dd_k = -(M Lam)_k / |row_k|^2
-    const R de = -M_e / (R)36, dep = -M_ep / (R)36, dqx = -M_qx / (R)12, dqy = -M_qy / (R)12;
-    const R dxx = -M_xx / four, dxy = -M_xy / four;
+    // (products with the rounded reciprocals: a divide is a long sequence on the FP64 pipe)
+    const R de = -M_e * ((R)1 / (R)36), dep = -M_ep * ((R)1 / (R)36);
+    const R dqx = -M_qx * ((R)1 / (R)12), dqy = -M_qy * ((R)1 / (R)12);
+    const R dxx = -M_xx * (R)0.25, dxy = -M_xy * (R)0.25;
     const R se = K<R>(P).s_e, sep = K<R>(P).s_eps, sq = K<R>(P).s_q, snu = K<R>(P).s_nu;
     // dL/dm_k = s_k dL/dd_k; dL/deq_k = -s_k dL/dd_k
     const R lme = se * de, lmep = sep * dep, lmqx = sq * dqx, lmqy = sq * dqy, lmxx = snu * dxx, lmxy = snu * dxy;
@@ -257,16 +259,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
     const R m_xx = (f[1] + f[3]) - (f[2] + f[4]), m_xy = (f[5] + f[7]) - (f[6] + f[8]);
     const R eq_qx = -rho * hx, eq_qy = -rho * hy, eq_xx = rho * (hx * hx - hy * hy), eq_xy = rho * hx * hy;
     // nu enters through s_nu (stress moments) and s_q (third-order moments)
-    dsnu = dxx * ((m_xx - eq_xx) + half * dt * two * (hx * Fx - hy * Fy)) + dxy * ((m_xy - eq_xy) + half * dt * (hx * Fy + hy * Fx));
-    dsq = dqx * ((m_qx - eq_qx) - half * dt * Fx) + dqy * ((m_qy - eq_qy) - half * dt * Fy);
+    const R hdt = K<R>(P).hdt;
+    dsnu = dxx * ((m_xx - eq_xx) + hdt * two * (hx * Fx - hy * Fy)) + dxy * ((m_xy - eq_xy) + hdt * (hx * Fy + hy * Fx));
+    dsq = dqx * ((m_qx - eq_qx) - hdt * Fx) + dqy * ((m_qy - eq_qy) - hdt * Fy);
     const R le = -se * de, lep = -sep * dep, lqx = -sq * dqx, lqy = -sq * dqy, lxx = -snu * dxx, lxy = -snu * dxy;
     R l_drho = le * (-two + three * usq) + lep * ((R)1 - three * usq) + lqx * (-hx) + lqy * (-hy) +
                lxx * (hx * hx - hy * hy) + lxy * (hx * hy);
     R l_hx = le * (six * rho * hx) + lep * (-six * rho * hx) + lqx * (-rho) + lxx * (two * rho * hx) + lxy * (rho * hy);
     R l_hy = le * (six * rho * hy) + lep * (-six * rho * hy) + lqy * (-rho) + lxx * (-two * rho * hy) + lxy * (rho * hx);
     // forcing moments that depend on u
-    const R l_uF = -six * ((R)1 - half * se) * dt * de + six * ((R)1 - half * sep) * dt * dep;
-    const R l_Fxx = -((R)1 - half * snu) * dt * dxx * two, l_Fxy = -((R)1 - half * snu) * dt * dxy;
+    // (1 - dt Lambda_k / 2) dt from the host-filled constants
+    const R l_uF = -six * K<R>(P).fk_e * de + six * K<R>(P).fk_eps * dep;
+    const R l_Fxx = -K<R>(P).fk_nu * dxx * two, l_Fxy = -K<R>(P).fk_nu * dxy;
     l_hx += l_uF * Fx + l_Fxx * Fx + l_Fxy * Fy;
     l_hy += l_uF * Fy - l_Fxx * Fy + l_Fxy * Fx;
 
@@ -275,13 +279,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
     const R B1 = -(lg[1] - lg[3]), B2 = -(lg[2] - lg[4]);
     const R B3 = -(-four * lg[0] + ((lg[1] + lg[2]) + (lg[3] + lg[4])));
     const R B4 = -((lg[1] + lg[3]) - (lg[2] + lg[4]));
-    const R t0 = B0 / (R)5, t1 = B1 / two, t2 = B2 / two, t3 = B3 / (R)20, t4 = B4 / four;
+    const R t0 = B0 * (R)0.2, t1 = B1 * half, t2 = B2 * half, t3 = B3 * (R)0.05, t4 = B4 * (R)0.25;
     const R sT = K<R>(P).omegaT;
     const R lm1 = sT * t1, lm2 = sT * t2, lm3 = t3, lm4 = t4;
     const R lT = -sT * hx * t1 - sT * hy * t2 + (two / three) * t3;
     l_hx += -sT * m.T * t1;
     l_hy += -sT * m.T * t2;
-    grad_add(grad_qdot, n, (R)(half * dt * lT - dt * t0 + (dt / three) * t3));
+    grad_add(grad_qdot, n, (R)(hdt * lT - dt * t0 + (dt * ((R)1 / three)) * t3));
 
     // ---- (5) back to the pre-collision populations ----------------------------
     R out[14];
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
       const R xx_row = (q >= 1 && q <= 4) ? (R)(cxq * cxq - cyq * cyq) : (R)0;
       const R xy_row = q >= 5 ? (R)(cxq * cyq) : (R)0;
       R v = lx[q] + e_row * lme + ep_row * lmep + qx_row * lmqx + qy_row * lmqy + xx_row * lmxx + xy_row * lmxy;
-      v += l_drho + (l_hx * ((R)cxq - hx) + l_hy * ((R)cyq - hy)) / rho;
+      v += l_drho + (l_hx * ((R)cxq - hx) + l_hy * ((R)cyq - hy)) * irho;
       out[q] = v;
     }
 #pragma unroll
