@@ -156,67 +156,77 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? LBM_ADJ_FP32_BLOCKS_PER_
     const R c = K<R>(P).c, ic = K<R>(P).inv_c;
     // ---- (1) Lam_X(t) = P^T Lam_pre(t+1) at this node --------------------------
     R lx[9], lg[5];
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-      R acc = 0;
-      // streaming consumer: node y + c_q pulls population q from here
-      int xi = i + cx9(q), xj = j + cy9(q);
-      if (P.xper) xi = wrap(xi, P.nx);
-      if (P.yper) xj = wrap(xj, P.ny);
-      if (xi >= 0 && xi < P.nx && xj >= 0 && xj < P.ny && streams_in(P, xi, xj, cx9(q), cy9(q), P.xper, P.yper))
-        acc += LPn[q * P.plane + nidx(P, xi, xj)];
-      // reflection consumer: the incoming p = opp(q) at this node built from X_q here
-      const int p = opp9(q);
-      const int side = entry_side(i, j, cx9(p), cy9(p), P.nx, P.ny, P.xper, P.yper);
-      if (side >= 0) acc += (P.side[side].kind == BC_PRESSURE ? (R)-1 : (R)1) * LPn[p * P.plane + n];
-      lx[q] = acc;
-    }
-    // outlet velocity extrapolation u_w = 1.5 u(x_b) - 0.5 u(x_b - n)
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-      if (P.side[s].kind != BC_PRESSURE) continue;
-      const bool on = (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
-      const int bi = i - (s == 0) + (s == 1), bj = j - (s == 2) + (s == 3);  // boundary node outward of here
-      const bool inner = !on && ((s == 0 && i == 1) || (s == 1 && i == P.nx - 2) || (s == 2 && j == 1) ||
-                                 (s == 3 && j == P.ny - 2));
-      if (!on && !inner) continue;
-      R Gx, Gy;
-      if (on) outlet_G<S, R>(P, Xt, LPn, s, i, j, Gx, Gy);
-      else outlet_G<S, R>(P, Xt, LPn, s, bi, bj, Gx, Gy);
-      R rho, ux, uy;
-      post_rho_u<S, R>(P, Xt, i, j, rho, ux, uy);
-      const R coef = (on ? (R)1.5 : (R)-0.5) / rho;  // one division for the nine links
-#pragma unroll
-      for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * (R)cx9(q) - ux) + Gy * (c * (R)cy9(q) - uy));
-    }
     const R *LPng = LPn + (long long)P.gbase * P.plane;
+    if (i >= 2 && i <= P.nx - 3 && j >= 2 && j <= P.ny - 3) {
+      // two or more cells from every side: every consumer of this node's populations is
+      // an ordinary streaming link (no reflection, outlet extrapolation, flux or outflow
+      // rule reaches it), so Lam_X is the plain gather
 #pragma unroll
-    for (int q = 0; q < 5; q++) {
-      R acc = 0;
-      int xi = i + cx5(q), xj = j + cy5(q);
-      if (P.txper) xi = wrap(xi, P.nx);
-      if (P.typer) xj = wrap(xj, P.ny);
-      if (xi >= 0 && xi < P.nx && xj >= 0 && xj < P.ny && streams_in(P, xi, xj, cx5(q), cy5(q), P.txper, P.typer))
-        acc += LPng[q * P.plane + nidx(P, xi, xj)];
-      const int p = opp5(q);
-      const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
-      if (side >= 0) {
-        const int tk = P.side[side].tkind;
-        if (tk == TBC_FLUX) acc += LPng[p * P.plane + n];
-        else if (tk == TBC_TEMP) acc -= LPng[p * P.plane + n];
+      for (int q = 0; q < 9; q++) lx[q] = LPn[q * P.plane + n + (long long)cy9(q) * P.pitch + cx9(q)];
+#pragma unroll
+      for (int q = 0; q < 5; q++) lg[q] = LPng[q * P.plane + n + (long long)cy5(q) * P.pitch + cx5(q)];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; q++) {
+        R acc = 0;
+        // streaming consumer: node y + c_q pulls population q from here
+        int xi = i + cx9(q), xj = j + cy9(q);
+        if (P.xper) xi = wrap(xi, P.nx);
+        if (P.yper) xj = wrap(xj, P.ny);
+        if (xi >= 0 && xi < P.nx && xj >= 0 && xj < P.ny && streams_in(P, xi, xj, cx9(q), cy9(q), P.xper, P.yper))
+          acc += LPn[q * P.plane + nidx(P, xi, xj)];
+        // reflection consumer: the incoming p = opp(q) at this node built from X_q here
+        const int p = opp9(q);
+        const int side = entry_side(i, j, cx9(p), cy9(p), P.nx, P.ny, P.xper, P.yper);
+        if (side >= 0) acc += (P.side[side].kind == BC_PRESSURE ? (R)-1 : (R)1) * LPn[p * P.plane + n];
+        lx[q] = acc;
       }
-      // outflow consumer: the unknown q of an outflow side reads X_q of this node
-      const int qside = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
-      if (qside >= 0 && P.side[qside].tkind == TBC_OUTFLOW) acc += LPng[q * P.plane + n];
-      lg[q] = acc;
-    }
-    // wall heat flux gradient: pre_p = X_o + flux_coef q''(a) on flux sides
+      // outlet velocity extrapolation u_w = 1.5 u(x_b) - 0.5 u(x_b - n)
 #pragma unroll
-    for (int p = 1; p < 5; p++) {
-      const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
-      if (side >= 2 && P.side[side].tkind == TBC_FLUX) {
-        double *gf = side == 2 ? grad_flux2 : grad_flux3;
-        gf[i] += P.flux_coef * (double)LPng[p * P.plane + n];
+      for (int s = 0; s < 4; s++) {
+        if (P.side[s].kind != BC_PRESSURE) continue;
+        const bool on = (s == 0 && i == 0) || (s == 1 && i == P.nx - 1) || (s == 2 && j == 0) || (s == 3 && j == P.ny - 1);
+        const int bi = i - (s == 0) + (s == 1), bj = j - (s == 2) + (s == 3);  // boundary node outward of here
+        const bool inner = !on && ((s == 0 && i == 1) || (s == 1 && i == P.nx - 2) || (s == 2 && j == 1) ||
+                                   (s == 3 && j == P.ny - 2));
+        if (!on && !inner) continue;
+        R Gx, Gy;
+        if (on) outlet_G<S, R>(P, Xt, LPn, s, i, j, Gx, Gy);
+        else outlet_G<S, R>(P, Xt, LPn, s, bi, bj, Gx, Gy);
+        R rho, ux, uy;
+        post_rho_u<S, R>(P, Xt, i, j, rho, ux, uy);
+        const R coef = (on ? (R)1.5 : (R)-0.5) / rho;  // one division for the nine links
+#pragma unroll
+        for (int q = 0; q < 9; q++) lx[q] += coef * (Gx * (c * (R)cx9(q) - ux) + Gy * (c * (R)cy9(q) - uy));
+      }
+#pragma unroll
+      for (int q = 0; q < 5; q++) {
+        R acc = 0;
+        int xi = i + cx5(q), xj = j + cy5(q);
+        if (P.txper) xi = wrap(xi, P.nx);
+        if (P.typer) xj = wrap(xj, P.ny);
+        if (xi >= 0 && xi < P.nx && xj >= 0 && xj < P.ny && streams_in(P, xi, xj, cx5(q), cy5(q), P.txper, P.typer))
+          acc += LPng[q * P.plane + nidx(P, xi, xj)];
+        const int p = opp5(q);
+        const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
+        if (side >= 0) {
+          const int tk = P.side[side].tkind;
+          if (tk == TBC_FLUX) acc += LPng[p * P.plane + n];
+          else if (tk == TBC_TEMP) acc -= LPng[p * P.plane + n];
+        }
+        // outflow consumer: the unknown q of an outflow side reads X_q of this node
+        const int qside = entry_side(i, j, cx5(q), cy5(q), P.nx, P.ny, P.txper, P.typer);
+        if (qside >= 0 && P.side[qside].tkind == TBC_OUTFLOW) acc += LPng[q * P.plane + n];
+        lg[q] = acc;
+      }
+      // wall heat flux gradient: pre_p = X_o + flux_coef q''(a) on flux sides
+#pragma unroll
+      for (int p = 1; p < 5; p++) {
+        const int side = entry_side(i, j, cx5(p), cy5(p), P.nx, P.ny, P.txper, P.typer);
+        if (side >= 2 && P.side[side].tkind == TBC_FLUX) {
+          double *gf = side == 2 ? grad_flux2 : grad_flux3;
+          gf[i] += P.flux_coef * (double)LPng[p * P.plane + n];
+        }
       }
     }
 
