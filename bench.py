@@ -507,6 +507,24 @@ def run_ours(args):
                           "loss": loss, "dL_dnu": gnu}), flush=True)
         s2.close()
         return
+    if args.profile_integrals:
+        # only the FP32 2048 x 256 channel: `warmup` steps, then `steps` pairs of one step
+        # and one lbm_integrals, for profiler captures of the integrals kernel
+        from paper_2302_04120_gb300 import workloads as wl
+        w = wl.channel(steps=0)
+        s2 = lbm.Solver(w["params"], precision=1, stream=stream.cuda_stream)
+        s2.apply_workload(w)
+        s2.step(1)
+        s2.set_launch(0, 64, 1)
+        s2.step(args.warmup)
+        out = None
+        for _ in range(args.steps):
+            s2.step(1)
+            out = s2.integrals()
+        print(json.dumps({"profile_integrals": WORKLOAD, "kernel": "k_integrals<1,FLOW_MRT,TH_MRT>",
+                          "integrals": list(out), "status": int(s2.check())}), flush=True)
+        s2.close()
+        return
     if args.profile_batch:
         # only the first 16 channels of the batched workload (1.35e7 nodes, 1.5 GB of
         # state, above L2), batched, for profiler captures of the batched step kernel
@@ -700,6 +718,9 @@ def main():
                     help="run only the FP32 2048x256 leg (for ncu captures of the step kernel)")
     ap.add_argument("--profile-prec", type=int, default=1, choices=[0, 1],
                     help="precision of --profile-step: 1 FP32 deviation (default), 0 FP64")
+    ap.add_argument("--profile-integrals", action="store_true",
+                    help="run only the 2048x256 FP32 channel, one lbm_integrals after each step (for ncu captures "
+                         "of the integrals kernel)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run only the first 16 channels of the batched workload, batched (for ncu captures of "
                          "the batched step kernel)")
