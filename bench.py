@@ -658,7 +658,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "status": int(chk32),
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and ws == 1:  # the oracle on the host cores: rank 0 at N = 1 only
         line["cpu_baseline"] = _cpu_baseline()
         line["cpu_baseline"]["one_thread"] = _cpu_baseline_1thread()
     print(json.dumps(line), flush=True)
