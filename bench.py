@@ -618,6 +618,9 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(total_s / args.steps * 1e3, 5),
+        # spread of the per-step event times on this rank (the value above is their mean)
+        "step_ms_quantiles": {q: round(sorted(t32)[min(len(t32) - 1, int(f * len(t32)))], 5)
+                              for q, f in (("p10", 0.1), ("p50", 0.5), ("p90", 0.9), ("max", 1.0))},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
