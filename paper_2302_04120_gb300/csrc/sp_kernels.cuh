@@ -220,9 +220,6 @@ template <typename R> struct Part {
     bad += o.bad;
   }
 };
-// The partials buffer holds 4 doubles per block; the FP32 partial is read as one float4.
-static_assert(sizeof(Part<double>) <= 4 * sizeof(double), "a partial must fit its 32-byte slot");
-static_assert(sizeof(Part<float>) == sizeof(float4), "the FP32 partial is loaded as one float4");
 // Partials written by other blocks of the launch: read through L2 (__ldcg).
 __device__ __forceinline__ Part<float> load_part(const Part<float> *p) {
   const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
