@@ -387,8 +387,9 @@ void lbm_batch_destroy(lbm_batch_t b);
  * Reverse-time discrete adjoint of the fused step for single-phase D2Q9 MRT + D2Q5 MRT
  * solves, in the handle's precision: FP64, or FP32 (the forward in FP32 deviation
  * storage, the adjoint variables and their arithmetic in FP32, the parameter gradients
- * accumulated in FP64; its gradient is that of the FP32 forward map, to FP32
- * rounding).  Call right after lbm_init_fields (and lbm_set_bc, lbm_set_source):
+ * accumulated to FP64 precision (the per-cell q''' gradient and the nu sums in
+ * compensated FP32 pairs, converted once); its gradient is that of the FP32 forward
+ * map, to FP32 rounding).  Call right after lbm_init_fields (and lbm_set_bc, lbm_set_source):
  * it runs the forward `steps` steps itself, keeping a checkpoint every ckpt_every
  * steps, then walks the steps backwards, recomputing each segment's states from its
  * checkpoint.  Device memory: (steps/ckpt_every + ckpt_every + 3) state buffers.  On
